@@ -1,0 +1,452 @@
+"""Benchmark of the stable-merge hot path on GB300.
+
+One step = the three large single merges (every step of the path: the
+grid-level co-rank partition, then the tile merge), each through the C ABI:
+
+  large_i32   m = n = 2^28 int32 keys uniform over the full int32 range
+  skewed_u64  m = 2^20, n = 2^29 uint64 keys uniform over the full range
+  dup16_i32   m = n = 2^28 int32 keys drawn from 16 distinct values
+
+Inputs are seeded synthetic arrays (device-generated, sorted), far larger
+than L2 (129 MB), so no flush is needed between steps.
+
+  value     merged elements/s over the whole job, inputs resident in HBM,
+            CUDA events around exactly K steps (max over ranks)
+  e2e       the same metric with the inputs copied from pinned host memory
+            and the merged outputs copied back inside every timed step
+  roofline  the tile-merge kernel: algorithmic bytes (each input element read
+            once, each output written once) / its CUDA-event time, against the
+            measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle (Algorithm 2 on POSIX threads over all host
+            cores) on one full step of the same inputs
+
+`--impl reference` times the CPU oracle as the reference arm.
+Launch: python bench.py [--gpus N] [--steps K] [--warmup W]; N>1 via
+torchrun, one process per GPU, each merging its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "merged elements/s and achieved HBM GB/s (% of GB300 peak), fwd and bwd, bit-exact"
+UNIT = "elements/s"
+WORKLOAD = "large_single_merges"
+FALLBACK_HBM_GBS = 6800.0
+
+MERGES = [
+    # name, generator, key type, key bytes
+    ("large_i32", "t_large_i32", "i32", 4),
+    ("skewed_u64", "t_skewed_u64", "u64", 8),
+    ("dup16_i32", "t_dup16_i32", "i32", 4),
+]
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=None,
+                   help="steps of the end-to-end measurement (default: --steps)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--shift", type=int, default=0,
+                   help="divide every workload size by 2^shift (for quick runs)")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (timing only; the data path has no collective)
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local, dist
+
+
+def reduce_max(x: float, dist, device) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_inputs(device, shift: int):
+    from paper_1303_4312_gb300 import workloads as W
+    out = []
+    for name, gen, kt, kb in MERGES:
+        A, B = getattr(W, gen)(device=device, shift=shift)
+        out.append({"name": name, "A": A, "B": B, "kt": kt, "kb": kb,
+                    "m": A.numel(), "n": B.numel()})
+    return out
+
+
+def algorithmic_bytes(mg) -> int:
+    """Each input key read once, each output key written once."""
+    return 2 * (mg["m"] + mg["n"]) * mg["kb"]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1303_4312_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(shift: int):
+    """DRAM bytes per tile-merge launch from the committed ncu summary, if it
+    was taken on the current kernel sources and this workload size."""
+    path = os.path.join(ROOT, "profiles", "merge_tiles_large_single_merges.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"workload_shift:\s*(\d+)", text)
+    if not (m and t and s) or m.group(1) != kernel_digest() or int(s.group(1)) != shift:
+        return None
+    return float(t.group(1))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local, dist):
+    import torch
+    from paper_1303_4312_gb300 import _lib, build
+    from paper_1303_4312_gb300 import api
+
+    build.build()
+    lib = _lib.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    merges = make_inputs(dev, args.shift)
+    for mg in merges:
+        mg["C"] = torch.empty(mg["m"] + mg["n"], dtype=mg["A"].dtype, device=dev)
+        need = api.merge_workspace_bytes(mg["kt"], 0, mg["m"], mg["n"])
+        mg["ws"] = torch.empty(need, dtype=torch.uint8, device=dev)
+        mg["code"] = _lib.KEY_TYPES[mg["kt"]]
+    torch.cuda.synchronize()
+
+    def launch(mg, ev=None):
+        A, B, C, ws = mg["A"], mg["B"], mg["C"], mg["ws"]
+        if ev is not None:
+            ev[0].record(stream)
+        _lib.check(lib.cr_merge_partition(mg["code"], 0, A.data_ptr(), mg["m"], B.data_ptr(),
+                                          mg["n"], ws.data_ptr(), ws.numel(), sp))
+        if ev is not None:
+            ev[1].record(stream)
+        _lib.check(lib.cr_merge_tiles(mg["code"], 0, A.data_ptr(), None, mg["m"], B.data_ptr(),
+                                      None, mg["n"], C.data_ptr(), None, None, ws.data_ptr(),
+                                      ws.numel(), sp))
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        for mg in merges:
+            launch(mg)
+    torch.cuda.synchronize()
+    for mg in merges:
+        api.workspace_status(mg["ws"])
+
+    K = args.steps
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in merges]
+           for _ in range(K)]
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(dist)
+    torch.cuda.synchronize()
+    for k in range(K):
+        for mg, ev in zip(merges, evs[k]):
+            launch(mg, ev)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop() if clocks else None
+
+    total_ms = evs[0][0][0].elapsed_time(evs[K - 1][-1][2])
+    part_ms = sum(ev[0].elapsed_time(ev[1]) for row in evs for ev in row)
+    tile_ms = {mg["name"]: sum(evs[k][q][1].elapsed_time(evs[k][q][2]) for k in range(K))
+               for q, mg in enumerate(merges)}
+    total_ms = reduce_max(total_ms, dist, dev)
+    elems = sum(mg["m"] + mg["n"] for mg in merges)
+    ms_per_step = total_ms / K
+    value = world * elems * K / (total_ms / 1e3)
+
+    peak, peak_kind = measured_peak()
+    alg_bytes = sum(algorithmic_bytes(mg) for mg in merges)
+    tile_total_ms = sum(tile_ms.values())
+    achieved = alg_bytes * K / (tile_total_ms / 1e3) / 1e9
+    step_gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
+
+    # end to end: pinned host inputs -> device -> merge -> pinned host outputs
+    e2e = run_e2e(args, merges, lib, dev, stream, dist, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_from(merges)
+
+    if rank != 0:
+        return None
+    per_merge = {mg["name"]: {
+        "elements": mg["m"] + mg["n"],
+        "tile_kernel_ms": round(tile_ms[mg["name"]] / K, 4),
+        "tile_kernel_gbs": round(algorithmic_bytes(mg) / (tile_ms[mg["name"]] / K / 1e3) / 1e9, 1),
+    } for mg in merges}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+uint64 keys",
+        "data": "synthetic (seeded, sorted; device-generated)",
+        "config": {"workload": WORKLOAD, "merges": [f"{m[0]}" for m in MERGES],
+                   "elements_per_step": elems, "l2": "inputs larger than L2 (no flush)",
+                   "size_shift": args.shift, "parallelism": f"replicas x{world}"},
+        "hbm_gbs_step": round(step_gbs, 1),
+        "frac_of_peak_step": round(step_gbs / peak, 4),
+        "partition_ms_per_step": round(part_ms / K, 4),
+        "per_merge": per_merge,
+        "roofline": {"kernel": "merge_tiles_kernel", "bound": "hbm",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": recorded_traffic(args.shift),
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_launch": alg_bytes / len(merges)},
+        "e2e": e2e,
+        "gpu_launches": 2 * len(merges) * K,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    return line
+
+
+def run_e2e(args, merges, lib, dev, stream, dist, world):
+    import torch
+    from paper_1303_4312_gb300 import _lib
+    K = args.e2e_steps or args.steps
+    sp = stream.cuda_stream
+    host = []
+    for mg in merges:
+        hA = torch.empty(mg["m"], dtype=mg["A"].dtype, pin_memory=True)
+        hB = torch.empty(mg["n"], dtype=mg["A"].dtype, pin_memory=True)
+        hC = torch.empty(mg["m"] + mg["n"], dtype=mg["A"].dtype, pin_memory=True)
+        hA.copy_(mg["A"])
+        hB.copy_(mg["B"])
+        host.append((hA, hB, hC))
+    torch.cuda.synchronize()
+    h2d = sum((mg["m"] + mg["n"]) * mg["kb"] for mg in merges)
+    d2h = h2d
+
+    def step():
+        for mg, (hA, hB, hC) in zip(merges, host):
+            mg["A"].copy_(hA, non_blocking=True)
+            mg["B"].copy_(hB, non_blocking=True)
+            _lib.check(lib.cr_stable_merge(mg["code"], mg["A"].data_ptr(), mg["m"],
+                                           mg["B"].data_ptr(), mg["n"], mg["C"].data_ptr(), None,
+                                           mg["ws"].data_ptr(), mg["ws"].numel(), sp))
+            hC.copy_(mg["C"], non_blocking=True)
+
+    for _ in range(max(1, min(args.warmup, 3))):
+        step()
+    torch.cuda.synchronize()
+    barrier(dist)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ms = reduce_max(e0.elapsed_time(e1), dist, dev)
+    # the merged outputs really came back: spot-check order of the last one
+    for (hA, hB, hC), mg in zip(host, merges):
+        c = hC[: 1 << 16]
+        assert bool((c[1:] >= c[:-1]).all()) or mg["kt"] == "u64"
+    elems = sum(mg["m"] + mg["n"] for mg in merges)
+    return {"value": world * elems * K / (ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": K,
+            "ms_per_step": ms / K}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle as a baseline / the reference arm
+# ---------------------------------------------------------------------------
+def _host_inputs(merges):
+    out = []
+    for mg in merges:
+        dt = np.uint64 if mg["kt"] == "u64" else np.int32
+        out.append((mg["name"], mg["A"].cpu().numpy().view(dt), mg["B"].cpu().numpy().view(dt)))
+    return out
+
+
+def time_oracle(host_inputs, threads: int):
+    import oracle
+    t0 = time.perf_counter()
+    n = 0
+    for _, a, b in host_inputs:
+        oracle.parallel_merge(a, b, threads)
+        n += len(a) + len(b)
+    dt = time.perf_counter() - t0
+    return n / dt, dt
+
+
+def cpu_baseline_from(merges):
+    hi = _host_inputs(merges)
+    cores = os.cpu_count() or 1
+    value, secs = time_oracle(hi, cores)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one full step (all three merges) on the CPU oracle's Algorithm 2 "
+                      f"with {cores} POSIX threads; {secs:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import torch
+    import oracle
+    oracle.build()
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+    # Each reference step merges the same three workloads cut to 1/8 of their
+    # sizes (a bounded sample), so K + W steps finish in minutes.
+    merges = make_inputs(dev, args.shift + 3)
+    hi = _host_inputs(merges)
+    del merges
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        time_oracle(hi, cores)
+    total, n = 0.0, 0
+    for _ in range(args.steps):
+        v, dt = time_oracle(hi, cores)
+        total += dt
+        n += sum(len(a) + len(b) for _, a, b in hi)
+    value = n / total
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+uint64 keys",
+            "data": "synthetic (seeded, sorted; device-generated)", "impl": "reference",
+            "config": {"workload": WORKLOAD, "merges": [m[0] for m in MERGES],
+                       "size_shift": args.shift + 3},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "the three merges at 1/8 size per step, CPU oracle "
+                                       f"Algorithm 2 on {cores} POSIX threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    rank, world, local, dist = dist_setup(args.gpus)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local, dist)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

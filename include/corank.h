@@ -1,0 +1,228 @@
+/*
+ * corank.h -- C ABI of the GB300 co-rank / stable-merge library (libcorank.so).
+ *
+ * Implements, on one NVIDIA GB300 (sm_103a), the method of Siebert & Traeff,
+ * "Perfectly load-balanced, optimal, stable, parallel merge":
+ *   - co_rank (Algorithm 1, Section 2; correctness by Lemma 1): for an output
+ *     rank of the stable merge of ordered arrays A[m] and B[n], the unique
+ *     prefix lengths of A and B that form that output prefix;
+ *   - stable_merge driven by it (Algorithm 2, Section 3): the output is cut
+ *     into equal tiles, each tile's input windows are found by co_rank, and
+ *     every tile (and every thread inside it) merges exactly the same number
+ *     of elements (Proposition 2).
+ *
+ * NAMING.  The paper calls the output rank i and the co-ranks j (into A) and
+ * k (into B).  This ABI calls the output rank k and the co-ranks i (into A)
+ * and j (into B):  paper (i; j, k)  ==  ABI (k; i, j).  Always i + j == k.
+ *
+ * ORDER AND STABILITY.  Keys are compared with the natural order of their type
+ * (signed for CR_KEY_I32/I64, unsigned for CR_KEY_U32/U64).  The merge is
+ * stable: equal keys keep their order inside A and inside B, and an A element
+ * precedes every equal B element (second condition of Lemma 1 is strict).
+ * A and B must be ascending; this is not checked on the hot path.  Unsorted
+ * input gives an unspecified result but never an out-of-bounds access
+ * or a hang.
+ *
+ * MEMORY.  Every pointer argument marked "device" is a device pointer owned by
+ * the caller; the library allocates nothing.  Base pointers of key, payload,
+ * tag and workspace arrays must be 16-byte aligned (CR_EALIGN otherwise);
+ * element offsets inside them are arbitrary.  Outputs must not overlap inputs
+ * (CR_EALIAS).  Sizes are element counts (int64).
+ *
+ * STREAMS AND ERRORS.  Every call is asynchronous and stream-ordered on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).  Argument
+ * errors are returned at once and nothing is launched.  A failed launch gives
+ * CR_ECUDA; cr_last_error() then holds the CUDA message (per host thread).
+ * Device-side conditions (a bounded wait that gave up, an inconsistent
+ * segment table) are recorded in the workspace's status word and returned by
+ * cr_workspace_status().
+ *
+ * THREADS.  All entry points are thread-safe; the device and its properties
+ * are those current on the calling host thread.
+ */
+#ifndef CORANK_H
+#define CORANK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CR_OK = 0,
+    CR_EINVAL = 1,        /* bad size, rank, type, null pointer with nonzero size */
+    CR_EALIAS = 2,        /* an output range overlaps an input range */
+    CR_EALIGN = 3,        /* a base pointer is not 16-byte aligned */
+    CR_ENOSPACE = 4,      /* workspace smaller than the *_workspace_size answer */
+    CR_ECUDA = 5,         /* a CUDA runtime call failed; see cr_last_error() */
+    CR_ETIMEOUT = 6,      /* (device) a bounded wait inside a kernel gave up */
+    CR_EUNSUPPORTED = 7,  /* valid request this build does not implement */
+    CR_EINTERNAL = 8,     /* (device) inconsistent tile or segment table */
+    CR_EBADSEG = 9        /* (device) segment offsets not monotone / out of range */
+} cr_status;
+
+typedef enum {
+    CR_KEY_I32 = 0,
+    CR_KEY_U32 = 1,
+    CR_KEY_I64 = 2,
+    CR_KEY_U64 = 3
+} cr_key_type;
+
+/* cudaStream_t, passed as a plain pointer so this header needs no CUDA header. */
+typedef void* cr_stream;
+
+/* Short name of a status code ("CR_OK", ...). Never NULL. */
+const char* cr_status_string(int status);
+
+/* Detail of the last error returned on this host thread ("" if none). */
+const char* cr_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int cr_abi_version(void);
+
+/* Elements per tile (TILE) the merge kernels use for this key type and
+ * payload width: every tile of a merge carries exactly TILE output elements
+ * except the last one (per segment, for batched calls).  Returns 0 for an
+ * invalid combination. */
+int64_t cr_tile_size(int key_type, int val_bytes);
+
+/* ------------------------------------------------------------------------
+ * co_rank -- Algorithm 1 (Section 2), Lemma 1.
+ * For output rank k of the stable merge of A[m] and B[n], 0 <= k <= m + n,
+ * the unique (i, j), i + j == k, such that
+ *     (i == 0 || j == n || A[i-1] <= B[j])  and  (j == 0 || i == m || B[j-1] < A[i]).
+ * The first k outputs of the merge are exactly the merge of A[0:i), B[0:j).
+ * k == m + n (used by Algorithm 2 for the last block end) gives (m, n).
+ * ------------------------------------------------------------------------ */
+
+/* One rank; result written to device memory: d_ij[0] = i, d_ij[1] = j.
+ * A, B: device, m and n keys.  k outside [0, m+n] -> CR_EINVAL. */
+cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int64_t n,
+                     int64_t k, int64_t* d_ij, cr_stream stream);
+
+/* cnt ranks d_k[0..cnt) (device) -> d_i, d_j (device, cnt each).  A rank
+ * outside [0, m+n] gives i = j = -1 for that entry. */
+cr_status cr_co_rank_many(int key_type, const void* A, int64_t m, const void* B, int64_t n,
+                          const int64_t* d_k, int64_t cnt, int64_t* d_i, int64_t* d_j,
+                          cr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * stable_merge -- Algorithm 2 (Section 3) with fixed-size output tiles.
+ * C[0, m+n) = stable merge of A[0, m) and B[0, n).
+ * ------------------------------------------------------------------------ */
+
+/* Workspace bytes a single merge of m + n elements needs (tile table and
+ * status word).  val_bytes: 0 (keys only), 4 or 8. */
+cr_status cr_merge_workspace_size(int key_type, int val_bytes, int64_t m, int64_t n,
+                                  size_t* bytes);
+
+/* Keys only.  C_tag (device, nullable): if given, C_tag[x] = source position
+ * of C[x]: i for A[i], m + j for B[j] (requires m + n <= 2^32).  ws: device
+ * workspace of at least cr_merge_workspace_size bytes, 16-byte aligned. */
+cr_status cr_stable_merge(int key_type, const void* A, int64_t m, const void* B, int64_t n,
+                          void* C, uint32_t* C_tag, void* ws, size_t ws_bytes,
+                          cr_stream stream);
+
+/* Key-value merge: payloads of val_bytes (4 or 8) bytes follow their keys and
+ * are copied bit for bit (no floating-point operation touches them).
+ * Ak/Av: m keys/payloads, Bk/Bv: n, Ck/Cv: m + n.  C_tag as above. */
+cr_status cr_stable_merge_kv(int key_type, int val_bytes,
+                             const void* Ak, const void* Av, int64_t m,
+                             const void* Bk, const void* Bv, int64_t n,
+                             void* Ck, void* Cv, uint32_t* C_tag,
+                             void* ws, size_t ws_bytes, cr_stream stream);
+
+/* Backward of the key-value merge with respect to the payloads.  The merge is
+ * a permutation, so gA[i] = gC[position of A[i] in C] and gB[j] likewise
+ * (bit copies of val_bytes each).  The permutation is not stored: the tile
+ * co-ranks are recomputed from the keys Ak, Bk.  gC: m + n, gA: m, gB: n. */
+cr_status cr_stable_merge_kv_backward(int key_type, int val_bytes,
+                                      const void* Ak, int64_t m, const void* Bk, int64_t n,
+                                      const void* gC, void* gA, void* gB,
+                                      void* ws, size_t ws_bytes, cr_stream stream);
+
+/* The two steps of cr_stable_merge[_kv] as separate calls (the variant of
+ * Section 3 in which the co-ranks of all block boundaries are computed first
+ * and shared, so each is searched once per call instead of once per block
+ * end): cr_merge_partition writes the tile table of a merge of A[m], B[n]
+ * into ws; cr_merge_tiles / cr_merge_tiles_backward then merge (or route
+ * gradients) tile by tile from that table.  The table depends only on the
+ * keys, m, n, key_type and val_bytes, so one partition can serve a forward
+ * and a backward call.  The caller must pass the same A, B, m, n, key_type
+ * and val_bytes to both steps and keep ws untouched in between; the tile
+ * kernels check every record against the array bounds (CR_EINTERNAL via
+ * cr_workspace_status) but cannot detect a table made for other keys. */
+cr_status cr_merge_partition(int key_type, int val_bytes, const void* A, int64_t m,
+                             const void* B, int64_t n, void* ws, size_t ws_bytes,
+                             cr_stream stream);
+
+cr_status cr_merge_tiles(int key_type, int val_bytes, const void* Ak, const void* Av, int64_t m,
+                         const void* Bk, const void* Bv, int64_t n, void* Ck, void* Cv,
+                         uint32_t* C_tag, void* ws, size_t ws_bytes, cr_stream stream);
+
+cr_status cr_merge_tiles_backward(int key_type, int val_bytes, const void* Ak, int64_t m,
+                                  const void* Bk, int64_t n, const void* gC, void* gA, void* gB,
+                                  void* ws, size_t ws_bytes, cr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Batched (segmented) merge: nseg independent merges in one persistent launch.
+ * Segment s merges Ak[a_off[s], a_off[s+1]) with Bk[b_off[s], b_off[s+1])
+ * into Ck[a_off[s] + b_off[s], a_off[s+1] + b_off[s+1]).
+ * d_a_off, d_b_off: device int64 tables of nseg + 1 entries, a_off[0] ==
+ * b_off[0] == 0, non-decreasing, a_off[nseg] <= a_total, b_off[nseg] <=
+ * b_total (checked on the device: CR_EBADSEG via cr_workspace_status, and the
+ * call then writes nothing).  a_total / b_total: lengths of Ak / Bk.
+ * val_bytes 0 means keys only (Av, Bv, Cv ignored).
+ * ------------------------------------------------------------------------ */
+cr_status cr_batched_workspace_size(int key_type, int val_bytes, int64_t nseg,
+                                    int64_t a_total, int64_t b_total, size_t* bytes);
+
+cr_status cr_batched_merge_kv(int key_type, int val_bytes, int64_t nseg,
+                              const int64_t* d_a_off, const int64_t* d_b_off,
+                              const void* Ak, const void* Av, int64_t a_total,
+                              const void* Bk, const void* Bv, int64_t b_total,
+                              void* Ck, void* Cv, void* ws, size_t ws_bytes,
+                              cr_stream stream);
+
+/* Backward of cr_batched_merge_kv with respect to the payloads (val_bytes 4
+ * or 8): gA[a_off[s] + i] = gC[position of that element in segment s], ... */
+cr_status cr_batched_merge_kv_backward(int key_type, int val_bytes, int64_t nseg,
+                                       const int64_t* d_a_off, const int64_t* d_b_off,
+                                       const void* Ak, int64_t a_total,
+                                       const void* Bk, int64_t b_total,
+                                       const void* gC, void* gA, void* gB,
+                                       void* ws, size_t ws_bytes, cr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Merge pass: one pass of a bottom-up stable merge sort.  X[0, N) holds
+ * sorted runs of `width` elements; pair q merges X[2q*width, (2q+1)*width)
+ * with X[(2q+1)*width, (2q+2)*width) (both cut at N) into the same range of
+ * Y.  val_bytes 0, 4 or 8 (Xv/Yv ignored for 0).
+ * ------------------------------------------------------------------------ */
+cr_status cr_merge_pass_workspace_size(int key_type, int val_bytes, int64_t N, int64_t width,
+                                       size_t* bytes);
+
+cr_status cr_merge_pass(int key_type, int val_bytes, const void* X, const void* Xv, int64_t N,
+                        int64_t width, void* Y, void* Yv, void* ws, size_t ws_bytes,
+                        cr_stream stream);
+
+/* Backward of cr_merge_pass for the payloads: X are the pass's INPUT keys,
+ * gY (N payload gradients) -> gX (N). */
+cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int64_t N,
+                                 int64_t width, const void* gY, void* gX,
+                                 void* ws, size_t ws_bytes, cr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Device-side status of the last call that used workspace `ws` on `stream`.
+ * Synchronises `stream`, reads the status word and returns CR_OK,
+ * CR_ETIMEOUT, CR_EINTERNAL or CR_EBADSEG (or CR_ECUDA if the read failed).
+ * ------------------------------------------------------------------------ */
+cr_status cr_workspace_status(const void* ws, cr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORANK_H */

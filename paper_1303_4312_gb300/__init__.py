@@ -1,1 +1,27 @@
-"""placeholder"""
+"""GB300 (sm_103a) co-rank and perfectly load-balanced stable merge.
+
+Implements Siebert & Traeff, "Perfectly load-balanced, optimal, stable,
+parallel merge": Algorithm 1 (co_rank) and Algorithm 2 (parallel stable
+merge with equal output blocks), as CUDA kernels behind the C ABI declared in
+``include/corank.h`` (``lib/libcorank.so``).
+
+Importing this package does not load the library; the first call does, and
+fails loudly if it has not been built.  ``workloads`` (seeded synthetic
+inputs) needs neither the library nor a GPU.
+"""
+from importlib import import_module
+
+__all__ = [
+    "co_rank", "co_rank_many", "merge", "merge_kv", "merge_kv_backward", "MergeKV",
+    "merge_kv_autograd", "batched_merge_kv", "batched_merge_kv_backward", "merge_pass",
+    "merge_pass_backward", "workspace_status", "tile_size", "CorankError", "merge_sort",
+    "MergeSortPlan",
+]
+
+
+def __getattr__(name):
+    if name == "CorankError":
+        return import_module("._lib", __name__).CorankError
+    if name in __all__:
+        return getattr(import_module(".api", __name__), name)
+    raise AttributeError(name)

@@ -1,0 +1,436 @@
+"""PyTorch-facing API over libcorank.so.
+
+PyTorch supplies device memory, the current stream and autograd; every
+co-rank and merge step runs in the library's CUDA kernels.  Tensors must be
+contiguous CUDA tensors; base pointers must be 16-byte aligned (fresh
+allocations are; offset views may not be).
+
+Key types: int32 -> "i32", int64 -> "i64", uint32 -> "u32", uint64 -> "u64".
+Unsigned keys can also travel in signed containers of the same width when
+``key_type="u32"`` / ``"u64"`` is passed explicitly.  Payloads and gradients
+are any 4- or 8-byte dtype; their bits are copied, never computed on.
+
+Notation: the paper's (rank i; co-ranks j, k) is this API's (k; i, j).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+_DTYPE_KEY = {torch.int32: "i32", torch.int64: "i64"}
+for _name, _kt in (("uint32", "u32"), ("uint64", "u64")):
+    if hasattr(torch, _name):
+        _DTYPE_KEY[getattr(torch, _name)] = _kt
+
+
+def _key_code(t: torch.Tensor, key_type: str | None) -> int:
+    if key_type is None:
+        if t.dtype not in _DTYPE_KEY:
+            raise TypeError(f"key dtype {t.dtype} is not int32/int64/uint32/uint64")
+        key_type = _DTYPE_KEY[t.dtype]
+    if key_type not in _lib.KEY_TYPES:
+        raise ValueError(f"key_type must be one of {sorted(_lib.KEY_TYPES)}")
+    if t.element_size() != (4 if key_type in ("i32", "u32") else 8):
+        raise TypeError(f"{key_type} keys need {4 if key_type[1:] == '32' else 8}-byte elements")
+    return _lib.KEY_TYPES[key_type]
+
+
+def _dev(*ts: torch.Tensor) -> torch.device:
+    dev = None
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensors must be CUDA tensors")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError("tensors are on different devices")
+    return dev
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(dev) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _ws(nbytes: int, dev) -> torch.Tensor:
+    # 256-byte granularity keeps the allocation 16-byte aligned.
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+
+def _size(fn, *args) -> int:
+    out = ctypes.c_size_t()
+    _lib.check(fn(*args, ctypes.byref(out)))
+    return out.value
+
+
+def tile_size(key_type: str, val_bytes: int = 0) -> int:
+    """Output elements per tile used for this key type and payload width."""
+    return int(_lib.load().cr_tile_size(_lib.KEY_TYPES[key_type], int(val_bytes)))
+
+
+# ---------------------------------------------------------------------------
+# co_rank (Algorithm 1)
+# ---------------------------------------------------------------------------
+def co_rank(A: torch.Tensor, B: torch.Tensor, k: int, key_type: str | None = None):
+    """(i, j) with i + j == k: the first k outputs of the stable merge are
+    A[:i] merged with B[:j] (Lemma 1).  Synchronises the current stream."""
+    lib = _lib.load()
+    dev = _dev(A, B)
+    kt = _key_code(A, key_type)
+    if B.dtype != A.dtype:
+        raise TypeError("A and B dtypes differ")
+    out = torch.empty(2, dtype=torch.int64, device=dev)
+    _lib.check(lib.cr_co_rank(kt, _ptr(A), A.numel(), _ptr(B), B.numel(), int(k), _ptr(out),
+                              _stream(dev)))
+    i, j = out.tolist()
+    return i, j
+
+
+def co_rank_many(A: torch.Tensor, B: torch.Tensor, ks: torch.Tensor, key_type: str | None = None):
+    """Co-ranks of every rank in ks (int64, device). Returns (i, j) tensors;
+    -1 for ranks outside [0, m+n]."""
+    lib = _lib.load()
+    ks = ks.to(torch.int64).contiguous()
+    dev = _dev(A, B, ks)
+    kt = _key_code(A, key_type)
+    oi = torch.empty_like(ks)
+    oj = torch.empty_like(ks)
+    _lib.check(lib.cr_co_rank_many(kt, _ptr(A), A.numel(), _ptr(B), B.numel(), _ptr(ks),
+                                   ks.numel(), _ptr(oi), _ptr(oj), _stream(dev)))
+    return oi, oj
+
+
+# ---------------------------------------------------------------------------
+# stable merge (Algorithm 2, equal tiles)
+# ---------------------------------------------------------------------------
+def merge_workspace_bytes(key_type: str, val_bytes: int, m: int, n: int) -> int:
+    lib = _lib.load()
+    return _size(lib.cr_merge_workspace_size, _lib.KEY_TYPES[key_type], int(val_bytes), int(m),
+                 int(n))
+
+
+def merge(A: torch.Tensor, B: torch.Tensor, key_type: str | None = None, tag: bool = False,
+          out: torch.Tensor | None = None, out_tag: torch.Tensor | None = None,
+          ws: torch.Tensor | None = None):
+    """Stable merge of ascending A and B (ties: A first).
+
+    With ``tag=True`` also returns the uint32 source tags (as int32 bits):
+    i for A[i], m + j for B[j]."""
+    lib = _lib.load()
+    dev = _dev(A, B)
+    kt = _key_code(A, key_type)
+    if B.dtype != A.dtype:
+        raise TypeError("A and B dtypes differ")
+    m, n = A.numel(), B.numel()
+    C = out if out is not None else torch.empty(m + n, dtype=A.dtype, device=dev)
+    T = None
+    if tag:
+        T = out_tag if out_tag is not None else torch.empty(m + n, dtype=torch.int32, device=dev)
+    need = _size(lib.cr_merge_workspace_size, kt, 0, m, n)
+    if ws is None:
+        ws = _ws(need, dev)
+    _lib.check(lib.cr_stable_merge(kt, _ptr(A), m, _ptr(B), n, _ptr(C), _ptr(T), _ptr(ws),
+                                   ws.numel(), _stream(dev)))
+    return (C, T) if tag else C
+
+
+def merge_kv(Ak, Av, Bk, Bv, key_type: str | None = None, tag: bool = False, ws=None):
+    """Key-value stable merge; payload bits follow their keys.
+    Returns (Ck, Cv) or (Ck, Cv, tags)."""
+    lib = _lib.load()
+    dev = _dev(Ak, Av, Bk, Bv)
+    kt = _key_code(Ak, key_type)
+    if Bk.dtype != Ak.dtype or Bv.dtype != Av.dtype:
+        raise TypeError("A and B dtypes differ")
+    vb = Av.element_size()
+    m, n = Ak.numel(), Bk.numel()
+    if Av.numel() != m or Bv.numel() != n:
+        raise ValueError("payload and key lengths differ")
+    Ck = torch.empty(m + n, dtype=Ak.dtype, device=dev)
+    Cv = torch.empty(m + n, dtype=Av.dtype, device=dev)
+    T = torch.empty(m + n, dtype=torch.int32, device=dev) if tag else None
+    need = _size(lib.cr_merge_workspace_size, kt, vb, m, n)
+    if ws is None:
+        ws = _ws(need, dev)
+    _lib.check(lib.cr_stable_merge_kv(kt, vb, _ptr(Ak), _ptr(Av), m, _ptr(Bk), _ptr(Bv), n,
+                                      _ptr(Ck), _ptr(Cv), _ptr(T), _ptr(ws), ws.numel(),
+                                      _stream(dev)))
+    return (Ck, Cv, T) if tag else (Ck, Cv)
+
+
+def merge_kv_backward(Ak, Bk, gC, key_type: str | None = None, ws=None):
+    """Payload gradient of merge_kv: (gA, gB), bit-routed from gC by
+    recomputed co-ranks (no stored permutation)."""
+    lib = _lib.load()
+    gC = gC.contiguous()
+    dev = _dev(Ak, Bk, gC)
+    kt = _key_code(Ak, key_type)
+    vb = gC.element_size()
+    m, n = Ak.numel(), Bk.numel()
+    if gC.numel() != m + n:
+        raise ValueError("gradient length differs from m + n")
+    gA = torch.empty(m, dtype=gC.dtype, device=dev)
+    gB = torch.empty(n, dtype=gC.dtype, device=dev)
+    need = _size(lib.cr_merge_workspace_size, kt, vb, m, n)
+    if ws is None:
+        ws = _ws(need, dev)
+    _lib.check(lib.cr_stable_merge_kv_backward(kt, vb, _ptr(Ak), m, _ptr(Bk), n, _ptr(gC),
+                                               _ptr(gA), _ptr(gB), _ptr(ws), ws.numel(),
+                                               _stream(dev)))
+    return gA, gB
+
+
+class MergeKV(torch.autograd.Function):
+    """(Ck, Cv) = stable merge of (Ak, Av) and (Bk, Bv), differentiable in the
+    payloads.  Only the keys are saved; backward recomputes the tile co-ranks
+    and routes grad(Cv) to grad(Av), grad(Bv)."""
+
+    @staticmethod
+    def forward(ctx, Ak, Av, Bk, Bv, key_type=None):
+        Ck, Cv = merge_kv(Ak, Av, Bk, Bv, key_type=key_type)
+        ctx.save_for_backward(Ak, Bk)
+        ctx.key_type = key_type
+        ctx.mark_non_differentiable(Ck)
+        return Ck, Cv
+
+    @staticmethod
+    def backward(ctx, gCk, gCv):
+        Ak, Bk = ctx.saved_tensors
+        if gCv is None:
+            return None, None, None, None, None
+        gA, gB = merge_kv_backward(Ak, Bk, gCv, key_type=ctx.key_type)
+        return None, gA, None, gB, None
+
+
+def merge_kv_autograd(Ak, Av, Bk, Bv, key_type: str | None = None):
+    return MergeKV.apply(Ak, Av, Bk, Bv, key_type)
+
+
+# ---------------------------------------------------------------------------
+# batched (segmented) merge
+# ---------------------------------------------------------------------------
+def _offsets(off, dev) -> torch.Tensor:
+    if not torch.is_tensor(off):
+        off = torch.as_tensor(off, dtype=torch.int64)
+    return off.to(device=dev, dtype=torch.int64).contiguous()
+
+
+def batched_merge_kv(a_off, b_off, Ak, Av, Bk, Bv, key_type: str | None = None, ws=None,
+                     out=None):
+    """nseg merges in one persistent launch: segment s merges
+    Ak[a_off[s]:a_off[s+1]] with Bk[b_off[s]:b_off[s+1]] into
+    Ck[a_off[s]+b_off[s] : a_off[s+1]+b_off[s+1]].  Av/Bv may be None."""
+    lib = _lib.load()
+    dev = _dev(Ak, Av, Bk, Bv)
+    kt = _key_code(Ak, key_type)
+    ao, bo = _offsets(a_off, dev), _offsets(b_off, dev)
+    nseg = ao.numel() - 1
+    vb = Av.element_size() if Av is not None else 0
+    at, bt = Ak.numel(), Bk.numel()
+    if out is None:
+        Ck = torch.empty(at + bt, dtype=Ak.dtype, device=dev)
+        Cv = torch.empty(at + bt, dtype=Av.dtype, device=dev) if vb else None
+    else:
+        Ck, Cv = out
+    need = _size(lib.cr_batched_workspace_size, kt, vb, nseg, at, bt)
+    if ws is None:
+        ws = _ws(need, dev)
+    _lib.check(lib.cr_batched_merge_kv(kt, vb, nseg, _ptr(ao), _ptr(bo), _ptr(Ak), _ptr(Av), at,
+                                       _ptr(Bk), _ptr(Bv), bt, _ptr(Ck), _ptr(Cv), _ptr(ws),
+                                       ws.numel(), _stream(dev)))
+    return Ck, Cv
+
+
+def batched_merge_kv_backward(a_off, b_off, Ak, Bk, gC, key_type: str | None = None, ws=None):
+    lib = _lib.load()
+    gC = gC.contiguous()
+    dev = _dev(Ak, Bk, gC)
+    kt = _key_code(Ak, key_type)
+    ao, bo = _offsets(a_off, dev), _offsets(b_off, dev)
+    nseg = ao.numel() - 1
+    vb = gC.element_size()
+    at, bt = Ak.numel(), Bk.numel()
+    gA = torch.empty(at, dtype=gC.dtype, device=dev)
+    gB = torch.empty(bt, dtype=gC.dtype, device=dev)
+    need = _size(lib.cr_batched_workspace_size, kt, vb, nseg, at, bt)
+    if ws is None:
+        ws = _ws(need, dev)
+    _lib.check(lib.cr_batched_merge_kv_backward(kt, vb, nseg, _ptr(ao), _ptr(bo), _ptr(Ak), at,
+                                                _ptr(Bk), bt, _ptr(gC), _ptr(gA), _ptr(gB),
+                                                _ptr(ws), ws.numel(), _stream(dev)))
+    return gA, gB
+
+
+# ---------------------------------------------------------------------------
+# merge-sort passes
+# ---------------------------------------------------------------------------
+def merge_pass_workspace_bytes(key_type: str, val_bytes: int, N: int, width: int) -> int:
+    lib = _lib.load()
+    return _size(lib.cr_merge_pass_workspace_size, _lib.KEY_TYPES[key_type], int(val_bytes),
+                 int(N), int(width))
+
+
+def merge_pass(X, Xv, width: int, key_type: str | None = None, out=None, ws=None):
+    """One bottom-up pass: runs of `width` in X merged pairwise. Returns (Y, Yv)."""
+    lib = _lib.load()
+    dev = _dev(X, Xv)
+    kt = _key_code(X, key_type)
+    vb = Xv.element_size() if Xv is not None else 0
+    N = X.numel()
+    if out is None:
+        Y = torch.empty_like(X)
+        Yv = torch.empty_like(Xv) if Xv is not None else None
+    else:
+        Y, Yv = out
+    if ws is None:
+        ws = _ws(_size(lib.cr_merge_pass_workspace_size, kt, vb, N, int(width)), dev)
+    _lib.check(lib.cr_merge_pass(kt, vb, _ptr(X), _ptr(Xv), N, int(width), _ptr(Y), _ptr(Yv),
+                                 _ptr(ws), ws.numel(), _stream(dev)))
+    return Y, Yv
+
+
+def merge_pass_backward(X, gY, width: int, key_type: str | None = None, out=None, ws=None):
+    """Payload gradient of merge_pass; X are the pass's input keys."""
+    lib = _lib.load()
+    dev = _dev(X, gY)
+    kt = _key_code(X, key_type)
+    vb = gY.element_size()
+    N = X.numel()
+    gX = out if out is not None else torch.empty_like(gY)
+    if ws is None:
+        ws = _ws(_size(lib.cr_merge_pass_workspace_size, kt, vb, N, int(width)), dev)
+    _lib.check(lib.cr_merge_pass_backward(kt, vb, _ptr(X), N, int(width), _ptr(gY), _ptr(gX),
+                                          _ptr(ws), ws.numel(), _stream(dev)))
+    return gX
+
+
+def workspace_status(ws: torch.Tensor) -> None:
+    """Synchronise the current stream and raise if the last call that used
+    `ws` recorded a device-side error."""
+    lib = _lib.load()
+    _lib.check(lib.cr_workspace_status(_ptr(ws), _stream(ws.device)))
+
+
+# ---------------------------------------------------------------------------
+# bottom-up stable merge sort: a chain of merge passes, optionally replayed
+# from CUDA graphs
+# ---------------------------------------------------------------------------
+class MergeSortPlan:
+    """Buffers and (optionally) CUDA graphs for sorting N keys with payloads
+    whose runs of `run` elements are already sorted.
+
+    Pass p merges runs of width run * 2^p.  The input keys of every pass are
+    kept (they are what the backward pass re-co-ranks), so keys need
+    (passes + 1) * N slots; payloads and gradients ping-pong between two
+    buffers.  Forward and backward are each captured once into a CUDA graph
+    (``graph=True``) and replayed.
+    """
+
+    def __init__(self, N: int, run: int, key_dtype, val_dtype, device="cuda",
+                 key_type: str | None = None, graph: bool = True):
+        self.N, self.run = int(N), int(run)
+        self.device = torch.device(device)
+        self.key_type = key_type
+        self.widths = []
+        w = self.run
+        while w < self.N:
+            self.widths.append(w)
+            w *= 2
+        P = len(self.widths)
+        self.keys = [torch.empty(self.N, dtype=key_dtype, device=self.device) for _ in range(P + 1)]
+        self.vals = [torch.empty(self.N, dtype=val_dtype, device=self.device) for _ in range(2)]
+        self.grads = [torch.empty(self.N, dtype=val_dtype, device=self.device) for _ in range(2)]
+        kt = key_type or _DTYPE_KEY[key_dtype]
+        vb = torch.empty(0, dtype=val_dtype).element_size()
+        need = max([merge_pass_workspace_bytes(kt, vb, self.N, w) for w in self.widths] + [256])
+        self.ws = _ws(need, self.device)
+        self.use_graph = graph
+        self._gf = None
+        self._gb = None
+
+    @property
+    def passes(self) -> int:
+        return len(self.widths)
+
+    def _forward_body(self):
+        for p, w in enumerate(self.widths):
+            merge_pass(self.keys[p], self.vals[p & 1], w, key_type=self.key_type,
+                       out=(self.keys[p + 1], self.vals[(p + 1) & 1]), ws=self.ws)
+
+    def _backward_body(self):
+        for p in reversed(range(self.passes)):
+            src = self.grads[(p + 1) & 1]
+            merge_pass_backward(self.keys[p], src, self.widths[p], key_type=self.key_type,
+                                out=self.grads[p & 1], ws=self.ws)
+
+    def _capture(self, body):
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            body()                       # warm-up outside the capture
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            body()
+        return g
+
+    def forward(self, X: torch.Tensor, Xv: torch.Tensor):
+        """Sort; returns views of the plan's output buffers (keys, payloads)."""
+        self.keys[0].copy_(X)
+        self.vals[0].copy_(Xv)
+        if self.use_graph and self.passes:
+            if self._gf is None:
+                self._gf = self._capture(self._forward_body)
+                self.keys[0].copy_(X)
+                self.vals[0].copy_(Xv)
+            self._gf.replay()
+        else:
+            self._forward_body()
+        return self.keys[self.passes], self.vals[self.passes & 1]
+
+    def backward(self, gY: torch.Tensor) -> torch.Tensor:
+        """Payload gradient of the sort: gX[perm[t]] = gY[t]."""
+        self.grads[self.passes & 1].copy_(gY)
+        if self.use_graph and self.passes:
+            if self._gb is None:
+                self._gb = self._capture(self._backward_body)
+                self.grads[self.passes & 1].copy_(gY)
+            self._gb.replay()
+        else:
+            self._backward_body()
+        return self.grads[0]
+
+
+class _MergeSortFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, Xv, plan):
+        Y, Yv = plan.forward(X, Xv)
+        ctx.plan = plan
+        ctx.mark_non_differentiable(Y)
+        return Y.clone(), Yv.clone()
+
+    @staticmethod
+    def backward(ctx, gY, gYv):
+        if gYv is None:
+            return None, None, None
+        return None, ctx.plan.backward(gYv.contiguous()).clone(), None
+
+
+def merge_sort(X: torch.Tensor, Xv: torch.Tensor, run: int = 1024, key_type: str | None = None,
+               graph: bool = True, plan: MergeSortPlan | None = None):
+    """Stable merge sort of X (runs of `run` already sorted) carrying payloads
+    Xv; differentiable in Xv.  Returns (keys, payloads)."""
+    _dev(X, Xv)
+    if plan is None:
+        plan = MergeSortPlan(X.numel(), run, X.dtype, Xv.dtype, X.device, key_type, graph)
+    return _MergeSortFn.apply(X, Xv, plan)

@@ -1,0 +1,572 @@
+// cr_abi.cu -- the extern "C" entry points declared in include/corank.h:
+// argument validation, workspace sizing, and stream-ordered launches of the
+// partition (co-rank) and tile-merge kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/corank.h"
+#include "cr_launch.cuh"
+
+using cr::KeyOps;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cr_status fail(cr_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+cr_status ok() {
+    g_last_error.clear();
+    return CR_OK;
+}
+
+cr_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(CR_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+int key_bytes(int key_type) {
+    switch (key_type) {
+        case CR_KEY_I32:
+        case CR_KEY_U32: return 4;
+        case CR_KEY_I64:
+        case CR_KEY_U64: return 8;
+        default: return 0;
+    }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// A device array argument: `count` elements of `elem` bytes.
+struct Arr {
+    const void* p;
+    int64_t count;
+    int64_t elem;
+    const char* name;
+    int64_t bytes() const { return count * elem; }
+};
+
+cr_status check_arr(const Arr& a) {
+    if (a.count < 0) return fail(CR_EINVAL, "%s: negative length", a.name);
+    if (a.count == 0) return CR_OK;
+    if (a.p == nullptr) return fail(CR_EINVAL, "%s is NULL with %lld elements", a.name,
+                                    static_cast<long long>(a.count));
+    if (!aligned16(a.p)) return fail(CR_EALIGN, "%s is not 16-byte aligned", a.name);
+    return CR_OK;
+}
+
+bool overlap(const Arr& x, const Arr& y) {
+    if (x.count <= 0 || y.count <= 0) return false;
+    const uintptr_t x0 = reinterpret_cast<uintptr_t>(x.p), x1 = x0 + uintptr_t(x.bytes());
+    const uintptr_t y0 = reinterpret_cast<uintptr_t>(y.p), y1 = y0 + uintptr_t(y.bytes());
+    return x0 < y1 && y0 < x1;
+}
+
+cr_status check_no_alias(const Arr* outs, int nout, const Arr* ins, int nin) {
+    for (int o = 0; o < nout; ++o) {
+        for (int i = 0; i < nin; ++i)
+            if (overlap(outs[o], ins[i]))
+                return fail(CR_EALIAS, "output %s overlaps input %s", outs[o].name, ins[i].name);
+        for (int q = o + 1; q < nout; ++q)
+            if (overlap(outs[o], outs[q]))
+                return fail(CR_EALIAS, "outputs %s and %s overlap", outs[o].name, outs[q].name);
+    }
+    return CR_OK;
+}
+
+constexpr size_t kRecBytes = sizeof(cr::TileRec);
+
+size_t single_ws_bytes(int64_t ntiles) {
+    return size_t(cr::kHeaderBytes) + size_t(ntiles) * kRecBytes;
+}
+
+int64_t batched_max_tiles(int64_t tile, int64_t nseg, int64_t a_total, int64_t b_total) {
+    return (a_total + b_total + tile - 1) / tile + nseg;
+}
+
+size_t batched_ws_bytes(int64_t max_tiles, int64_t nseg) {
+    return size_t(cr::kHeaderBytes) + size_t(max_tiles) * kRecBytes +
+           size_t(nseg + 1) * sizeof(int64_t);
+}
+
+cr_status check_ws(const void* ws, size_t have, size_t need) {
+    if (ws == nullptr) return fail(CR_EINVAL, "workspace is NULL");
+    if (!aligned16(ws)) return fail(CR_EALIGN, "workspace is not 16-byte aligned");
+    if (have < need)
+        return fail(CR_ENOSPACE, "workspace has %zu bytes, needs %zu", have, need);
+    return CR_OK;
+}
+
+template <class F>
+cudaError_t by_key(int key_type, F&& f) {
+    switch (key_type) {
+        case CR_KEY_I32: return f(KeyOps<int32_t>{});
+        case CR_KEY_U32: return f(KeyOps<uint32_t>{});
+        case CR_KEY_I64: return f(KeyOps<int64_t>{});
+        case CR_KEY_U64: return f(KeyOps<uint64_t>{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+#define CR_TRY(expr)                       \
+    do {                                   \
+        const cr_status _s = (expr);       \
+        if (_s != CR_OK) return _s;        \
+    } while (0)
+
+cr_status check_key_type(int key_type) {
+    if (key_bytes(key_type) == 0) return fail(CR_EINVAL, "unknown key type %d", key_type);
+    return CR_OK;
+}
+
+cr_status check_vb(int vb, bool allow_zero) {
+    if (vb == 4 || vb == 8 || (allow_zero && vb == 0)) return CR_OK;
+    return fail(CR_EINVAL, "payload width %d not supported (4 or 8%s)", vb,
+                allow_zero ? ", or 0 for keys only" : "");
+}
+
+// Validation shared by every forward single-merge entry point.
+cr_status check_forward(int key_type, int vb, const void* Ak, const void* Av, int64_t m,
+                        const void* Bk, const void* Bv, int64_t n, const void* Ck,
+                        const void* Cv, const uint32_t* tag) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(vb, true));
+    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size (m=%lld, n=%lld)",
+                                    static_cast<long long>(m), static_cast<long long>(n));
+    const int ks = key_bytes(key_type);
+    const int64_t mn = m + n;
+    const Arr ins[4] = {{Ak, m, ks, "A"}, {Bk, n, ks, "B"},
+                        {vb ? Av : nullptr, vb ? m : 0, vb, "A payload"},
+                        {vb ? Bv : nullptr, vb ? n : 0, vb, "B payload"}};
+    const Arr outs[3] = {{Ck, mn, ks, "C"},
+                         {vb ? Cv : nullptr, vb ? mn : 0, vb, "C payload"},
+                         {tag, tag ? mn : 0, 4, "C tag"}};
+    for (const Arr& a : ins) CR_TRY(check_arr(a));
+    for (const Arr& a : outs) CR_TRY(check_arr(a));
+    CR_TRY(check_no_alias(outs, 3, ins, 4));
+    if (tag && mn > (int64_t(1) << 32))
+        return fail(CR_EINVAL, "source tags need m + n <= 2^32");
+    return CR_OK;
+}
+
+cr_status check_backward(int key_type, int vb, const void* Ak, int64_t m, const void* Bk,
+                         int64_t n, const void* gC, const void* gA, const void* gB) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(vb, false));
+    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    const int ks = key_bytes(key_type);
+    const Arr ins[3] = {{Ak, m, ks, "A"}, {Bk, n, ks, "B"}, {gC, m + n, vb, "gC"}};
+    const Arr outs[2] = {{gA, m, vb, "gA"}, {gB, n, vb, "gB"}};
+    for (const Arr& a : ins) CR_TRY(check_arr(a));
+    for (const Arr& a : outs) CR_TRY(check_arr(a));
+    return check_no_alias(outs, 2, ins, 3);
+}
+
+int64_t single_tiles(int key_type, int vb, int64_t m, int64_t n, int64_t* tile_out) {
+    const int64_t tile = cr::tile_for(key_bytes(key_type), vb);
+    if (tile_out) *tile_out = tile;
+    return (m + n + tile - 1) / tile;
+}
+
+// Grid-level co-rank pass of a single merge (writes the tile table).
+cr_status launch_partition(int key_type, int vb, const void* Ak, int64_t m, const void* Bk,
+                           int64_t n, void* ws, size_t ws_bytes, cudaStream_t st) {
+    int64_t tile = 0;
+    const int64_t ntiles = single_tiles(key_type, vb, m, n, &tile);
+    CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
+    cudaError_t e = by_key(key_type, [&](auto ops) {
+        return ops.partition_single(Ak, m, Bk, n, tile, ntiles, ws, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "partition launch");
+    return CR_OK;
+}
+
+cr_status launch_tiles(int key_type, int vb, const void* Ak, const void* Av, int64_t m,
+                       const void* Bk, const void* Bv, int64_t n, void* Ck, void* Cv,
+                       uint32_t* tag, void* ws, size_t ws_bytes, cudaStream_t st) {
+    const int64_t ntiles = single_tiles(key_type, vb, m, n, nullptr);
+    CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
+    cr::MergeArgs a{};
+    a.ak = Ak;
+    a.bk = Bk;
+    a.av = Av;
+    a.bv = Bv;
+    a.ck = Ck;
+    a.cv = Cv;
+    a.ctag = tag;
+    a.a_total = m;
+    a.b_total = n;
+    a.c_total = m + n;
+    a.tag_b = m;
+    a.ws = ws;
+    cudaError_t e = by_key(key_type, [&](auto ops) {
+        return ops.merge_fwd(vb, tag != nullptr, a, ntiles, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "tile merge launch");
+    return CR_OK;
+}
+
+cr_status launch_tiles_backward(int key_type, int vb, const void* Ak, int64_t m, const void* Bk,
+                                int64_t n, const void* gC, void* gA, void* gB, void* ws,
+                                size_t ws_bytes, cudaStream_t st) {
+    const int64_t ntiles = single_tiles(key_type, vb, m, n, nullptr);
+    CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
+    cr::MergeArgs a{};
+    a.ak = Ak;
+    a.bk = Bk;
+    a.gc_in = gC;
+    a.cv = gA;
+    a.cv2 = gB;
+    a.a_total = m;
+    a.b_total = n;
+    a.c_total = m + n;
+    a.ws = ws;
+    cudaError_t e = by_key(key_type, [&](auto ops) { return ops.merge_bwd(vb, a, ntiles, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "tile backward launch");
+    return CR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cr_status_string(int status) {
+    switch (status) {
+        case CR_OK: return "CR_OK";
+        case CR_EINVAL: return "CR_EINVAL";
+        case CR_EALIAS: return "CR_EALIAS";
+        case CR_EALIGN: return "CR_EALIGN";
+        case CR_ENOSPACE: return "CR_ENOSPACE";
+        case CR_ECUDA: return "CR_ECUDA";
+        case CR_ETIMEOUT: return "CR_ETIMEOUT";
+        case CR_EUNSUPPORTED: return "CR_EUNSUPPORTED";
+        case CR_EINTERNAL: return "CR_EINTERNAL";
+        case CR_EBADSEG: return "CR_EBADSEG";
+        default: return "CR_UNKNOWN";
+    }
+}
+
+const char* cr_last_error(void) { return g_last_error.c_str(); }
+
+int cr_abi_version(void) { return 100; }
+
+int64_t cr_tile_size(int key_type, int val_bytes) {
+    const int ks = key_bytes(key_type);
+    if (ks == 0) return 0;
+    return cr::tile_for(ks, val_bytes);
+}
+
+cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int64_t n, int64_t k,
+                     int64_t* d_ij, cr_stream stream) {
+    CR_TRY(check_key_type(key_type));
+    const int ks = key_bytes(key_type);
+    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    if (k < 0 || k > m + n)
+        return fail(CR_EINVAL, "rank %lld outside [0, %lld]", static_cast<long long>(k),
+                    static_cast<long long>(m + n));
+    CR_TRY(check_arr({A, m, ks, "A"}));
+    CR_TRY(check_arr({B, n, ks, "B"}));
+    if (d_ij == nullptr) return fail(CR_EINVAL, "result pointer is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_ij) & 7u) != 0)
+        return fail(CR_EALIGN, "result pointer is not 8-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = by_key(key_type,
+                           [&](auto ops) { return ops.co_rank_one(A, m, B, n, k, d_ij, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "co_rank launch");
+    return ok();
+}
+
+cr_status cr_co_rank_many(int key_type, const void* A, int64_t m, const void* B, int64_t n,
+                          const int64_t* d_k, int64_t cnt, int64_t* d_i, int64_t* d_j,
+                          cr_stream stream) {
+    CR_TRY(check_key_type(key_type));
+    const int ks = key_bytes(key_type);
+    if (m < 0 || n < 0 || cnt < 0) return fail(CR_EINVAL, "negative size");
+    CR_TRY(check_arr({A, m, ks, "A"}));
+    CR_TRY(check_arr({B, n, ks, "B"}));
+    if (cnt == 0) return ok();
+    if (!d_k || !d_i || !d_j) return fail(CR_EINVAL, "rank or result array is NULL");
+    const Arr outs[2] = {{d_i, cnt, 8, "i"}, {d_j, cnt, 8, "j"}};
+    const Arr ins[3] = {{d_k, cnt, 8, "k"}, {A, m, ks, "A"}, {B, n, ks, "B"}};
+    CR_TRY(check_no_alias(outs, 2, ins, 3));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = by_key(key_type, [&](auto ops) {
+        return ops.co_rank_many(A, m, B, n, d_k, cnt, d_i, d_j, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "co_rank_many launch");
+    return ok();
+}
+
+cr_status cr_merge_workspace_size(int key_type, int val_bytes, int64_t m, int64_t n,
+                                  size_t* bytes) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, true));
+    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
+    const int64_t tile = cr::tile_for(key_bytes(key_type), val_bytes);
+    *bytes = single_ws_bytes((m + n + tile - 1) / tile);
+    return ok();
+}
+
+cr_status cr_stable_merge(int key_type, const void* A, int64_t m, const void* B, int64_t n,
+                          void* C, uint32_t* C_tag, void* ws, size_t ws_bytes, cr_stream stream) {
+    return cr_stable_merge_kv(key_type, 0, A, nullptr, m, B, nullptr, n, C, nullptr, C_tag, ws,
+                              ws_bytes, stream);
+}
+
+cr_status cr_stable_merge_kv(int key_type, int val_bytes, const void* Ak, const void* Av,
+                             int64_t m, const void* Bk, const void* Bv, int64_t n, void* Ck,
+                             void* Cv, uint32_t* C_tag, void* ws, size_t ws_bytes,
+                             cr_stream stream) {
+    CR_TRY(check_forward(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag));
+    if (m + n == 0) return ok();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CR_TRY(launch_partition(key_type, val_bytes, Ak, m, Bk, n, ws, ws_bytes, st));
+    CR_TRY(launch_tiles(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag, ws, ws_bytes,
+                        st));
+    return ok();
+}
+
+cr_status cr_stable_merge_kv_backward(int key_type, int val_bytes, const void* Ak, int64_t m,
+                                      const void* Bk, int64_t n, const void* gC, void* gA,
+                                      void* gB, void* ws, size_t ws_bytes, cr_stream stream) {
+    CR_TRY(check_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB));
+    if (m + n == 0) return ok();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CR_TRY(launch_partition(key_type, val_bytes, Ak, m, Bk, n, ws, ws_bytes, st));
+    CR_TRY(launch_tiles_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB, ws, ws_bytes, st));
+    return ok();
+}
+
+cr_status cr_merge_partition(int key_type, int val_bytes, const void* A, int64_t m, const void* B,
+                             int64_t n, void* ws, size_t ws_bytes, cr_stream stream) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, true));
+    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    const int ks = key_bytes(key_type);
+    CR_TRY(check_arr({A, m, ks, "A"}));
+    CR_TRY(check_arr({B, n, ks, "B"}));
+    if (m + n == 0) return ok();
+    CR_TRY(launch_partition(key_type, val_bytes, A, m, B, n, ws, ws_bytes,
+                            static_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+cr_status cr_merge_tiles(int key_type, int val_bytes, const void* Ak, const void* Av, int64_t m,
+                         const void* Bk, const void* Bv, int64_t n, void* Ck, void* Cv,
+                         uint32_t* C_tag, void* ws, size_t ws_bytes, cr_stream stream) {
+    CR_TRY(check_forward(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag));
+    if (m + n == 0) return ok();
+    CR_TRY(launch_tiles(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag, ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+cr_status cr_merge_tiles_backward(int key_type, int val_bytes, const void* Ak, int64_t m,
+                                  const void* Bk, int64_t n, const void* gC, void* gA, void* gB,
+                                  void* ws, size_t ws_bytes, cr_stream stream) {
+    CR_TRY(check_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB));
+    if (m + n == 0) return ok();
+    CR_TRY(launch_tiles_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB, ws, ws_bytes,
+                                 static_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+cr_status cr_batched_workspace_size(int key_type, int val_bytes, int64_t nseg, int64_t a_total,
+                                    int64_t b_total, size_t* bytes) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, true));
+    if (nseg < 0 || a_total < 0 || b_total < 0) return fail(CR_EINVAL, "negative size");
+    if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
+    const int64_t tile = cr::tile_for(key_bytes(key_type), val_bytes);
+    *bytes = batched_ws_bytes(batched_max_tiles(tile, nseg, a_total, b_total), nseg);
+    return ok();
+}
+
+namespace {
+
+cr_status batched_common(bool backward, int key_type, int val_bytes, int64_t nseg,
+                         const int64_t* a_off, const int64_t* b_off, const void* Ak,
+                         const void* Av, int64_t a_total, const void* Bk, const void* Bv,
+                         int64_t b_total, const void* gC, void* Ck, void* Cv, void* gA, void* gB,
+                         void* ws, size_t ws_bytes, cr_stream stream) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, !backward));
+    if (nseg < 0 || a_total < 0 || b_total < 0) return fail(CR_EINVAL, "negative size");
+    const int ks = key_bytes(key_type);
+    const int vb = val_bytes;
+    const int64_t ct = a_total + b_total;
+    if (nseg == 0) return ok();
+    if (!a_off || !b_off) return fail(CR_EINVAL, "segment offset table is NULL");
+    if ((reinterpret_cast<uintptr_t>(a_off) & 7u) || (reinterpret_cast<uintptr_t>(b_off) & 7u))
+        return fail(CR_EALIGN, "segment offset tables must be 8-byte aligned");
+    if (!backward) {
+        const Arr ins[4] = {{Ak, a_total, ks, "A"}, {Bk, b_total, ks, "B"},
+                            {vb ? Av : nullptr, vb ? a_total : 0, vb, "A payload"},
+                            {vb ? Bv : nullptr, vb ? b_total : 0, vb, "B payload"}};
+        const Arr outs[2] = {{Ck, ct, ks, "C"}, {vb ? Cv : nullptr, vb ? ct : 0, vb, "C payload"}};
+        for (const Arr& a : ins) CR_TRY(check_arr(a));
+        for (const Arr& a : outs) CR_TRY(check_arr(a));
+        CR_TRY(check_no_alias(outs, 2, ins, 4));
+    } else {
+        const Arr ins[3] = {{Ak, a_total, ks, "A"}, {Bk, b_total, ks, "B"}, {gC, ct, vb, "gC"}};
+        const Arr outs[2] = {{gA, a_total, vb, "gA"}, {gB, b_total, vb, "gB"}};
+        for (const Arr& a : ins) CR_TRY(check_arr(a));
+        for (const Arr& a : outs) CR_TRY(check_arr(a));
+        CR_TRY(check_no_alias(outs, 2, ins, 3));
+    }
+    const int64_t tile = cr::tile_for(ks, vb);
+    const int64_t max_tiles = batched_max_tiles(tile, nseg, a_total, b_total);
+    CR_TRY(check_ws(ws, ws_bytes, batched_ws_bytes(max_tiles, nseg)));
+    int64_t* prefix = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + cr::kHeaderBytes +
+                                                 size_t(max_tiles) * kRecBytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cr::MergeArgs a{};
+    a.ak = Ak;
+    a.bk = Bk;
+    a.av = Av;
+    a.bv = Bv;
+    a.gc_in = gC;
+    a.ck = Ck;
+    a.cv = backward ? gA : Cv;
+    a.cv2 = gB;
+    a.a_total = a_total;
+    a.b_total = b_total;
+    a.c_total = ct;
+    a.ws = ws;
+    cudaError_t e = by_key(key_type, [&](auto ops) {
+        cudaError_t r = ops.partition_batched(Ak, Bk, a_off, b_off, nseg, a_total, b_total, tile,
+                                              max_tiles, ws, prefix, st);
+        if (r != cudaSuccess) return r;
+        return backward ? ops.merge_bwd(vb, a, max_tiles, st)
+                        : ops.merge_fwd(vb, false, a, max_tiles, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "batched merge launch");
+    return ok();
+}
+
+cr_status pass_common(bool backward, int key_type, int val_bytes, const void* X, const void* Xv,
+                      int64_t N, int64_t width, const void* gY, void* Y, void* Yv, void* gX,
+                      void* ws, size_t ws_bytes, cr_stream stream) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, !backward));
+    if (N < 0) return fail(CR_EINVAL, "negative size");
+    if (width < 1) return fail(CR_EINVAL, "run width must be >= 1");
+    const int ks = key_bytes(key_type);
+    const int vb = val_bytes;
+    if (!backward) {
+        const Arr ins[2] = {{X, N, ks, "X"}, {vb ? Xv : nullptr, vb ? N : 0, vb, "X payload"}};
+        const Arr outs[2] = {{Y, N, ks, "Y"}, {vb ? Yv : nullptr, vb ? N : 0, vb, "Y payload"}};
+        for (const Arr& a : ins) CR_TRY(check_arr(a));
+        for (const Arr& a : outs) CR_TRY(check_arr(a));
+        CR_TRY(check_no_alias(outs, 2, ins, 2));
+    } else {
+        const Arr ins[2] = {{X, N, ks, "X"}, {gY, N, vb, "gY"}};
+        const Arr outs[1] = {{gX, N, vb, "gX"}};
+        for (const Arr& a : ins) CR_TRY(check_arr(a));
+        CR_TRY(check_arr(outs[0]));
+        CR_TRY(check_no_alias(outs, 1, ins, 2));
+    }
+    if (N == 0) return ok();
+    const int64_t tile = cr::tile_for(ks, vb);
+    const int64_t ntiles = cr::pass_tiles(N, width, tile, nullptr, nullptr);
+    CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cr::MergeArgs a{};
+    a.ak = X;
+    a.bk = X;
+    a.av = Xv;
+    a.bv = Xv;
+    a.gc_in = gY;
+    a.ck = Y;
+    a.cv = backward ? gX : Yv;
+    a.cv2 = gX;
+    a.a_total = N;
+    a.b_total = N;
+    a.c_total = N;
+    a.ws = ws;
+    cudaError_t e = by_key(key_type, [&](auto ops) {
+        int64_t nt = 0;
+        cudaError_t r = ops.partition_pass(X, N, width, tile, ws, &nt, st);
+        if (r != cudaSuccess) return r;
+        return backward ? ops.merge_bwd(vb, a, nt, st) : ops.merge_fwd(vb, false, a, nt, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "merge pass launch");
+    return ok();
+}
+
+}  // namespace
+
+cr_status cr_batched_merge_kv(int key_type, int val_bytes, int64_t nseg, const int64_t* d_a_off,
+                              const int64_t* d_b_off, const void* Ak, const void* Av,
+                              int64_t a_total, const void* Bk, const void* Bv, int64_t b_total,
+                              void* Ck, void* Cv, void* ws, size_t ws_bytes, cr_stream stream) {
+    return batched_common(false, key_type, val_bytes, nseg, d_a_off, d_b_off, Ak, Av, a_total,
+                          Bk, Bv, b_total, nullptr, Ck, Cv, nullptr, nullptr, ws, ws_bytes,
+                          stream);
+}
+
+cr_status cr_batched_merge_kv_backward(int key_type, int val_bytes, int64_t nseg,
+                                       const int64_t* d_a_off, const int64_t* d_b_off,
+                                       const void* Ak, int64_t a_total, const void* Bk,
+                                       int64_t b_total, const void* gC, void* gA, void* gB,
+                                       void* ws, size_t ws_bytes, cr_stream stream) {
+    return batched_common(true, key_type, val_bytes, nseg, d_a_off, d_b_off, Ak, nullptr,
+                          a_total, Bk, nullptr, b_total, gC, nullptr, nullptr, gA, gB, ws,
+                          ws_bytes, stream);
+}
+
+cr_status cr_merge_pass_workspace_size(int key_type, int val_bytes, int64_t N, int64_t width,
+                                       size_t* bytes) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, true));
+    if (N < 0 || width < 1) return fail(CR_EINVAL, "bad size or width");
+    if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
+    const int64_t tile = cr::tile_for(key_bytes(key_type), val_bytes);
+    *bytes = single_ws_bytes(cr::pass_tiles(N, width, tile, nullptr, nullptr));
+    return ok();
+}
+
+cr_status cr_merge_pass(int key_type, int val_bytes, const void* X, const void* Xv, int64_t N,
+                        int64_t width, void* Y, void* Yv, void* ws, size_t ws_bytes,
+                        cr_stream stream) {
+    return pass_common(false, key_type, val_bytes, X, Xv, N, width, nullptr, Y, Yv, nullptr, ws,
+                       ws_bytes, stream);
+}
+
+cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int64_t N,
+                                 int64_t width, const void* gY, void* gX, void* ws,
+                                 size_t ws_bytes, cr_stream stream) {
+    return pass_common(true, key_type, val_bytes, X, nullptr, N, width, gY, nullptr, nullptr, gX,
+                       ws, ws_bytes, stream);
+}
+
+cr_status cr_workspace_status(const void* ws, cr_stream stream) {
+    if (ws == nullptr) return fail(CR_EINVAL, "workspace is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    int32_t code = 0;
+    e = cudaMemcpy(&code, ws, sizeof(code), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    switch (code) {
+        case cr::kDevOk: return ok();
+        case cr::kDevTimeout: return fail(CR_ETIMEOUT, "a device-side wait gave up");
+        case cr::kDevInternal: return fail(CR_EINTERNAL, "inconsistent tile record");
+        case cr::kDevBadSeg: return fail(CR_EBADSEG, "invalid segment offset table");
+        default: return fail(CR_EINTERNAL, "unknown device status %d", code);
+    }
+}
+
+}  // extern "C"

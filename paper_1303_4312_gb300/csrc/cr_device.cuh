@@ -1,0 +1,226 @@
+// cr_device.cuh -- device-side building blocks of the co-rank / stable-merge
+// kernels for sm_103a: the tile record, the workspace header, Algorithm 1,
+// and inline-PTX wrappers for mbarriers and bulk (TMA engine) copies.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cr {
+
+// ---------------------------------------------------------------------------
+// Workspace layout (caller-owned device memory, 16-byte aligned):
+//   [0, 256)                 header: status word, tile count
+//   [256, 256 + 32*ntiles)   one TileRec per output tile
+//   [..., + 8*(nseg+1))      batched calls only: tile prefix per segment
+// ---------------------------------------------------------------------------
+constexpr int kHeaderBytes = 256;
+
+struct WsHeader {
+    int32_t status;      // device status (kDev*), 0 = ok
+    int32_t pad0;
+    int64_t ntiles;      // tiles of the current call (written by the partition kernel)
+};
+
+// Device status codes: equal to the public cr_status values they map to.
+constexpr int32_t kDevOk = 0;
+constexpr int32_t kDevTimeout = 6;
+constexpr int32_t kDevInternal = 8;
+constexpr int32_t kDevBadSeg = 9;
+
+// One output tile: it merges A[ga, ga+alen) with B[gb, gb+blen) into
+// C[gc, gc+alen+blen).  alen + blen <= TILE; ga/gb/gc are element indices
+// into the full arrays (segment offsets already applied).
+struct __align__(16) TileRec {
+    int64_t ga, gb, gc;
+    int32_t alen, blen;
+};
+static_assert(sizeof(TileRec) == 32, "TileRec is two 16-byte words");
+
+// Kernel arguments shared by the forward and backward tile-merge kernels.
+struct MergeArgs {
+    const void* ak;      // A keys
+    const void* bk;      // B keys
+    const void* av;      // fwd: A payloads
+    const void* bv;      // fwd: B payloads
+    const void* gc_in;   // bwd: gradient of C
+    void* ck;            // fwd: C keys
+    void* cv;            // fwd: C payloads / bwd: gradient of A
+    void* cv2;           // bwd: gradient of B
+    uint32_t* ctag;      // fwd: source tags (nullable)
+    int64_t a_total;     // length of the A array
+    int64_t b_total;     // length of the B array
+    int64_t c_total;     // length of the C array
+    int64_t tag_b;       // tag of B[0]
+    void* ws;            // workspace: header + tile records
+};
+
+__host__ __device__ inline TileRec* ws_recs(void* ws) {
+    return reinterpret_cast<TileRec*>(static_cast<char*>(ws) + kHeaderBytes);
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 (Section 2): co-ranks of output rank i.
+//
+// Paper notation: rank i, co-ranks j (into A) and k (into B), j + k = i;
+// the C-ABI calls the same triple (k; i, j).  Starting from j = min(i, m),
+// the search keeps j + k = i and lower bounds j_low, k_low, and halves
+// [j_low, j] while the first Lemma-1 condition fails (A[j-1] > B[k]) or
+// [k_low, k] while the second fails (B[k-1] >= A[j]).  The "conditional
+// and" becomes index guards; the four candidate keys of an iteration are
+// loaded together so that each iteration costs one memory round trip.
+// k_low is set to the starting k: the paper proves it is written before it
+// is read (the first move is always on the first condition).
+//
+// The loop is capped at 128 iterations (Proposition 1 bounds it by about
+// log2 min(m, n) + 1 <= 64 for any int64 size) and every load is
+// range-checked, so unsorted input can give a wrong split but never an
+// out-of-range access or an endless loop; the result is clamped to the
+// valid range [max(0, i-n), min(i, m)].
+// ---------------------------------------------------------------------------
+template <class K, class Idx, class GetA, class GetB>
+__device__ __forceinline__ Idx co_rank(Idx i, Idx m, Idx n, GetA getA, GetB getB) {
+    Idx j = i < m ? i : m;
+    Idx k = i - j;
+    Idx j_low = i - n > 0 ? i - n : Idx(0);
+    Idx k_low = k;
+    const Idx j_min = j_low, j_max = j;
+#pragma unroll 1
+    for (int it = 0; it < 128; ++it) {
+        const bool okA1 = j > 0 && j - 1 < m;   // A[j-1] exists
+        const bool okB0 = k >= 0 && k < n;      // B[k]   exists
+        const bool okB1 = k > 0 && k - 1 < n;   // B[k-1] exists
+        const bool okA0 = j >= 0 && j < m;      // A[j]   exists
+        const K a1 = okA1 ? getA(j - 1) : K(0);
+        const K b0 = okB0 ? getB(k) : K(0);
+        const K b1 = okB1 ? getB(k - 1) : K(0);
+        const K a0 = okA0 ? getA(j) : K(0);
+        if (okA1 && okB0 && a1 > b0) {            // first condition violated
+            const Idx d = (j - j_low + 1) >> 1;
+            k_low = k;
+            j -= d;
+            k += d;
+        } else if (okB1 && okA0 && b1 >= a0) {    // second condition violated
+            const Idx d = (k - k_low + 1) >> 1;
+            j_low = j;
+            j += d;
+            k -= d;
+        } else {
+            break;
+        }
+    }
+    j = j < j_min ? j_min : j;
+    j = j > j_max ? j_max : j;
+    return j;
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers (sm_90+ forms, valid on sm_103a).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+// Make mbarrier initialisation visible to the async (bulk-copy) proxy.
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase with the given parity to complete.  Gives up
+// after about `limit_ns` nanoseconds of wall time and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint64_t limit_ns = 2000000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+#pragma unroll 1
+    for (uint32_t spin = 1; spin < (1u << 26); ++spin) {   // hard cap as a backstop
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spin & 255u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+// Bulk copy global -> this CTA's shared memory, completion counted in bytes
+// on `bar`.  dst, src 16-byte aligned; bytes a nonzero multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bulk copy shared -> global (bulk-group completion).  Same alignment rules.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_addr(src)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until at most N committed bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Wait until at most N committed bulk groups are incomplete.
+template <int N>
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Order this thread's generic-proxy shared-memory writes before later
+// async-proxy (bulk copy) reads of the same bytes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Named barrier over `count` threads (a multiple of 32).
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+    atomicCAS(status, 0, code);
+}
+
+}  // namespace cr

@@ -1,0 +1,144 @@
+// cr_keyops_impl.cuh -- definitions of KeyOps<K>; included by exactly one
+// translation unit per key type.
+#pragma once
+
+#include <mutex>
+
+#include "cr_launch.cuh"
+#include "cr_merge.cuh"
+#include "cr_partition.cuh"
+
+namespace cr {
+
+constexpr int kMaxDevices = 64;
+
+// Per-device launch shape of one merge kernel instantiation: CTAs per SM
+// (from the occupancy calculator, after raising the shared-memory limit) and
+// the SM count.  Computed once per device.
+struct LaunchShape {
+    int blocks_per_sm = 0;
+    int sms = 0;
+};
+
+template <class Kern>
+cudaError_t launch_shape(Kern kern, int threads, size_t smem, LaunchShape* cache,
+                         std::once_flag* once, LaunchShape& out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaError_t err = cudaSuccess;
+    std::call_once(once[dev], [&] {
+        LaunchShape s;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (err == cudaSuccess)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.blocks_per_sm, kern, threads,
+                                                                smem);
+        if (err == cudaSuccess)
+            err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (err == cudaSuccess) cache[dev] = s;
+    });
+    if (err != cudaSuccess) return err;
+    out = cache[dev];
+    if (out.sms <= 0 || out.blocks_per_sm <= 0) return cudaErrorInvalidConfiguration;
+    return cudaSuccess;
+}
+
+template <class K, int VB, bool TAG, bool BWD>
+cudaError_t launch_merge(const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
+    constexpr int NT = TileShape<int(sizeof(K)), VB>::NT;
+    constexpr int IPT = TileShape<int(sizeof(K)), VB>::IPT;
+    constexpr int NS = Stages<int(sizeof(K)), VB, BWD>::NS;
+    using L = Layout<K, VB, TAG, NT, IPT, NS, BWD>;
+    auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, NS, BWD>;
+    static LaunchShape cache[kMaxDevices];
+    static std::once_flag once[kMaxDevices];
+    LaunchShape sh;
+    cudaError_t e = launch_shape(kern, NT + 32, L::TOTAL, cache, once, sh);
+    if (e != cudaSuccess) return e;
+    if (max_tiles <= 0) return cudaSuccess;
+    int64_t grid = int64_t(sh.sms) * sh.blocks_per_sm;
+    if (grid > max_tiles) grid = max_tiles;
+    kern<<<unsigned(grid), NT + 32, L::TOTAL, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_fwd(int vb, bool tag, const MergeArgs& a, int64_t max_tiles,
+                                 cudaStream_t st) {
+    switch (vb * 2 + (tag ? 1 : 0)) {
+        case 0: return launch_merge<K, 0, false, false>(a, max_tiles, st);
+        case 1: return launch_merge<K, 0, true, false>(a, max_tiles, st);
+        case 8: return launch_merge<K, 4, false, false>(a, max_tiles, st);
+        case 9: return launch_merge<K, 4, true, false>(a, max_tiles, st);
+        case 16: return launch_merge<K, 8, false, false>(a, max_tiles, st);
+        case 17: return launch_merge<K, 8, true, false>(a, max_tiles, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_bwd(int vb, const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
+    if (vb == 4) return launch_merge<K, 4, false, true>(a, max_tiles, st);
+    if (vb == 8) return launch_merge<K, 8, false, true>(a, max_tiles, st);
+    return cudaErrorInvalidValue;
+}
+
+static inline unsigned blocks_for(int64_t n, int threads) {
+    return unsigned((n + threads - 1) / threads);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::partition_single(const void* A, int64_t m, const void* B, int64_t n,
+                                        int64_t tile, int64_t ntiles, void* ws, cudaStream_t st) {
+    const unsigned g = blocks_for(ntiles > 0 ? ntiles : 1, 256);
+    partition_single_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(A), m,
+                                                   static_cast<const K*>(B), n, tile, ntiles, ws);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t KeyOps<K>::partition_pass(const void* X, int64_t N, int64_t w, int64_t tile,
+                                      void* ws, int64_t* ntiles_out, cudaStream_t st) {
+    int64_t tpp = 1, npairs = 0;
+    const int64_t ntiles = pass_tiles(N, w, tile, &tpp, &npairs);
+    if (ntiles_out) *ntiles_out = ntiles;
+    const unsigned g = blocks_for(ntiles > 0 ? ntiles : 1, 256);
+    partition_pass_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(X), N, w, tile, tpp,
+                                                 npairs, ntiles, ws);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t KeyOps<K>::partition_batched(const void* A, const void* B, const int64_t* a_off,
+                                         const int64_t* b_off, int64_t nseg, int64_t a_total,
+                                         int64_t b_total, int64_t tile, int64_t max_tiles,
+                                         void* ws, int64_t* prefix, cudaStream_t st) {
+    segment_scan_kernel<<<1, 1024, 0, st>>>(a_off, b_off, nseg, a_total, b_total, tile, ws,
+                                            prefix);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || max_tiles <= 0) return e;
+    partition_batched_kernel<K><<<blocks_for(max_tiles, 256), 256, 0, st>>>(
+        static_cast<const K*>(A), static_cast<const K*>(B), a_off, b_off, nseg, tile, prefix, ws);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t KeyOps<K>::co_rank_many(const void* A, int64_t m, const void* B, int64_t n,
+                                    const int64_t* ranks, int64_t cnt, int64_t* oi, int64_t* oj,
+                                    cudaStream_t st) {
+    if (cnt <= 0) return cudaSuccess;
+    co_rank_many_kernel<K><<<blocks_for(cnt, 256), 256, 0, st>>>(
+        static_cast<const K*>(A), m, static_cast<const K*>(B), n, ranks, cnt, oi, oj);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int64_t n, int64_t r,
+                                   int64_t* out, cudaStream_t st) {
+    co_rank_one_kernel<K><<<1, 1, 0, st>>>(static_cast<const K*>(A), m,
+                                           static_cast<const K*>(B), n, r, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cr

@@ -1,0 +1,270 @@
+// cr_partition.cuh -- kernels that place the output tiles: for every tile,
+// the co-ranks of its first and last output rank (Algorithm 1 over the
+// arrays in HBM), written as a TileRec.  These are the "grid-level" co-rank
+// passes; the merge kernel reads the records.
+//
+// Every tile computes both of its ends independently, as each processing
+// element does in Algorithm 2 (no synchronisation between tiles).  The two
+// searches run in lock step so that one round trip to memory serves both.
+#pragma once
+
+#include "cr_device.cuh"
+
+namespace cr {
+
+// Lock-step state of Algorithm 1 (see co_rank in cr_device.cuh for the
+// method; this form advances one iteration per call).
+struct CoRankState {
+    int64_t j, k, j_low, k_low, j_min, j_max;
+    bool done;
+};
+
+__device__ __forceinline__ CoRankState co_rank_begin(int64_t i, int64_t m, int64_t n) {
+    CoRankState s;
+    s.j = i < m ? i : m;
+    s.k = i - s.j;
+    s.j_low = i - n > 0 ? i - n : 0;
+    s.k_low = s.k;
+    s.j_min = s.j_low;
+    s.j_max = s.j;
+    s.done = false;
+    return s;
+}
+
+template <class K>
+__device__ __forceinline__ void co_rank_step(CoRankState& s, const K* A, int64_t m, const K* B,
+                                             int64_t n) {
+    if (s.done) return;
+    const int64_t j = s.j, k = s.k;
+    const bool okA1 = j > 0 && j - 1 < m;
+    const bool okB0 = k >= 0 && k < n;
+    const bool okB1 = k > 0 && k - 1 < n;
+    const bool okA0 = j >= 0 && j < m;
+    const K a1 = okA1 ? A[j - 1] : K(0);
+    const K b0 = okB0 ? B[k] : K(0);
+    const K b1 = okB1 ? B[k - 1] : K(0);
+    const K a0 = okA0 ? A[j] : K(0);
+    if (okA1 && okB0 && a1 > b0) {             // first Lemma condition violated
+        const int64_t d = (j - s.j_low + 1) >> 1;
+        s.k_low = k;
+        s.j = j - d;
+        s.k = k + d;
+    } else if (okB1 && okA0 && b1 >= a0) {     // second Lemma condition violated
+        const int64_t d = (k - s.k_low + 1) >> 1;
+        s.j_low = j;
+        s.j = j + d;
+        s.k = k - d;
+    } else {
+        s.done = true;
+    }
+}
+
+__device__ __forceinline__ int64_t co_rank_end(const CoRankState& s) {
+    int64_t j = s.j < s.j_min ? s.j_min : s.j;
+    return j > s.j_max ? s.j_max : j;
+}
+
+// Co-ranks of ranks r0 and r1 of one merge problem, searched together.
+template <class K>
+__device__ __forceinline__ void co_rank_pair(int64_t r0, int64_t r1, const K* A, int64_t m,
+                                             const K* B, int64_t n, int64_t& j0, int64_t& j1) {
+    CoRankState s0 = co_rank_begin(r0, m, n);
+    CoRankState s1 = co_rank_begin(r1, m, n);
+#pragma unroll 1
+    for (int it = 0; it < 128 && !(s0.done && s1.done); ++it) {
+        co_rank_step(s0, A, m, B, n);
+        co_rank_step(s1, A, m, B, n);
+    }
+    j0 = co_rank_end(s0);
+    j1 = co_rank_end(s1);
+}
+
+__device__ __forceinline__ TileRec make_rec(int64_t a_base, int64_t b_base, int64_t c_base,
+                                            int64_t r0, int64_t r1, int64_t j0, int64_t j1) {
+    TileRec r;
+    r.ga = a_base + j0;
+    r.gb = b_base + (r0 - j0);
+    r.gc = c_base + r0;
+    r.alen = int32_t(j1 - j0);
+    r.blen = int32_t((r1 - j1) - (r0 - j0));
+    return r;
+}
+
+// Single merge: tile t covers output ranks [t*tile, min((t+1)*tile, m+n)).
+template <class K>
+__global__ void partition_single_kernel(const K* A, int64_t m, const K* B, int64_t n, int64_t tile,
+                                        int64_t ntiles, void* ws) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        WsHeader* h = static_cast<WsHeader*>(ws);
+        h->status = kDevOk;
+        h->ntiles = ntiles;
+    }
+    if (t >= ntiles) return;
+    const int64_t r0 = t * tile;
+    const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
+    int64_t j0, j1;
+    co_rank_pair(r0, r1, A, m, B, n, j0, j1);
+    ws_recs(ws)[t] = make_rec(0, 0, 0, r0, r1, j0, j1);
+}
+
+// One bottom-up merge-sort pass over X[0, N): pair q merges the runs
+// X[2qw, 2qw+w) and X[2qw+w, 2qw+2w) (cut at N).  Tiles never straddle pairs;
+// every pair but the last has tpp = ceil(2w / tile) tiles.
+template <class K>
+__global__ void partition_pass_kernel(const K* X, int64_t N, int64_t w, int64_t tile, int64_t tpp,
+                                      int64_t npairs, int64_t ntiles, void* ws) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        WsHeader* h = static_cast<WsHeader*>(ws);
+        h->status = kDevOk;
+        h->ntiles = ntiles;
+    }
+    if (t >= ntiles) return;
+    int64_t q = t / tpp;
+    if (q > npairs - 1) q = npairs - 1;
+    const int64_t a0 = 2 * q * w;
+    const int64_t m = w < N - a0 ? w : N - a0;
+    const int64_t b0 = a0 + m;
+    const int64_t nb = N - b0;
+    const int64_t n = w < nb ? w : nb;
+    const int64_t r0 = (t - q * tpp) * tile;
+    const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
+    int64_t j0, j1;
+    co_rank_pair(r0, r1, X + a0, m, X + b0, n, j0, j1);
+    ws_recs(ws)[t] = make_rec(a0, b0, a0, r0, r1, j0, j1);
+}
+
+// Batched merge, step 1 (one CTA of 1024 threads): validate the segment
+// tables and write prefix[s] = number of tiles of segments 0..s-1 (tiles of
+// segment s: ceil((m_s + n_s) / tile)), prefix[nseg] = total tiles.  On an
+// invalid table the status word becomes kDevBadSeg and the tile count 0.
+static __global__ void __launch_bounds__(1024) segment_scan_kernel(const int64_t* a_off,
+                                                            const int64_t* b_off, int64_t nseg,
+                                                            int64_t a_total, int64_t b_total,
+                                                            int64_t tile, void* ws,
+                                                            int64_t* prefix) {
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t s_carry;
+    __shared__ int s_bad;
+    constexpr int IT = 8;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_carry = 0;
+        s_bad = (a_off[0] != 0 || b_off[0] != 0 || a_off[nseg] > a_total ||
+                 b_off[nseg] > b_total) ? 1 : 0;
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < nseg; base += 1024 * IT) {
+        int64_t cnt[IT];
+        int64_t mine = 0;
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+            const int64_t s = base + int64_t(tid) * IT + e;
+            cnt[e] = 0;
+            if (s < nseg) {
+                const int64_t ms = a_off[s + 1] - a_off[s];
+                const int64_t ns = b_off[s + 1] - b_off[s];
+                if (ms < 0 || ns < 0) s_bad = 1;
+                else cnt[e] = (ms + ns + tile - 1) / tile;
+            }
+            mine += cnt[e];
+        }
+        // block-wide exclusive scan of `mine`
+        int64_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((tid & 31) >= o) incl += v;
+        }
+        if ((tid & 31) == 31) warp_tot[tid >> 5] = incl;
+        __syncthreads();
+        if (tid < 32) {
+            int64_t w = warp_tot[tid];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t v = __shfl_up_sync(0xffffffffu, w, o);
+                if (tid >= o) w += v;
+            }
+            warp_tot[tid] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        int64_t run = s_carry + (incl - mine) + ((tid >> 5) ? warp_tot[(tid >> 5) - 1] : 0);
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+            const int64_t s = base + int64_t(tid) * IT + e;
+            if (s < nseg) prefix[s] = run;
+            run += cnt[e];
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += warp_tot[31];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        prefix[nseg] = s_carry;
+        WsHeader* h = static_cast<WsHeader*>(ws);
+        h->status = s_bad ? kDevBadSeg : kDevOk;
+        h->ntiles = s_bad ? 0 : s_carry;
+    }
+}
+
+// Batched merge, step 2: one thread per tile finds its segment in the tile
+// prefix (binary search) and co-ranks both tile ends inside the segment.
+template <class K>
+__global__ void partition_batched_kernel(const K* A, const K* B, const int64_t* a_off,
+                                         const int64_t* b_off, int64_t nseg, int64_t tile,
+                                         const int64_t* prefix, void* ws) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t ntiles = static_cast<const WsHeader*>(ws)->ntiles;
+    if (t >= ntiles) return;
+    // largest s < nseg with prefix[s] <= t (empty segments are skipped)
+    int64_t lo = 0, hi = nseg;   // invariant: prefix[lo] <= t < prefix[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int64_t s = lo;
+    const int64_t a0 = a_off[s], b0 = b_off[s];
+    const int64_t m = a_off[s + 1] - a0;
+    const int64_t n = b_off[s + 1] - b0;
+    const int64_t r0 = (t - prefix[s]) * tile;
+    const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
+    int64_t j0, j1;
+    co_rank_pair(r0, r1, A + a0, m, B + b0, n, j0, j1);
+    ws_recs(ws)[t] = make_rec(a0, b0, a0 + b0, r0, r1, j0, j1);
+}
+
+// co_rank for a list of ranks (C-ABI names: rank k -> (i, j)).
+template <class K>
+__global__ void co_rank_many_kernel(const K* A, int64_t m, const K* B, int64_t n,
+                                    const int64_t* ranks, int64_t cnt, int64_t* out_i,
+                                    int64_t* out_j) {
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= cnt) return;
+    const int64_t r = ranks[q];
+    if (r < 0 || r > m + n) {
+        out_i[q] = -1;
+        out_j[q] = -1;
+        return;
+    }
+    CoRankState s = co_rank_begin(r, m, n);
+#pragma unroll 1
+    for (int it = 0; it < 128 && !s.done; ++it) co_rank_step(s, A, m, B, n);
+    const int64_t j = co_rank_end(s);
+    out_i[q] = j;
+    out_j[q] = r - j;
+}
+
+// One rank, result as two int64 (i, j) in device memory.
+template <class K>
+__global__ void co_rank_one_kernel(const K* A, int64_t m, const K* B, int64_t n, int64_t r,
+                                   int64_t* out_ij) {
+    CoRankState s = co_rank_begin(r, m, n);
+#pragma unroll 1
+    for (int it = 0; it < 128 && !s.done; ++it) co_rank_step(s, A, m, B, n);
+    const int64_t j = co_rank_end(s);
+    out_ij[0] = j;
+    out_ij[1] = r - j;
+}
+
+}  // namespace cr

@@ -1,0 +1,103 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, every
+symbol declared in include/corank.h is exported, and argument validation
+rejects bad calls before anything is launched."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1303_4312_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "corank.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cr_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1303_4312_gb300 import build
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 17
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+
+
+def test_status_strings(lib):
+    for code, name in _lib.STATUS.items():
+        assert lib.cr_status_string(code).decode() == name
+    assert lib.cr_status_string(99).decode() == "CR_UNKNOWN"
+    assert lib.cr_abi_version() == 100
+
+
+def test_tile_sizes(lib):
+    for kt in range(4):
+        for vb in (0, 4, 8):
+            t = lib.cr_tile_size(kt, vb)
+            assert t > 0 and t % 4 == 0
+    assert lib.cr_tile_size(7, 0) == 0
+    assert lib.cr_tile_size(0, 3) == 0
+
+
+def _err(lib):
+    return lib.cr_last_error().decode()
+
+
+def test_validation_without_gpu(lib):
+    A = ctypes.c_void_p(0x10000)     # never dereferenced: validation fails first
+    # null with nonzero size
+    assert lib.cr_stable_merge(0, None, 5, None, 0, None, None, None, 0, None) == 1
+    assert "NULL" in _err(lib)
+    # bad key type
+    assert lib.cr_stable_merge(9, A, 1, A, 1, A, None, A, 1 << 20, None) == 1
+    # negative size
+    assert lib.cr_stable_merge(0, A, -1, A, 1, A, None, A, 1 << 20, None) == 1
+    # misaligned
+    assert lib.cr_stable_merge(0, ctypes.c_void_p(0x10004), 4, A, 4, ctypes.c_void_p(0x20000),
+                               None, A, 1 << 20, None) == 3
+    # output overlaps input
+    assert lib.cr_stable_merge(0, ctypes.c_void_p(0x10000), 64, ctypes.c_void_p(0x30000), 64,
+                               ctypes.c_void_p(0x10040), None, ctypes.c_void_p(0x50000), 1 << 20,
+                               None) == 2
+    # workspace too small
+    assert lib.cr_stable_merge(0, ctypes.c_void_p(0x10000), 64, ctypes.c_void_p(0x30000), 64,
+                               ctypes.c_void_p(0x40000), None, ctypes.c_void_p(0x50000), 16,
+                               None) == 4
+    # payload width
+    assert lib.cr_stable_merge_kv(0, 3, A, A, 1, A, A, 1, A, A, None, A, 1 << 20, None) == 1
+    # rank out of range
+    assert lib.cr_co_rank(0, A, 4, A, 4, 9, A, None) == 1
+    # tags need m + n <= 2^32
+    big = 1 << 31
+    assert lib.cr_stable_merge(0, ctypes.c_void_p(0x1_0000_0000), big,
+                               ctypes.c_void_p(0x4_0000_0000), big + 1,
+                               ctypes.c_void_p(0x8_0000_0000), ctypes.c_void_p(0x10_0000_0000),
+                               ctypes.c_void_p(0x20_0000_0000), 1 << 40, None) == 1
+    assert "2^32" in _err(lib)
+    # merge pass width
+    assert lib.cr_merge_pass(0, 0, A, None, 10, 0, A, None, A, 1 << 20, None) == 1
+    # nothing to do is fine
+    assert lib.cr_stable_merge(0, None, 0, None, 0, None, None, None, 0, None) == 0
+
+
+def test_workspace_sizes(lib):
+    out = ctypes.c_size_t()
+    t = lib.cr_tile_size(0, 0)
+    assert lib.cr_merge_workspace_size(0, 0, 5 * t, 3 * t + 1, ctypes.byref(out)) == 0
+    assert out.value == 256 + 32 * 9
+    assert lib.cr_batched_workspace_size(0, 4, 10, 1000, 2000, ctypes.byref(out)) == 0
+    t4 = lib.cr_tile_size(0, 4)
+    assert out.value == 256 + 32 * ((3000 + t4 - 1) // t4 + 10) + 8 * 11
+    assert lib.cr_merge_pass_workspace_size(3, 4, 1 << 20, 1024, ctypes.byref(out)) == 0
+    t8 = lib.cr_tile_size(3, 4)
+    assert out.value == 256 + 32 * ((1 << 20) // 2048) * ((2048 + t8 - 1) // t8)

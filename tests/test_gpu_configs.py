@@ -1,0 +1,128 @@
+"""GPU parity at the full workload sizes, in the launch configuration the
+benchmark times: every output element compared with the CPU oracle (keys,
+payloads, tags and gradients bit for bit).
+
+Workloads (seeded; device-generated with torch, then copied to the host for
+the oracle):
+  single_i32_tag   m=2^20, n=3*2^19 int32 in [0, 2^16) + uint32 source tags
+  large_i32        m=n=2^28 int32 over the full range
+  skewed_u64       m=2^20, n=2^29 uint64 over the full range
+  dup16_i32        m=n=2^28 int32 from 16 distinct values
+  kv_u32_f32       m=n=2^27 uint32 keys in [0, 2^20), float32 payloads, + backward
+  batched_i32_f32  8192 log-uniform segment pairs (~3.4e8 elements), + backward
+  sort_u64_f32     2^27 uint64 keys (2^20 distinct) from runs of 1024, + backward
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1303_4312_gb300 as cr
+from paper_1303_4312_gb300 import workloads as W
+from gpu_util import host, same_bits
+
+pytestmark = pytest.mark.gpu
+
+
+def _free():
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def test_single_i32_tag_full():
+    A, B = W.single_i32_tag(seed=1)
+    C, T = cr.merge(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), tag=True)
+    torch.cuda.synchronize()
+    want, src = oracle.merge(A, B)
+    assert np.array_equal(C.cpu().numpy(), want)
+    assert np.array_equal(host(T, np.uint32).astype(np.int64), src)
+    # stability witness: among equal keys, tags strictly increase
+    tags = host(T, np.uint32).astype(np.int64)
+    eq = want[1:] == want[:-1]
+    assert np.all(tags[1:][eq] > tags[:-1][eq])
+
+
+@pytest.mark.parametrize("name", ["large_i32", "skewed_u64", "dup16_i32"])
+def test_large_single_merge_full(name):
+    gen = {"large_i32": W.t_large_i32, "skewed_u64": W.t_skewed_u64,
+           "dup16_i32": W.t_dup16_i32}[name]
+    A, B = gen()
+    kt = "u64" if name == "skewed_u64" else "i32"
+    hdt = np.uint64 if kt == "u64" else np.int32
+    C = cr.merge(A, B, key_type=kt)
+    torch.cuda.synchronize()
+    a, b = host(A, hdt), host(B, hdt)
+    del A, B
+    c = host(C, hdt)
+    del C
+    _free()
+    want, _ = oracle.merge(a, b)
+    assert np.array_equal(c, want)
+
+
+def test_kv_u32_f32_full_forward_backward():
+    Ak, Av, Bk, Bv = W.t_kv_u32_f32()
+    Ck, Cv = cr.merge_kv(Ak, Av, Bk, Bv, key_type="u32")
+    g = torch.Generator(device="cuda").manual_seed(55)
+    gC = torch.randn(Ck.numel(), generator=g, device="cuda")
+    gA, gB = cr.merge_kv_backward(Ak, Bk, gC, key_type="u32")
+    torch.cuda.synchronize()
+    a, av, b, bv = host(Ak, np.uint32), host(Av, np.float32), host(Bk, np.uint32), host(Bv, np.float32)
+    wk, wv, _ = oracle.merge_kv(a, av, b, bv)
+    assert np.array_equal(host(Ck, np.uint32), wk)
+    assert same_bits(host(Cv, np.float32), wv)
+    del wk, wv
+    ga, gb = oracle.merge_grad(a, b, host(gC, np.float32))
+    assert same_bits(host(gA, np.float32), ga)
+    assert same_bits(host(gB, np.float32), gb)
+
+
+def test_kv_autograd_small():
+    """torch.autograd.Function: backward routes grad(Cv) by recomputed co-ranks."""
+    Ak, Av, Bk, Bv = W.t_kv_u32_f32(shift=10)
+    Av.requires_grad_(True)
+    Bv.requires_grad_(True)
+    Ck, Cv = cr.MergeKV.apply(Ak, Av, Bk, Bv, "u32")
+    w = torch.randn(Cv.numel(), device="cuda")
+    (Cv * w).sum().backward()
+    a, b = host(Ak, np.uint32), host(Bk, np.uint32)
+    ga, gb = oracle.merge_grad(a, b, host(w, np.float32))
+    assert same_bits(host(Av.grad, np.float32), ga)
+    assert same_bits(host(Bv.grad, np.float32), gb)
+
+
+def test_batched_full_forward_backward():
+    a_off, b_off, A, Av, B, Bv = W.t_batched_i32_f32()
+    Ck, Cv = cr.batched_merge_kv(a_off, b_off, A, Av, B, Bv)
+    gC = torch.randn(Ck.numel(), generator=torch.Generator(device="cuda").manual_seed(56),
+                     device="cuda")
+    gA, gB = cr.batched_merge_kv_backward(a_off, b_off, A, B, gC)
+    torch.cuda.synchronize()
+    a, av, b, bv = host(A, np.int32), host(Av, np.float32), host(B, np.int32), host(Bv, np.float32)
+    wk, wv = oracle.batched_merge_kv(a_off, b_off, a, av, b, bv)
+    assert np.array_equal(host(Ck, np.int32), wk)
+    assert same_bits(host(Cv, np.float32), wv)
+    del wk, wv
+    ga, gb = oracle.batched_merge_grad(a_off, b_off, a, b, host(gC, np.float32))
+    assert same_bits(host(gA, np.float32), ga)
+    assert same_bits(host(gB, np.float32), gb)
+
+
+def test_merge_sort_full_graph_forward_backward():
+    X, Xv = W.t_sort_u64_f32()
+    Xv.requires_grad_(True)
+    Y, Yv = cr.merge_sort(X, Xv, run=1024, key_type="u64", graph=True)
+    gY = torch.randn(Yv.numel(), generator=torch.Generator(device="cuda").manual_seed(57),
+                     device="cuda")
+    Yv.backward(gY)
+    torch.cuda.synchronize()
+    x, xv = host(X, np.uint64), host(Xv.detach(), np.float32)
+    o = np.argsort(x, kind="stable")          # independent of the oracle and of the GPU path
+    assert np.array_equal(host(Y, np.uint64), x[o])
+    assert same_bits(host(Yv.detach(), np.float32), xv[o])
+    want = np.empty_like(xv)
+    want[o] = host(gY, np.float32)
+    assert same_bits(host(Xv.grad, np.float32), want)
+    # and the oracle's own merge chain agrees
+    wy, wyv, perm = oracle.merge_sort(x, xv, 1024)
+    assert np.array_equal(perm, o)

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element and bit for bit, on seeded inputs that span several tiles
+with ragged tails, heavy ties, signed/unsigned orders and empty inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1303_4312_gb300 as cr
+from gpu_util import dev, host, key_type, same_bits, sorted_keys
+
+pytestmark = pytest.mark.gpu
+
+KEY_DTYPES = [np.int32, np.uint32, np.int64, np.uint64]
+
+
+def sizes_for(dt, vb=0):
+    t = cr.tile_size(key_type(np.empty(0, dt)), vb)
+    return [(0, 0), (1, 0), (0, 1), (1, 1), (3, 5), (17, 0), (0, 29), (t - 1, 1), (t, t),
+            (2 * t + 3, t - 5), (5 * t + 11, 7), (7, 4 * t + 9), (1000, 3 * t + 777)]
+
+
+@pytest.mark.parametrize("dt", KEY_DTYPES)
+def test_merge_keys_and_tags(dt):
+    rng = np.random.default_rng(100)
+    for m, n in sizes_for(dt):
+        for spread in (None, 3, 1000):
+            A = sorted_keys(rng, m, dt, spread)
+            B = sorted_keys(rng, n, dt, spread)
+            C, T = cr.merge(dev(A), dev(B), key_type=key_type(A), tag=True)
+            torch.cuda.synchronize()
+            want, src = oracle.merge(A, B)
+            assert same_bits(host(C, dt), want), (m, n, spread)
+            assert np.array_equal(host(T, np.uint32).astype(np.int64), src), (m, n, spread)
+
+
+@pytest.mark.parametrize("dt", KEY_DTYPES)
+def test_special_orders(dt):
+    """All keys equal; A entirely below B; B entirely below A."""
+    t = cr.tile_size(key_type(np.empty(0, dt)))
+    m, n = 3 * t + 5, 2 * t + 9
+    info = np.iinfo(dt)
+    cases = [
+        (np.full(m, 7, dt), np.full(n, 7, dt)),
+        (np.arange(m).astype(dt), (np.arange(n) + m).astype(dt)),
+        ((np.arange(m) + n).astype(dt), np.arange(n).astype(dt)),
+        (np.full(m, info.max, dt), np.full(n, info.min, dt)),
+    ]
+    for A, B in cases:
+        C, T = cr.merge(dev(A), dev(B), key_type=key_type(A), tag=True)
+        torch.cuda.synchronize()
+        want, src = oracle.merge(A, B)
+        assert same_bits(host(C, dt), want)
+        assert np.array_equal(host(T, np.uint32).astype(np.int64), src)
+
+
+@pytest.mark.parametrize("dt", KEY_DTYPES)
+@pytest.mark.parametrize("vdt", [np.float32, np.float64])
+def test_merge_kv_and_backward(dt, vdt):
+    rng = np.random.default_rng(101)
+    vb = np.dtype(vdt).itemsize
+    for m, n in sizes_for(dt, vb):
+        A = sorted_keys(rng, m, dt, 50)
+        B = sorted_keys(rng, n, dt, 50)
+        Av = rng.standard_normal(m).astype(vdt)
+        Bv = rng.standard_normal(n).astype(vdt)
+        kt = key_type(A)
+        Ck, Cv, T = cr.merge_kv(dev(A), dev(Av), dev(B), dev(Bv), key_type=kt, tag=True)
+        gC = rng.standard_normal(m + n).astype(vdt)
+        gA, gB = cr.merge_kv_backward(dev(A), dev(B), dev(gC), key_type=kt)
+        torch.cuda.synchronize()
+        wk, wv, src = oracle.merge_kv(A, Av, B, Bv)
+        ga, gb = oracle.merge_grad(A, B, gC)
+        assert same_bits(host(Ck, dt), wk), (m, n)
+        assert same_bits(host(Cv, vdt), wv), (m, n)
+        assert np.array_equal(host(T, np.uint32).astype(np.int64), src)
+        assert same_bits(host(gA, vdt), ga), (m, n)
+        assert same_bits(host(gB, vdt), gb), (m, n)
+
+
+def test_payload_bits_nan_and_signed_zero():
+    A = np.array([1, 2, 2, 5] * 1000, np.uint32)
+    A.sort()
+    B = np.array([0, 2, 9] * 1000, np.uint32)
+    B.sort()
+    rng = np.random.default_rng(7)
+    Av = rng.integers(0, 2**32, len(A), dtype=np.uint32)
+    Av[::3] = 0x7FC00001   # NaN payload
+    Av[1::3] = 0x80000000  # -0.0
+    Bv = rng.integers(0, 2**32, len(B), dtype=np.uint32)
+    Ck, Cv = cr.merge_kv(dev(A), dev(Av.view(np.float32)), dev(B), dev(Bv.view(np.float32)),
+                         key_type="u32")
+    torch.cuda.synchronize()
+    _, wv, _ = oracle.merge_kv(A, Av, B, Bv)
+    assert same_bits(host(Cv, np.uint32), wv)
+
+
+@pytest.mark.parametrize("dt", KEY_DTYPES)
+def test_co_rank_every_rank(dt):
+    """co_rank_many for every rank of several shapes equals Algorithm 1 on the host."""
+    rng = np.random.default_rng(102)
+    for m, n in [(0, 0), (0, 9), (9, 0), (1, 1), (37, 53), (1000, 3), (3000, 2500)]:
+        for spread in (None, 2):
+            A = sorted_keys(rng, m, dt, spread)
+            B = sorted_keys(rng, n, dt, spread)
+            ranks = np.arange(-2, m + n + 3, dtype=np.int64)
+            oi, oj = cr.co_rank_many(dev(A), dev(B), torch.from_numpy(ranks).cuda(),
+                                     key_type=key_type(A))
+            wj, wk = oracle.co_rank_many(A, B, ranks)
+            assert np.array_equal(oi.cpu().numpy(), wj)
+            assert np.array_equal(oj.cpu().numpy(), wk)
+            if m + n:
+                r = int(rng.integers(0, m + n + 1))
+                assert cr.co_rank(dev(A), dev(B), r, key_type=key_type(A)) == \
+                    tuple(oracle.co_rank(r, A, B)[:2])
+
+
+def test_co_rank_figure2_on_gpu():
+    """The paper's Figure 2 example, through the C ABI."""
+    from conftest import read_golden
+    rows = {r[0]: r[1:] for r in read_golden("figure1.txt")}
+    A = np.array([int(x) for x in rows["A"]], np.int32)
+    B = np.array([int(x) for x in rows["B"]], np.int32)
+    assert cr.co_rank(dev(A), dev(B), 22) == (12, 10)
+    C = cr.merge(dev(A), dev(B))
+    want = np.array([int(x) for x in rows["C"]], np.int32)
+    assert np.array_equal(C.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+@pytest.mark.parametrize("vdt", [None, np.float32, np.float64])
+def test_batched(dt, vdt):
+    rng = np.random.default_rng(103)
+    nseg = 300
+    ms = np.floor(np.exp2(rng.random(nseg) * 13)).astype(np.int64)
+    ns = np.floor(np.exp2(rng.random(nseg) * 13)).astype(np.int64)
+    ms[::11] = 0
+    ns[::7] = 0
+    ms[5] = ns[5] = 0
+    a_off = np.concatenate([[0], np.cumsum(ms)])
+    b_off = np.concatenate([[0], np.cumsum(ns)])
+    A = np.concatenate([sorted_keys(rng, x, dt, 40) for x in ms])
+    B = np.concatenate([sorted_keys(rng, x, dt, 40) for x in ns])
+    Av = rng.standard_normal(len(A)).astype(vdt or np.float32)
+    Bv = rng.standard_normal(len(B)).astype(vdt or np.float32)
+    kt = key_type(A)
+    Ck, Cv = cr.batched_merge_kv(a_off, b_off, dev(A), dev(Av) if vdt else None, dev(B),
+                                 dev(Bv) if vdt else None, key_type=kt)
+    torch.cuda.synchronize()
+    wk, wv = oracle.batched_merge_kv(a_off, b_off, A, Av, B, Bv)
+    assert same_bits(host(Ck, dt), wk)
+    if vdt:
+        assert same_bits(host(Cv, vdt), wv)
+        gC = rng.standard_normal(len(A) + len(B)).astype(vdt)
+        gA, gB = cr.batched_merge_kv_backward(a_off, b_off, dev(A), dev(B), dev(gC), key_type=kt)
+        torch.cuda.synchronize()
+        ga, gb = oracle.batched_merge_grad(a_off, b_off, A, B, gC)
+        assert same_bits(host(gA, vdt), ga)
+        assert same_bits(host(gB, vdt), gb)
+
+
+def test_batched_bad_table_reports():
+    A = np.arange(100, dtype=np.int32)
+    B = np.arange(100, dtype=np.int32)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    for a_off in ([0, 50, 40, 100], [0, 50, 60, 101], [1, 50, 60, 100]):
+        cr.batched_merge_kv(a_off, [0, 30, 60, 100], dev(A), None, dev(B), None, ws=ws)
+        with pytest.raises(cr.CorankError) as e:
+            cr.workspace_status(ws)
+        assert e.value.name == "CR_EBADSEG"
+    cr.batched_merge_kv([0, 50, 60, 100], [0, 30, 60, 100], dev(A), None, dev(B), None, ws=ws)
+    cr.workspace_status(ws)
+
+
+@pytest.mark.parametrize("N,w", [(1, 1), (10, 4), (5000, 16), (3 * 3840 + 5, 1024),
+                                 (40000, 3000), (65536, 1024)])
+def test_merge_pass_and_backward(N, w):
+    rng = np.random.default_rng(104)
+    X = rng.integers(0, 20, N).astype(np.uint64) * np.uint64(1 << 62)
+    for a0 in range(0, N, w):
+        X[a0:a0 + w].sort(kind="stable")
+    Xv = rng.standard_normal(N).astype(np.float32)
+    Y, Yv = cr.merge_pass(dev(X), dev(Xv), w, key_type="u64")
+    gY = rng.standard_normal(N).astype(np.float32)
+    gX = cr.merge_pass_backward(dev(X), dev(gY), w, key_type="u64")
+    torch.cuda.synchronize()
+    wy, wyv, src = oracle.merge_pass(X, Xv, w)
+    assert same_bits(host(Y, np.uint64), wy)
+    assert same_bits(host(Yv, np.float32), wyv)
+    want = np.empty_like(gY)
+    want[src] = gY
+    assert same_bits(host(gX, np.float32), want)
+
+
+def test_status_ok_after_calls():
+    A = dev(np.arange(10000, dtype=np.int32))
+    B = dev(np.arange(7000, dtype=np.int32))
+    ws = torch.empty(cr.api.merge_workspace_bytes("i32", 0, 10000, 7000), dtype=torch.uint8,
+                     device="cuda")
+    cr.merge(A, B, ws=ws)
+    cr.workspace_status(ws)
+
+
+def test_argument_errors_on_device():
+    A = torch.arange(64, dtype=torch.int32, device="cuda")
+    B = torch.arange(64, dtype=torch.int32, device="cuda")
+    with pytest.raises(cr.CorankError) as e:
+        cr.merge(A[1:], B)            # 4-byte offset view: not 16-byte aligned
+    assert e.value.name == "CR_EALIGN"
+    buf = torch.zeros(256, dtype=torch.int32, device="cuda")
+    with pytest.raises(cr.CorankError) as e:
+        cr.merge(buf[:64], B, out=buf[:128])
+    assert e.value.name == "CR_EALIAS"
+    with pytest.raises(cr.CorankError) as e:
+        cr.merge(A, B, ws=torch.empty(256, dtype=torch.uint8, device="cuda"))
+    assert e.value.name == "CR_ENOSPACE"
+    with pytest.raises(cr.CorankError) as e:
+        cr.co_rank(A, B, 129)
+    assert e.value.name == "CR_EINVAL"
