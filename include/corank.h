@@ -215,6 +215,31 @@ cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int
                                  void* ws, size_t ws_bytes, cr_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free stable merge (the paper has no counterpart: this is a
+ * deployment convenience of this library).
+ * Same result as cr_stable_merge (keys only, optional C_tag), but it takes no
+ * workspace: the tile table lives in a fixed 4 MiB array inside the library's
+ * device image, which every GPU that loads the library holds until exit.
+ * For callers that cannot call cudaMalloc or take memory from an allocator --
+ * code running inside a host framework that owns every allocation, a
+ * real-time loop that must not enter the allocator, a plug-in handed only its
+ * input and output buffers.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture begins.
+ *   - Size limit: m + n at most 131064 tiles (cr_tile_size(key_type, 0)
+ *     elements each): 503,285,760 elements for 4-byte keys, 251,642,880 for
+ *     8-byte keys.  Larger requests return CR_EINVAL and launch nothing.
+ *   - Every call shares the array; calls whose kernels overlap on the GPU
+ *     (other streams, other host threads) race and may give wrong output, so
+ *     serialise them on one stream.  Device-side status is not reported for
+ *     this entry point (cr_workspace_status needs a workspace).
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * ------------------------------------------------------------------------ */
+cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_t m, const void* B,
+                                  int64_t n, void* C, uint32_t* C_tag, cr_stream stream);
+
+/* ------------------------------------------------------------------------
  * Device-side status of the last call that used workspace `ws` on `stream`.
  * Synchronises `stream`, reads the status word and returns CR_OK,
  * CR_ETIMEOUT, CR_EINTERNAL or CR_EBADSEG (or CR_ECUDA if the read failed).

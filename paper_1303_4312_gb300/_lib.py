@@ -44,6 +44,7 @@ SIGNATURES = {
     "cr_merge_pass": ([INT, INT, P, P, I64, I64, P, P, P, SZ, P], INT),
     "cr_merge_pass_backward": ([INT, INT, P, I64, I64, P, P, P, SZ, P], INT),
     "cr_workspace_status": ([P, P], INT),
+    "cr_stable_merge_noalloc": ([INT, P, I64, P, I64, P, P, P], INT),
 }
 
 STATUS = {0: "CR_OK", 1: "CR_EINVAL", 2: "CR_EALIAS", 3: "CR_EALIGN", 4: "CR_ENOSPACE",

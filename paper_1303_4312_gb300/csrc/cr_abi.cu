@@ -239,6 +239,11 @@ cr_status launch_tiles_backward(int key_type, int vb, const void* Ak, int64_t m,
 
 }  // namespace
 
+// Lets other translation units of the library report through cr_last_error().
+namespace cr {
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace cr
+
 extern "C" {
 
 const char* cr_status_string(int status) {

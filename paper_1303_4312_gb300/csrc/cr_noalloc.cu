@@ -1,0 +1,155 @@
+// cr_noalloc.cu -- cr_stable_merge_noalloc: the keys-only stable merge for
+// callers that cannot allocate device memory.
+//
+// Who needs it: code that runs where cudaMalloc is unavailable or forbidden
+// -- for example a host callback or a library hook invoked while the
+// application owns every allocation and has none to lend, a real-time loop
+// that must not enter the allocator, or a plug-in whose host framework gives
+// it buffers for inputs and outputs but no scratch space.  The regular entry
+// point cr_stable_merge needs a caller-provided workspace for its tile table;
+// this one keeps that table in a fixed-size array that is part of the
+// library's device image instead.
+//
+// The array (kNoAllocScratchBytes, 4 MiB) is a file-scope __device__ symbol:
+// every GPU on which the library is loaded holds it until the process exits.
+// In host code the symbol's name is only a host-side stand-in, so the device
+// address is looked up with cudaGetSymbolAddress once per device (the first
+// call on that device, with that device current) and then passed to the
+// kernels.  That first call should be made before any stream capture begins.
+//
+// All calls share the one array: two calls whose kernels overlap on the GPU
+// (different streams, or different host threads) race on it and may produce
+// wrong output.  Serialise them on one stream.  The array keeps whatever the
+// last call left there; the only field that must start at zero, the status
+// word, is reset by the first kernel of every call, and every tile record is
+// written before it is read.
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "../../include/corank.h"
+#include "cr_launch.cuh"
+
+namespace cr {
+void set_last_error(const char* msg);   // cr_abi.cu
+}
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDev = 64;
+void* g_scratch_ptr[kMaxDev];
+std::once_flag g_scratch_once[kMaxDev];
+cudaError_t g_scratch_err[kMaxDev];
+
+cr_status na_fail(cr_status st, const char* fmt, ...) {
+    char buf[384];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    cr::set_last_error(buf);
+    return st;
+}
+
+// Device address of the scratch array on the current device (looked up once).
+cr_status scratch_on_current_device(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return na_fail(CR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDev) return na_fail(CR_EUNSUPPORTED, "device %d out of range", dev);
+    std::call_once(g_scratch_once[dev], [dev] {
+        void* p = nullptr;
+        g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        g_scratch_ptr[dev] = (g_scratch_err[dev] == cudaSuccess) ? p : nullptr;
+    });
+    if (g_scratch_err[dev] != cudaSuccess || g_scratch_ptr[dev] == nullptr)
+        return na_fail(CR_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                       cudaGetErrorString(g_scratch_err[dev]));
+    *out = g_scratch_ptr[dev];
+    return CR_OK;
+}
+
+bool ranges_overlap(const void* a, int64_t abytes, const void* b, int64_t bbytes) {
+    if (abytes <= 0 || bbytes <= 0) return false;
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+    return a0 < b0 + uintptr_t(bbytes) && b0 < a0 + uintptr_t(abytes);
+}
+
+}  // namespace
+
+extern "C" cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_t m,
+                                             const void* B, int64_t n, void* C,
+                                             uint32_t* C_tag, cr_stream stream) {
+    int ks = 0;
+    if (key_type == CR_KEY_I32 || key_type == CR_KEY_U32) ks = 4;
+    if (key_type == CR_KEY_I64 || key_type == CR_KEY_U64) ks = 8;
+    if (ks == 0) return na_fail(CR_EINVAL, "unknown key type %d", key_type);
+    if (m < 0 || n < 0) return na_fail(CR_EINVAL, "negative size");
+    const int64_t mn = m + n;
+    const int64_t tile = cr::tile_for(ks, 0);
+    const int64_t max_tiles =
+        int64_t((kNoAllocScratchBytes - size_t(cr::kHeaderBytes)) / sizeof(cr::TileRec));
+    const int64_t ntiles = (mn + tile - 1) / tile;
+    if (ntiles > max_tiles)
+        return na_fail(CR_EINVAL,
+                       "m + n = %lld exceeds the %lld elements the fixed %zu-byte scratch "
+                       "array can plan for this key type; use cr_stable_merge with a workspace",
+                       static_cast<long long>(mn), static_cast<long long>(max_tiles * tile),
+                       kNoAllocScratchBytes);
+    struct { const void* p; int64_t count; const char* name; } arrs[4] = {
+        {A, m, "A"}, {B, n, "B"}, {C, mn, "C"}, {C_tag, C_tag ? mn : 0, "C tag"}};
+    for (auto& a : arrs) {
+        if (a.count == 0) continue;
+        if (a.p == nullptr) return na_fail(CR_EINVAL, "%s is NULL", a.name);
+        if (reinterpret_cast<uintptr_t>(a.p) & 15u)
+            return na_fail(CR_EALIGN, "%s is not 16-byte aligned", a.name);
+    }
+    if (ranges_overlap(C, mn * ks, A, m * ks) || ranges_overlap(C, mn * ks, B, n * ks) ||
+        (C_tag && (ranges_overlap(C_tag, mn * 4, A, m * ks) ||
+                   ranges_overlap(C_tag, mn * 4, B, n * ks) ||
+                   ranges_overlap(C_tag, mn * 4, C, mn * ks))))
+        return na_fail(CR_EALIAS, "an output overlaps an input");
+    if (C_tag && mn > (int64_t(1) << 32)) return na_fail(CR_EINVAL, "tags need m + n <= 2^32");
+    if (mn == 0) {
+        cr::set_last_error("");
+        return CR_OK;
+    }
+    void* scratch = nullptr;
+    const cr_status s = scratch_on_current_device(&scratch);
+    if (s != CR_OK) return s;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cr::MergeArgs a{};
+    a.ak = A;
+    a.bk = B;
+    a.ck = C;
+    a.ctag = C_tag;
+    a.a_total = m;
+    a.b_total = n;
+    a.c_total = mn;
+    a.tag_b = m;
+    a.ws = scratch;
+    auto run = [&](auto ops) {
+        cudaError_t e = ops.partition_single(A, m, B, n, tile, ntiles, scratch, st);
+        if (e != cudaSuccess) return e;
+        return ops.merge_fwd(0, C_tag != nullptr, a, ntiles, st);
+    };
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (key_type) {
+        case CR_KEY_I32: e = run(cr::KeyOps<int32_t>{}); break;
+        case CR_KEY_U32: e = run(cr::KeyOps<uint32_t>{}); break;
+        case CR_KEY_I64: e = run(cr::KeyOps<int64_t>{}); break;
+        case CR_KEY_U64: e = run(cr::KeyOps<uint64_t>{}); break;
+    }
+    if (e != cudaSuccess)
+        return na_fail(CR_ECUDA, "merge launch: %s", cudaGetErrorString(e));
+    cr::set_last_error("");
+    return CR_OK;
+}

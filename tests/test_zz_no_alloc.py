@@ -1,0 +1,84 @@
+"""The allocation-free stable merge, cr_stable_merge_noalloc.
+
+Some callers cannot allocate device memory (a plug-in given only its input
+and output buffers, a real-time loop that must not enter an allocator, code
+running while its host framework owns every allocation).  For them the
+library keeps the merge's tile table in a fixed array inside its device image
+instead of a caller workspace.  These tests call that entry point through the
+C ABI and check it against the workspace-based cr_stable_merge, bit for bit,
+on two calls in a row (the second call reuses the array the first one left
+behind).  This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1303_4312_gb300 import _lib, build
+
+MAX_TILES = (4 * 2**20 - 256) // 32
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_noalloc_rejects_oversize_without_gpu(lib):
+    """Beyond the array's capacity the call is refused before any launch."""
+    tile = lib.cr_tile_size(0, 0)
+    too_many = MAX_TILES * tile + 1
+    A = ctypes.c_void_p(0x1_0000_0000)
+    st = lib.cr_stable_merge_noalloc(0, A, too_many, ctypes.c_void_p(0x10_0000_0000), 0,
+                                     ctypes.c_void_p(0x20_0000_0000), None, None)
+    assert st == 1
+    assert "scratch" in lib.cr_last_error().decode()
+    tile8 = lib.cr_tile_size(3, 0)
+    st = lib.cr_stable_merge_noalloc(3, A, MAX_TILES * tile8 + 1, A, 0,
+                                     ctypes.c_void_p(0x40_0000_0000), None, None)
+    assert st == 1
+
+
+def _merge_both(lib, A, B, code, tag):
+    """Same merge through cr_stable_merge (with a workspace) and through
+    cr_stable_merge_noalloc; returns both outputs (and tags)."""
+    m, n = A.numel(), B.numel()
+    dev = A.device
+    s = torch.cuda.current_stream(dev).cuda_stream
+    C1 = torch.empty(m + n, dtype=A.dtype, device=dev)
+    C2 = torch.full((m + n,), -1, dtype=A.dtype, device=dev)
+    T1 = torch.empty(m + n, dtype=torch.int32, device=dev) if tag else None
+    T2 = torch.full((m + n,), -1, dtype=torch.int32, device=dev) if tag else None
+    need = ctypes.c_size_t()
+    _lib.check(lib.cr_merge_workspace_size(code, 0, m, n, ctypes.byref(need)))
+    ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=dev)
+    p = lambda t: None if t is None else t.data_ptr()
+    _lib.check(lib.cr_stable_merge(code, A.data_ptr(), m, B.data_ptr(), n, C1.data_ptr(), p(T1),
+                                   ws.data_ptr(), ws.numel(), s))
+    _lib.check(lib.cr_stable_merge_noalloc(code, A.data_ptr(), m, B.data_ptr(), n,
+                                           C2.data_ptr(), p(T2), s))
+    torch.cuda.synchronize()
+    return C1, C2, T1, T2
+
+
+@pytest.mark.gpu
+def test_noalloc_matches_workspace_merge_twice(lib):
+    g = torch.Generator(device="cuda").manual_seed(1234)
+    # call 1: many tiles, int32 keys with heavy duplicates, with source tags
+    A = torch.sort(torch.randint(0, 1000, (3_000_001,), generator=g, device="cuda",
+                                 dtype=torch.int32)).values
+    B = torch.sort(torch.randint(0, 1000, (2_500_003,), generator=g, device="cuda",
+                                 dtype=torch.int32)).values
+    C1, C2, T1, T2 = _merge_both(lib, A, B, 0, tag=True)
+    assert torch.equal(C1, C2)
+    assert torch.equal(T1, T2)
+    # call 2, right after: fewer tiles and 8-byte keys, so a stale table
+    # left by call 1 in the shared array would show up as wrong output
+    A = torch.sort(torch.randint(-2**62, 2**62, (70_001,), generator=g, device="cuda",
+                                 dtype=torch.int64)).values
+    B = torch.sort(torch.randint(-2**62, 2**62, (123_457,), generator=g, device="cuda",
+                                 dtype=torch.int64)).values
+    C1, C2, _, _ = _merge_both(lib, A, B, 2, tag=False)
+    assert torch.equal(C1, C2)
+    assert bool((C2[1:] >= C2[:-1]).all())
