@@ -48,9 +48,10 @@ template <class K, int VB, bool TAG, bool BWD>
 cudaError_t launch_merge(const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
     constexpr int NT = TileShape<int(sizeof(K)), VB>::NT;
     constexpr int IPT = TileShape<int(sizeof(K)), VB>::IPT;
-    constexpr int NS = Stages<int(sizeof(K)), VB, BWD>::NS;
+    constexpr int NS = Stages<int(sizeof(K)), VB, TAG, BWD>::NS;
+    constexpr int MINB = Stages<int(sizeof(K)), VB, TAG, BWD>::MINB;
     using L = Layout<K, VB, TAG, NT, IPT, NS, BWD>;
-    auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, NS, BWD>;
+    auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, NS, MINB, BWD>;
     static LaunchShape cache[kMaxDevices];
     static std::once_flag once[kMaxDevices];
     LaunchShape sh;
@@ -91,7 +92,8 @@ static inline unsigned blocks_for(int64_t n, int threads) {
 template <class K>
 cudaError_t KeyOps<K>::partition_single(const void* A, int64_t m, const void* B, int64_t n,
                                         int64_t tile, int64_t ntiles, void* ws, cudaStream_t st) {
-    const unsigned g = blocks_for(ntiles > 0 ? ntiles : 1, 256);
+    // 256 threads search 256 consecutive boundaries = 255 tiles per block
+    const unsigned g = unsigned(((ntiles > 0 ? ntiles : 1) + 254) / 255);
     partition_single_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(A), m,
                                                    static_cast<const K*>(B), n, tile, ntiles, ws);
     return cudaGetLastError();

@@ -11,15 +11,19 @@
 namespace cr {
 
 // Tile shape per key size and payload width: consumer threads NT and items per
-// thread IPT (odd, so that a warp's stride-IPT shared-memory writes fall in
+// thread IPT (odd, so that a warp's stride-IPT shared-memory accesses fall in
 // distinct banks).  TILE = NT * IPT is the same for the forward and the
 // backward kernel of a (key, payload) pair.
-template <int KS, int VB> struct TileShape { static constexpr int NT = 128, IPT = 15; };
+template <int KS, int VB> struct TileShape { static constexpr int NT = 256, IPT = 7; };
 template <> struct TileShape<4, 0> { static constexpr int NT = 256, IPT = 15; };
 
-// Stages in the shared-memory ring (fit two CTAs per SM where possible).
-template <int KS, int VB, bool BWD> struct Stages {
-    static constexpr int NS = (BWD || KS + VB <= 8) ? 3 : 2;
+// Stages in the shared-memory ring and the CTAs per SM they leave room for:
+// four stages when a stage is at most 16 KB (three CTAs per SM), else three.
+template <int KS, int VB, bool TAG, bool BWD> struct Stages {
+    static constexpr int TILE = TileShape<KS, VB>::NT * TileShape<KS, VB>::IPT;
+    static constexpr int BYTES = TILE * (KS + VB + (TAG && !BWD ? 4 : 0));
+    static constexpr int NS = BYTES <= 16384 ? 4 : 3;
+    static constexpr int MINB = NS == 4 ? 3 : 2;
 };
 
 template <int KS, int VB> constexpr int64_t tile_of() {

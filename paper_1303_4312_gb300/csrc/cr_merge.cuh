@@ -1,23 +1,30 @@
-// cr_merge.cuh -- the persistent tile-merge kernels (forward and payload
-// backward) for sm_103a.
+// cr_merge.cuh -- the persistent tile-merge kernel (forward and payload
+// backward) for sm_103a, driven by a table of tile records.
 //
 // Each CTA runs one producer warp and NT consumer threads and walks the
-// output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...  Because every
-// tile carries exactly TILE = NT*IPT output elements (Algorithm 2 with equal
-// blocks, Proposition 2), the static round-robin schedule is balanced.
+// output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...  Every tile
+// carries exactly TILE = NT*IPT output elements (the last one of a merge or
+// segment fewer), so the static round-robin schedule is balanced
+// (Algorithm 2 with equal blocks, Proposition 2).
 //
-//  producer (one lane):  reads the tile record (A window, B window, output
-//      offset) written by a partition kernel, then stages the windows into
-//      an NS-deep ring of shared-memory buffers with bulk copies (TMA
-//      engine, cp.async.bulk + mbarrier transaction counts).  Windows start
-//      at arbitrary element offsets: the copy covers the 16-byte aligned
+//  producer (one lane): reads the tile record (A window, B window, output
+//      offset; prefetched one tile ahead), then stages the windows into an
+//      NS-deep ring of shared-memory stages with bulk copies (TMA engine,
+//      cp.async.bulk completing on the stage's mbarrier).  Windows start at
+//      arbitrary element offsets: the copy covers the 16-byte aligned
 //      superset and the consumers index from the head offset.
-//  consumers (NT threads): thread s co-ranks diagonal s*IPT inside the two
-//      shared-memory windows (Algorithm 1 again, now over a tile), then merges
-//      exactly IPT elements serially (ties take A) and writes them to an
-//      output staging buffer in shared memory; one thread then issues bulk
-//      stores of the whole tile (the 16-byte aligned interior) and a few
-//      threads store the ragged ends with plain stores.
+//  consumers (NT threads): thread s finds the split of diagonal s*IPT of
+//      the tile inside the shared-memory windows, merges exactly IPT
+//      elements serially into registers (ties take A), and after a barrier
+//      writes them back into the same stage, which then serves as the output
+//      staging buffer; one thread issues bulk stores of the 16-byte aligned
+//      interior and a few threads store the ragged ends.  A stage is handed
+//      back to the producer one tile later, once its bulk store has read it.
+//
+// The in-tile split is the unique co-rank of Lemma 1, found by bisection on
+// the first Lemma condition (A[j-1] <= B[d-j] holds exactly for j <= j*):
+// one comparison per step instead of Algorithm 1's two-sided test, which
+// matters here because every consumer thread runs it once per tile.
 #pragma once
 
 #include "cr_device.cuh"
@@ -34,11 +41,13 @@ struct StageInfo {
     int64_t ga, gb, gc;      // window starts (elements) in A, B and output
     int32_t alen, blen;      // window lengths
     int32_t ak, bk;          // smem element offset of A[ga] / B[gb] in the key stage
-    int32_t av, bv;          // same in the payload / gradient stage
+    int32_t av, bv;          // same in the payload stage (forward) / head of gC (backward)
 };
 static_assert(sizeof(StageInfo) == 48, "StageInfo size");
 
 // Shared-memory layout of one kernel instantiation (host and device agree).
+// A stage holds the input windows and, after the consumers have read them,
+// the tile's output (forward: keys, payloads, tags; backward: gA, gB).
 template <class K, int VB, bool TAG, int NT, int IPT, int NS, bool BWD>
 struct Layout {
     static constexpr int TILE = NT * IPT;
@@ -46,28 +55,20 @@ struct Layout {
     static constexpr int EK = 16 / KS;
     static constexpr int VS = VB ? VB : 4;
     static constexpr int EV = 16 / VS;
-    // stage buffers (elements)
     static constexpr int SK = TILE + 4 * EK;                      // A and B key windows
     static constexpr int SV = (VB && !BWD) ? TILE + 4 * EV : 0;   // A and B payload windows
-    static constexpr int SG = BWD ? TILE + 2 * EV : 0;            // gradient window of C
+    static constexpr int ST = (TAG && !BWD) ? TILE + 8 : 0;       // output tags
+    static constexpr int SG = BWD ? TILE + 4 * EV : 0;            // gC window, then gA | gB
     static constexpr size_t STAGE_K = align_up_sz(size_t(SK) * KS, 128);
     static constexpr size_t STAGE_V = align_up_sz(size_t(SV) * VS, 128);
+    static constexpr size_t STAGE_T = align_up_sz(size_t(ST) * 4, 128);
     static constexpr size_t STAGE_G = align_up_sz(size_t(SG) * VS, 128);
-    static constexpr size_t STAGE = STAGE_K + STAGE_V + STAGE_G;
-    // output buffers
-    static constexpr int OK = BWD ? 0 : TILE + 2 * EK;
-    static constexpr int OV = BWD ? TILE + 4 * EV : (VB ? TILE + 2 * EV : 0);
-    static constexpr int OT = (TAG && !BWD) ? TILE + 8 : 0;
-    static constexpr size_t OUT_K = align_up_sz(size_t(OK) * KS, 128);
-    static constexpr size_t OUT_V = align_up_sz(size_t(OV) * VS, 128);
-    static constexpr size_t OUT_T = align_up_sz(size_t(OT) * 4, 128);
-    static constexpr size_t OUT = OUT_K + OUT_V + OUT_T;
-    // regions
+    static constexpr size_t STAGE = STAGE_K + STAGE_V + STAGE_T + STAGE_G;
     static constexpr size_t BAR_OFF = 0;                       // full[NS], empty[NS], flags
     static constexpr size_t INFO_OFF = 256;
     static constexpr size_t STAGE_OFF = align_up_sz(INFO_OFF + NS * sizeof(StageInfo), 128);
-    static constexpr size_t OUT_OFF = STAGE_OFF + NS * STAGE;
-    static constexpr size_t TOTAL = OUT_OFF + 2 * OUT + 128;  // + slack for one-past reads
+    static constexpr size_t TOTAL = STAGE_OFF + NS * STAGE + 128;  // + slack for one-past reads
+    static_assert(NS >= 3, "the consumers hold two stages at a time");
     static_assert(2 * NS * 8 + 16 <= INFO_OFF, "barrier area");
     static_assert(TILE % EK == 0 && TILE % EV == 0 && TILE % 4 == 0, "tile alignment");
     static_assert(TOTAL <= 232448, "exceeds 227 KB of shared memory per CTA");
@@ -114,8 +115,8 @@ __device__ __forceinline__ void window_bulk(T* region, const T* gbase, const Win
 }
 
 // Store the staged output window buf[ph + x] (x < len) to gbase[g0 + x],
-// ph = g0 mod E.  bulk part (whole 16-byte chunks): issued by the caller
-// thread; edge elements: thread `lane` in [0, 2E) of a helper group.
+// ph = g0 mod E.  store_bulk: the whole 16-byte chunks (one thread);
+// store_edges: the ragged ends, one element per `lane` in [0, 2E).
 template <class T>
 __device__ __forceinline__ void store_bulk(T* gbase, const T* buf, int64_t g0, int32_t len, int E) {
     const int64_t mask = ~int64_t(E - 1);
@@ -146,13 +147,28 @@ __device__ __forceinline__ void store_edges(T* gbase, const T* buf, int64_t g0, 
     if (g >= 0) gbase[g] = buf[ph + (g - g0)];
 }
 
+// Number of A elements among the first d outputs of the stable merge of
+// sA[0, alen) and sB[0, blen): the co-rank j of Lemma 1, by bisection on
+// its first condition.
+template <class K>
+__device__ __forceinline__ int split_in_tile(const K* sA, int alen, const K* sB, int blen, int d) {
+    int lo = d - blen > 0 ? d - blen : 0;
+    int hi = d < alen ? d : alen;
+#pragma unroll 1
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (!(sB[d - 1 - mid] < sA[mid])) lo = mid + 1;   // A[mid] <= B[d-1-mid]: A[mid] is in
+        else hi = mid;
+    }
+    return lo;
+}
 
 // ---------------------------------------------------------------------------
 // Forward (BWD = false): C keys [+ payloads] [+ tags].
 // Backward (BWD = true): gA / gB from gC, routed by the same merge decisions.
 // ---------------------------------------------------------------------------
-template <class K, int VB, bool TAG, int NT, int IPT, int NS, bool BWD>
-__global__ void __launch_bounds__(NT + 32, 1) merge_tiles_kernel(const MergeArgs p) {
+template <class K, int VB, bool TAG, int NT, int IPT, int NS, int MINB, bool BWD>
+__global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeArgs p) {
     using L = Layout<K, VB, TAG, NT, IPT, NS, BWD>;
     using V = typename VBits<VB>::T;
     constexpr int TILE = L::TILE;
@@ -169,19 +185,14 @@ __global__ void __launch_bounds__(NT + 32, 1) merge_tiles_kernel(const MergeArgs
     volatile int32_t* s_issued = s_abort + 1;
     StageInfo* info = reinterpret_cast<StageInfo*>(smem + L::INFO_OFF);
 
-    auto stage_k = [&](int s) { return reinterpret_cast<K*>(smem + L::STAGE_OFF + s * L::STAGE); };
-    auto stage_v = [&](int s) {
-        return reinterpret_cast<V*>(smem + L::STAGE_OFF + s * L::STAGE + L::STAGE_K);
+    auto base = [&](int s) { return smem + L::STAGE_OFF + size_t(s) * L::STAGE; };
+    auto stage_k = [&](int s) { return reinterpret_cast<K*>(base(s)); };
+    auto stage_v = [&](int s) { return reinterpret_cast<V*>(base(s) + L::STAGE_K); };
+    auto stage_t = [&](int s) {
+        return reinterpret_cast<uint32_t*>(base(s) + L::STAGE_K + L::STAGE_V);
     };
     auto stage_g = [&](int s) {
-        return reinterpret_cast<V*>(smem + L::STAGE_OFF + s * L::STAGE + L::STAGE_K + L::STAGE_V);
-    };
-    auto out_k = [&](int b) { return reinterpret_cast<K*>(smem + L::OUT_OFF + b * L::OUT); };
-    auto out_v = [&](int b) {
-        return reinterpret_cast<V*>(smem + L::OUT_OFF + b * L::OUT + L::OUT_K);
-    };
-    auto out_t = [&](int b) {
-        return reinterpret_cast<uint32_t*>(smem + L::OUT_OFF + b * L::OUT + L::OUT_K + L::OUT_V);
+        return reinterpret_cast<V*>(base(s) + L::STAGE_K + L::STAGE_V + L::STAGE_T);
     };
 
     WsHeader* hdr = reinterpret_cast<WsHeader*>(p.ws);
@@ -286,105 +297,125 @@ __global__ void __launch_bounds__(NT + 32, 1) merge_tiles_kernel(const MergeArgs
     int it = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int s = it % NS;
-        const int ob = it & 1;
-        if (tid == 0) bulk_wait_read<1>();   // output buffer `ob` (tile it-2) drained
-        named_sync(1, NT);
-        bool ready = mbar_wait(&full[s], (it / NS) & 1);
+        const bool ready = mbar_wait(&full[s], (it / NS) & 1);
         if (!ready) {
             set_status(&hdr->status, kDevTimeout);
             *s_abort = 1;
         }
         const StageInfo in = info[s];
-        const int len = ready ? in.alen + in.blen : 0;
+        const int alen = ready ? in.alen : 0;
+        const int blen = ready ? in.blen : 0;
+        const int len = alen + blen;
         const int d = min(tid * IPT, len);
         const int cnt = min(IPT, len - d);
-        const K* sk = stage_k(s);
-        const int ao = in.ak, bo = in.bk;
-        const int alen = in.alen, blen = in.blen;
-        int j = 0;
-        if (cnt > 0) {
-            j = co_rank<K, int>(d, alen, blen, [&](int x) { return sk[ao + x]; },
-                                [&](int x) { return sk[bo + x]; });
-        }
+        K* sk = stage_k(s);
+        const K* sA = sk + in.ak;
+        const K* sB = sk + in.bk;
+        int j = split_in_tile(sA, alen, sB, blen, d);
         int k = d - j;
         K a = K(0), b = K(0);
         if (cnt > 0) {
-            a = sk[ao + j];   // may be one past A's window: unused then
-            b = sk[bo + k];
+            a = sA[j];   // may be one past A's window: never taken then
+            b = sB[k];
         }
-        if (!BWD) {
-            K* ok = out_k(ob);
-            const int ph = int(in.gc & (EK - 1));
-            V* ov = out_v(ob);
-            const int phv = int(in.gc & (EV - 1));
-            uint32_t* ot = out_t(ob);
-            const int pht = int(in.gc & 3);
+        if constexpr (!BWD) {
+            K okey[IPT];
+            V oval[VB ? IPT : 1];
+            uint32_t otag[TAG ? IPT : 1];
             const V* sv = stage_v(s);
             const int avo = in.av, bvo = in.bv;
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 if (q < cnt) {
-                    const bool takeB = (k < blen) && (j >= alen || b < a);
-                    ok[ph + d + q] = takeB ? b : a;
-                    if constexpr (VB != 0) ov[phv + d + q] = sv[takeB ? bvo + k : avo + j];
+                    const bool takeA = (k >= blen) || (j < alen && !(b < a));   // ties: A first
+                    okey[q] = takeA ? a : b;
+                    if constexpr (VB != 0) oval[q] = sv[takeA ? avo + j : bvo + k];
                     if constexpr (TAG)
-                        ot[pht + d + q] = takeB ? uint32_t(p.tag_b + in.gb + k) : uint32_t(in.ga + j);
-                    const K nx = sk[takeB ? bo + k + 1 : ao + j + 1];
-                    if (takeB) { b = nx; ++k; } else { a = nx; ++j; }
+                        otag[q] = takeA ? uint32_t(in.ga + j) : uint32_t(p.tag_b + in.gb + k);
+                    if (takeA) ++j; else ++k;
+                    const K nx = takeA ? sA[j] : sB[k];
+                    if (takeA) a = nx; else b = nx;
                 }
             }
+            named_sync(1, NT);   // every input of stage s has been read
+            const int ph = int(in.gc & (EK - 1));
+#pragma unroll
+            for (int q = 0; q < IPT; ++q)
+                if (q < cnt) sk[ph + d + q] = okey[q];
+            if constexpr (VB != 0) {
+                V* ov = stage_v(s);
+                const int phv = int(in.gc & (EV - 1));
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if (q < cnt) ov[phv + d + q] = oval[q];
+            }
+            if constexpr (TAG) {
+                uint32_t* ot = stage_t(s);
+                const int pht = int(in.gc & 3);
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if (q < cnt) ot[pht + d + q] = otag[q];
+            }
         } else {
-            V* oa = out_v(ob);
-            const int pha = int(in.ga & (EV - 1));
-            const int ob_off = int(((pha + alen + EV - 1) / EV) * EV);
-            V* obb = oa + ob_off;
-            const int phb = int(in.gb & (EV - 1));
+            V gval[IPT];
+            int dst[IPT];
             const V* sg = stage_g(s) + in.av;
+            const int pha = int(in.ga & (EV - 1));
+            const int boff = ((pha + alen + EV - 1) / EV) * EV + int(in.gb & (EV - 1));
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 if (q < cnt) {
-                    const bool takeB = (k < blen) && (j >= alen || b < a);
-                    const V g = sg[d + q];
-                    if (takeB) obb[phb + k] = g; else oa[pha + j] = g;
-                    const K nx = sk[takeB ? bo + k + 1 : ao + j + 1];
-                    if (takeB) { b = nx; ++k; } else { a = nx; ++j; }
+                    const bool takeA = (k >= blen) || (j < alen && !(b < a));
+                    gval[q] = sg[d + q];
+                    dst[q] = takeA ? pha + j : boff + k;
+                    if (takeA) ++j; else ++k;
+                    const K nx = takeA ? sA[j] : sB[k];
+                    if (takeA) a = nx; else b = nx;
                 }
             }
+            named_sync(1, NT);   // every input of stage s has been read
+            V* og = stage_g(s);
+#pragma unroll
+            for (int q = 0; q < IPT; ++q)
+                if (q < cnt) og[dst[q]] = gval[q];
         }
         fence_proxy_async_smem();
-        named_sync(1, NT);
+        named_sync(1, NT);       // the tile's output is staged
         if (*s_abort) break;
-        // Stage s is consumed; output buffer ob is complete.
-        if (!BWD) {
+        if constexpr (!BWD) {
             K* C = static_cast<K*>(p.ck);
             if (tid == 0) {
-                mbar_arrive(&empty[s]);
-                store_bulk(C, out_k(ob), in.gc, len, EK);
-                if constexpr (VB != 0) store_bulk(static_cast<V*>(p.cv), out_v(ob), in.gc, len, EV);
-                if constexpr (TAG) store_bulk(p.ctag, out_t(ob), in.gc, len, 4);
+                store_bulk(C, sk, in.gc, len, EK);
+                if constexpr (VB != 0) store_bulk(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV);
+                if constexpr (TAG) store_bulk(p.ctag, stage_t(s), in.gc, len, 4);
                 bulk_commit();
             } else if (tid <= 2 * EK) {
-                store_edges(C, out_k(ob), in.gc, len, EK, tid - 1);
+                store_edges(C, sk, in.gc, len, EK, tid - 1);
             } else if (VB != 0 && tid >= 32 && tid < 32 + 2 * EV) {
-                store_edges(static_cast<V*>(p.cv), out_v(ob), in.gc, len, EV, tid - 32);
+                store_edges(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV, tid - 32);
             } else if (TAG && tid >= 64 && tid < 64 + 8) {
-                store_edges(p.ctag, out_t(ob), in.gc, len, 4, tid - 64);
+                store_edges(p.ctag, stage_t(s), in.gc, len, 4, tid - 64);
             }
         } else {
             V* gA = static_cast<V*>(p.cv);
             V* gB = static_cast<V*>(p.cv2);
             const int pha = int(in.ga & (EV - 1));
-            const int ob_off = int(((pha + in.alen + EV - 1) / EV) * EV);
+            const int ob = ((pha + in.alen + EV - 1) / EV) * EV;
             if (tid == 0) {
-                mbar_arrive(&empty[s]);
-                store_bulk(gA, out_v(ob), in.ga, in.alen, EV);
-                store_bulk(gB, out_v(ob) + ob_off, in.gb, in.blen, EV);
+                store_bulk(gA, stage_g(s), in.ga, in.alen, EV);
+                store_bulk(gB, stage_g(s) + ob, in.gb, in.blen, EV);
                 bulk_commit();
             } else if (tid <= 2 * EV) {
-                store_edges(gA, out_v(ob), in.ga, in.alen, EV, tid - 1);
+                store_edges(gA, stage_g(s), in.ga, in.alen, EV, tid - 1);
             } else if (tid >= 32 && tid < 32 + 2 * EV) {
-                store_edges(gB, out_v(ob) + ob_off, in.gb, in.blen, EV, tid - 32);
+                store_edges(gB, stage_g(s) + ob, in.gb, in.blen, EV, tid - 32);
             }
+        }
+        if (tid == 0) {
+            // Hand the previous tile's stage back once its bulk store has read
+            // it (its edge stores finished before this iteration's barriers).
+            bulk_wait_read<1>();
+            if (it > 0) mbar_arrive(&empty[(it - 1) % NS]);
         }
     }
     if (*s_abort && tid == 0) {

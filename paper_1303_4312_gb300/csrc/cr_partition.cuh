@@ -91,21 +91,33 @@ __device__ __forceinline__ TileRec make_rec(int64_t a_base, int64_t b_base, int6
 }
 
 // Single merge: tile t covers output ranks [t*tile, min((t+1)*tile, m+n)).
+// A block of 256 threads co-ranks 256 consecutive tile boundaries (each
+// boundary once, Algorithm 1 over HBM) and writes the records of the 255
+// tiles between them; neighbouring blocks share one boundary.
 template <class K>
-__global__ void partition_single_kernel(const K* A, int64_t m, const K* B, int64_t n, int64_t tile,
-                                        int64_t ntiles, void* ws) {
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) partition_single_kernel(const K* A, int64_t m, const K* B,
+                                                               int64_t n, int64_t tile,
+                                                               int64_t ntiles, void* ws) {
+    __shared__ int64_t s_j[256];
+    const int64_t t = int64_t(blockIdx.x) * 255 + threadIdx.x;   // boundary index
     if (t == 0) {
         WsHeader* h = static_cast<WsHeader*>(ws);
         h->status = kDevOk;
         h->ntiles = ntiles;
     }
-    if (t >= ntiles) return;
-    const int64_t r0 = t * tile;
-    const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
-    int64_t j0, j1;
-    co_rank_pair(r0, r1, A, m, B, n, j0, j1);
-    ws_recs(ws)[t] = make_rec(0, 0, 0, r0, r1, j0, j1);
+    if (t <= ntiles) {
+        const int64_t r = t * tile < m + n ? t * tile : m + n;
+        CoRankState s = co_rank_begin(r, m, n);
+#pragma unroll 1
+        for (int it = 0; it < 128 && !s.done; ++it) co_rank_step(s, A, m, B, n);
+        s_j[threadIdx.x] = co_rank_end(s);
+    }
+    __syncthreads();
+    if (threadIdx.x < 255 && t < ntiles) {
+        const int64_t r0 = t * tile;
+        const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
+        ws_recs(ws)[t] = make_rec(0, 0, 0, r0, r1, s_j[threadIdx.x], s_j[threadIdx.x + 1]);
+    }
 }
 
 // One bottom-up merge-sort pass over X[0, N): pair q merges the runs
