@@ -90,32 +90,86 @@ __device__ __forceinline__ TileRec make_rec(int64_t a_base, int64_t b_base, int6
     return r;
 }
 
+// Co-rank of output rank i by a group of G lanes (mask `gmask`, this lane's
+// index `l` in the group): the largest j in [max(0, i-n), min(i, m)] for
+// which the first Lemma-1 condition holds (A[j-1] <= B[i-j], with B[n] =
+// +inf); the condition holds exactly for j <= j*, so G probes per round cut
+// the interval (G+1)-fold.
+template <class K, int G>
+__device__ __forceinline__ int64_t co_rank_group(const K* A, int64_t m, const K* B, int64_t n,
+                                                 int64_t i, int l, unsigned gmask, int gshift) {
+    int64_t lo = i - n > 0 ? i - n : 0;
+    int64_t hi = i < m ? i : m;
+#pragma unroll 1
+    for (int round = 0; round < 64 && hi > lo; ++round) {
+        const int64_t w = hi - lo;
+        const int64_t p = lo + ((int64_t(l) + 1) * w + G - 1) / G;   // in (lo, hi]
+        const int64_t k = i - p;                                     // in [0, n]
+        const bool c1 = (k >= n) || !(B[k] < A[p - 1]);
+        const unsigned ball = (__ballot_sync(gmask, c1) >> gshift) & ((1u << G) - 1u);
+        const int cnt = __popc(ball);   // the condition holds on a prefix of the probes
+        if (cnt == 0) {
+            hi = lo + (w + G - 1) / G - 1;
+        } else {
+            const int64_t plast = lo + (int64_t(cnt) * w + G - 1) / G;
+            if (cnt < G) hi = lo + ((int64_t(cnt) + 1) * w + G - 1) / G - 1;
+            lo = plast;
+        }
+    }
+    return lo;
+}
+
 // Single merge: tile t covers output ranks [t*tile, min((t+1)*tile, m+n)).
-// A block of 256 threads co-ranks 256 consecutive tile boundaries (each
-// boundary once, Algorithm 1 over HBM) and writes the records of the 255
-// tiles between them; neighbouring blocks share one boundary.
+// A block of 256 threads handles 256 consecutive tile boundaries (255 tiles;
+// neighbouring blocks share one boundary), in two steps:
+//  1. the producer-style warp 0 co-ranks the block's first and last boundary
+//     (16 lanes each, co_rank_group), giving the block's A interval
+//     [jb0, jb1] that contains every co-rank the block needs;
+//  2. every thread bisects that common interval for its own boundary on the
+//     first Lemma-1 condition.  All threads start from the same interval, so
+//     the top levels of their searches probe the same few positions (L1 and
+//     L2 hits) and only the last levels touch distinct DRAM sectors.
 template <class K>
 __global__ void __launch_bounds__(256) partition_single_kernel(const K* A, int64_t m, const K* B,
                                                                int64_t n, int64_t tile,
                                                                int64_t ntiles, void* ws) {
     __shared__ int64_t s_j[256];
-    const int64_t t = int64_t(blockIdx.x) * 255 + threadIdx.x;   // boundary index
+    __shared__ int64_t s_jb[2];
+    const int64_t mn = m + n;
+    const int64_t tb = int64_t(blockIdx.x) * 255;
+    const int64_t t = tb + threadIdx.x;   // boundary index
     if (t == 0) {
         WsHeader* h = static_cast<WsHeader*>(ws);
         h->status = kDevOk;
         h->ntiles = ntiles;
     }
+    if (threadIdx.x < 32) {
+        const int grp = threadIdx.x >> 4;
+        const int64_t tt = grp == 0 ? tb : (tb + 255 < ntiles ? tb + 255 : ntiles);
+        const int64_t i = tt * tile < mn ? tt * tile : mn;
+        const int64_t j = co_rank_group<K, 16>(A, m, B, n, i, threadIdx.x & 15,
+                                               0xFFFFu << (16 * grp), 16 * grp);
+        if ((threadIdx.x & 15) == 0) s_jb[grp] = j;
+    }
+    __syncthreads();
     if (t <= ntiles) {
-        const int64_t r = t * tile < m + n ? t * tile : m + n;
-        CoRankState s = co_rank_begin(r, m, n);
+        const int64_t i = t * tile < mn ? t * tile : mn;
+        // largest j in [jb0, jb1] with the first condition true at (j, i-j);
+        // k > n counts as true (B[n] = +inf), k < 0 as false (j > i).
+        int64_t lo = s_jb[0], hi = s_jb[1];
 #pragma unroll 1
-        for (int it = 0; it < 128 && !s.done; ++it) co_rank_step(s, A, m, B, n);
-        s_j[threadIdx.x] = co_rank_end(s);
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;   // > lo >= 0
+            const int64_t k = i - mid;
+            const bool c1 = k >= n || (k >= 0 && !(B[k] < A[mid - 1]));
+            if (c1) lo = mid; else hi = mid - 1;
+        }
+        s_j[threadIdx.x] = lo;
     }
     __syncthreads();
     if (threadIdx.x < 255 && t < ntiles) {
         const int64_t r0 = t * tile;
-        const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
+        const int64_t r1 = r0 + tile < mn ? r0 + tile : mn;
         ws_recs(ws)[t] = make_rec(0, 0, 0, r0, r1, s_j[threadIdx.x], s_j[threadIdx.x + 1]);
     }
 }

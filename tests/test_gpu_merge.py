@@ -212,8 +212,83 @@ def test_argument_errors_on_device():
         cr.merge(buf[:64], B, out=buf[:128])
     assert e.value.name == "CR_EALIAS"
     with pytest.raises(cr.CorankError) as e:
-        cr.merge(A, B, ws=torch.empty(256, dtype=torch.uint8, device="cuda"))
+        cr.merge(A, B, ws=torch.empty(128, dtype=torch.uint8, device="cuda"))
     assert e.value.name == "CR_ENOSPACE"
     with pytest.raises(cr.CorankError) as e:
         cr.co_rank(A, B, 129)
     assert e.value.name == "CR_EINVAL"
+
+
+@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+@pytest.mark.parametrize("vdt", [None, np.float32])
+def test_shared_corank_table_path(dt, vdt):
+    """The two-step form (cr_merge_partition, then cr_merge_tiles and
+    cr_merge_tiles_backward on the same tile table) against the oracle."""
+    import ctypes
+    from paper_1303_4312_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(105)
+    vb = np.dtype(vdt).itemsize if vdt else 0
+    kt = key_type(np.empty(0, dt))
+    code = _lib.KEY_TYPES[kt]
+    t = cr.tile_size(kt, vb)
+    for m, n in [(1, 0), (5 * t + 3, 2 * t - 1), (t, 7 * t), (123457, 98765)]:
+        A = sorted_keys(rng, m, dt, 300)
+        B = sorted_keys(rng, n, dt, 300)
+        Ad, Bd = dev(A), dev(B)
+        C = torch.empty(m + n, dtype=Ad.dtype, device="cuda")
+        need = ctypes.c_size_t()
+        _lib.check(lib.cr_merge_workspace_size(code, vb, m, n, ctypes.byref(need)))
+        ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream
+        _lib.check(lib.cr_merge_partition(code, vb, Ad.data_ptr(), m, Bd.data_ptr(), n,
+                                          ws.data_ptr(), ws.numel(), s))
+        if vdt is None:
+            _lib.check(lib.cr_merge_tiles(code, 0, Ad.data_ptr(), None, m, Bd.data_ptr(), None, n,
+                                          C.data_ptr(), None, None, ws.data_ptr(), ws.numel(), s))
+            torch.cuda.synchronize()
+            assert same_bits(host(C, dt), oracle.merge(A, B)[0])
+            continue
+        Av = rng.standard_normal(m).astype(vdt)
+        Bv = rng.standard_normal(n).astype(vdt)
+        Cv = torch.empty(m + n, dtype=torch.float32, device="cuda")
+        Avd, Bvd = dev(Av), dev(Bv)   # keep the device copies alive until the kernel ran
+        _lib.check(lib.cr_merge_tiles(code, vb, Ad.data_ptr(), Avd.data_ptr(), m,
+                                      Bd.data_ptr(), Bvd.data_ptr(), n, C.data_ptr(),
+                                      Cv.data_ptr(), None, ws.data_ptr(), ws.numel(), s))
+        gC = rng.standard_normal(m + n).astype(vdt)
+        gA = torch.empty(m, dtype=torch.float32, device="cuda")
+        gB = torch.empty(n, dtype=torch.float32, device="cuda")
+        gCd = dev(gC)
+        _lib.check(lib.cr_merge_tiles_backward(code, vb, Ad.data_ptr(), m, Bd.data_ptr(), n,
+                                               gCd.data_ptr(), gA.data_ptr() if m else None,
+                                               gB.data_ptr() if n else None, ws.data_ptr(),
+                                               ws.numel(), s))
+        torch.cuda.synchronize()
+        wk, wv, _ = oracle.merge_kv(A, Av, B, Bv)
+        ga, gb = oracle.merge_grad(A, B, gC)
+        assert same_bits(host(C, dt), wk)
+        assert same_bits(host(Cv, np.float32), wv)
+        assert same_bits(host(gA, np.float32), ga)
+        assert same_bits(host(gB, np.float32), gb)
+        cr.workspace_status(ws)
+
+
+@pytest.mark.parametrize("dt", [np.int32, np.int64])
+def test_streaming_merge_block_edges(dt):
+    """Sizes around the streaming kernel's block and chunk boundaries: a few
+    tiles per CTA, one tile per CTA, more CTAs than tiles, and inputs whose
+    ends fall inside a 16-byte unit."""
+    rng = np.random.default_rng(106)
+    t = cr.tile_size(key_type(np.empty(0, dt)))
+    for total in (t * 152 - 1, t * 304 + 5, t * 700 + 13, 3 * t + 1):
+        for frac in (0.0, 0.01, 0.5, 0.97, 1.0):
+            m = int(total * frac)
+            n = total - m
+            A = sorted_keys(rng, m, dt, None if frac == 0.5 else 7)
+            B = sorted_keys(rng, n, dt, None if frac == 0.5 else 7)
+            C, T = cr.merge(dev(A), dev(B), key_type=key_type(A), tag=True)
+            torch.cuda.synchronize()
+            want, src = oracle.merge(A, B)
+            assert same_bits(host(C, dt), want), (total, frac)
+            assert np.array_equal(host(T, np.uint32).astype(np.int64), src), (total, frac)
