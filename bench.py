@@ -66,6 +66,10 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--shift", type=int, default=0,
                    help="divide every workload size by 2^shift (for quick runs)")
+    p.add_argument("--workload", default=WORKLOAD,
+                   choices=[WORKLOAD, "single_tag", "kv", "batched", "merge_sort"],
+                   help="the default is the headline workload; the others measure the "
+                        "remaining rows of the path (one JSON line each)")
     return p.parse_args()
 
 
@@ -376,6 +380,209 @@ def run_e2e(args, merges, lib, dev, stream, dist, world):
 
 
 # ---------------------------------------------------------------------------
+# the other rows of the path, one measured line each
+# ---------------------------------------------------------------------------
+class KernelTimer:
+    """CUDA events around each launch of a step; sums per label."""
+
+    def __init__(self, stream):
+        import torch
+        self.torch = torch
+        self.stream = stream
+        self.marks = []
+
+    def mark(self, label=None):
+        ev = self.torch.cuda.Event(enable_timing=True)
+        ev.record(self.stream)
+        self.marks.append((label, ev))
+
+    def totals(self):
+        out = {}
+        for (_, a), (label, b) in zip(self.marks, self.marks[1:]):
+            if label is not None:
+                out[label] = out.get(label, 0.0) + a.elapsed_time(b)
+        return out
+
+
+def _l2_flush_buffer(dev):
+    import torch
+    return torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+
+def run_row(args):
+    import torch
+    from paper_1303_4312_gb300 import _lib, api, build
+    from paper_1303_4312_gb300 import workloads as W
+    build.build()
+    lib = _lib.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    peak, peak_kind = measured_peak()
+    K, Wm = args.steps, args.warmup
+    ptr = lambda t: None if t is None else t.data_ptr()
+    res = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": Wm,
+           "higher_is_better": True, "data": "synthetic (seeded)", "peak_gbs": peak,
+           "peak_source": peak_kind}
+
+    def finish(timer_totals, alg, name, elems, extra=None):
+        step_ms = sum(timer_totals.values()) / K
+        res.update({"value": elems / (step_ms / 1e3), "ms_per_step": step_ms,
+                    "config": {"workload": name, "elements_per_step": elems,
+                               "size_shift": args.shift}})
+        kern = {}
+        for label, ms in timer_totals.items():
+            b = alg.get(label)
+            kern[label] = {"ms": round(ms / K, 4)}
+            if b:
+                gbs = b / (ms / K / 1e3) / 1e9
+                kern[label].update({"gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                                    "alg_bytes": b})
+        res["kernels"] = kern
+        if extra:
+            res.update(extra)
+        return res
+
+    if args.workload == "single_tag":
+        A, B = W.single_i32_tag(seed=1, shift=args.shift)
+        A, B = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        m, n = A.numel(), B.numel()
+        C = torch.empty(m + n, dtype=torch.int32, device=dev)
+        T = torch.empty(m + n, dtype=torch.int32, device=dev)
+        ws = torch.empty(api.merge_workspace_bytes("i32", 0, m, n), dtype=torch.uint8, device=dev)
+        flush = _l2_flush_buffer(dev)
+        timer = KernelTimer(stream)
+        for k in range(Wm + K):
+            flush.fill_(k & 0xFF)      # L2 flush between steps (outside the timed marks)
+            if k >= Wm:
+                timer.mark()
+            _lib.check(lib.cr_merge_partition(0, 0, ptr(A), m, ptr(B), n, ptr(ws), ws.numel(), sp))
+            if k >= Wm:
+                timer.mark("partition")
+            _lib.check(lib.cr_merge_tiles(0, 0, ptr(A), None, m, ptr(B), None, n, ptr(C), None,
+                                          ptr(T), ptr(ws), ws.numel(), sp))
+            if k >= Wm:
+                timer.mark("tiles_keys_tags")
+            if k >= Wm:
+                timer.marks.append((None, timer.marks[-1][1]))
+        torch.cuda.synchronize()
+        api.workspace_status(ws)
+        tot = {k: v for k, v in timer.totals().items()}
+        return finish(tot, {"tiles_keys_tags": 12 * (m + n)}, "single_i32_tag", m + n,
+                      {"l2": "flushed between steps (256 MB write)"})
+
+    if args.workload == "kv":
+        Ak, Av, Bk, Bv = W.t_kv_u32_f32(device=dev, shift=args.shift)
+        m, n = Ak.numel(), Bk.numel()
+        Ck = torch.empty(m + n, dtype=torch.int32, device=dev)
+        Cv = torch.empty(m + n, dtype=torch.float32, device=dev)
+        gC = torch.randn(m + n, device=dev)
+        gA = torch.empty(m, device=dev)
+        gB = torch.empty(n, device=dev)
+        ws = torch.empty(api.merge_workspace_bytes("u32", 4, m, n), dtype=torch.uint8, device=dev)
+        timer = KernelTimer(stream)
+        for k in range(Wm + K):
+            t = k >= Wm
+            if t:
+                timer.mark()
+            _lib.check(lib.cr_merge_partition(1, 4, ptr(Ak), m, ptr(Bk), n, ptr(ws), ws.numel(), sp))
+            if t:
+                timer.mark("fwd_partition")
+            _lib.check(lib.cr_merge_tiles(1, 4, ptr(Ak), ptr(Av), m, ptr(Bk), ptr(Bv), n, ptr(Ck),
+                                          ptr(Cv), None, ptr(ws), ws.numel(), sp))
+            if t:
+                timer.mark("fwd_tiles")
+            # backward recomputes the partition from the keys (nothing stored)
+            _lib.check(lib.cr_merge_partition(1, 4, ptr(Ak), m, ptr(Bk), n, ptr(ws), ws.numel(), sp))
+            if t:
+                timer.mark("bwd_partition")
+            _lib.check(lib.cr_merge_tiles_backward(1, 4, ptr(Ak), m, ptr(Bk), n, ptr(gC), ptr(gA),
+                                                   ptr(gB), ptr(ws), ws.numel(), sp))
+            if t:
+                timer.mark("bwd_tiles")
+                timer.marks.append((None, timer.marks[-1][1]))
+        torch.cuda.synchronize()
+        api.workspace_status(ws)
+        tot = timer.totals()
+        N = m + n
+        fwd_ms = (tot["fwd_partition"] + tot["fwd_tiles"]) / K
+        bwd_ms = (tot["bwd_partition"] + tot["bwd_tiles"]) / K
+        return finish(tot, {"fwd_tiles": 16 * N, "bwd_tiles": 12 * N}, "kv_u32_f32", N,
+                      {"fwd": {"ms": round(fwd_ms, 4), "elements_per_s": N / (fwd_ms / 1e3),
+                               "gbs": round(16 * N / (fwd_ms / 1e3) / 1e9, 1)},
+                       "bwd": {"ms": round(bwd_ms, 4), "elements_per_s": N / (bwd_ms / 1e3),
+                               "gbs": round(12 * N / (bwd_ms / 1e3) / 1e9, 1)}})
+
+    if args.workload == "batched":
+        a_off, b_off, A, Av, B, Bv = W.t_batched_i32_f32(device=dev)
+        ao = torch.from_numpy(a_off).to(dev)
+        bo = torch.from_numpy(b_off).to(dev)
+        at, bt = A.numel(), B.numel()
+        nseg = len(a_off) - 1
+        Ck = torch.empty(at + bt, dtype=torch.int32, device=dev)
+        Cv = torch.empty(at + bt, dtype=torch.float32, device=dev)
+        gC = torch.randn(at + bt, device=dev)
+        gA = torch.empty(at, device=dev)
+        gB = torch.empty(bt, device=dev)
+        need = ctypes.c_size_t()
+        _lib.check(lib.cr_batched_workspace_size(0, 4, nseg, at, bt, ctypes.byref(need)))
+        ws = torch.empty(need.value, dtype=torch.uint8, device=dev)
+        timer = KernelTimer(stream)
+        for k in range(Wm + K):
+            t = k >= Wm
+            if t:
+                timer.mark()
+            _lib.check(lib.cr_batched_merge_kv(0, 4, nseg, ptr(ao), ptr(bo), ptr(A), ptr(Av), at,
+                                               ptr(B), ptr(Bv), bt, ptr(Ck), ptr(Cv), ptr(ws),
+                                               ws.numel(), sp))
+            if t:
+                timer.mark("fwd")
+            _lib.check(lib.cr_batched_merge_kv_backward(0, 4, nseg, ptr(ao), ptr(bo), ptr(A), at,
+                                                        ptr(B), bt, ptr(gC), ptr(gA), ptr(gB),
+                                                        ptr(ws), ws.numel(), sp))
+            if t:
+                timer.mark("bwd")
+                timer.marks.append((None, timer.marks[-1][1]))
+        torch.cuda.synchronize()
+        api.workspace_status(ws)
+        tot = timer.totals()
+        N = at + bt
+        return finish(tot, {"fwd": 16 * N, "bwd": 12 * N}, "batched_i32_f32", N,
+                      {"segments": nseg, "note": "fwd/bwd include the segment scan and "
+                       "partition launches (3 kernels each)"})
+
+    if args.workload == "merge_sort":
+        X, Xv = W.t_sort_u64_f32(device=dev, shift=args.shift)
+        N = X.numel()
+        plan = api.MergeSortPlan(N, 1024, X.dtype, Xv.dtype, dev, key_type="u64", graph=True)
+        gY = torch.randn(N, device=dev)
+        plan.forward(X, Xv)       # captures the forward graph
+        plan.backward(gY)         # captures the backward graph
+        timer = KernelTimer(stream)
+        for k in range(Wm + K):
+            t = k >= Wm
+            plan.keys[0].copy_(X)
+            plan.vals[0].copy_(Xv)
+            plan.grads[plan.passes & 1].copy_(gY)
+            if t:
+                timer.mark()
+            plan._gf.replay()
+            if t:
+                timer.mark("fwd_graph")
+            plan._gb.replay()
+            if t:
+                timer.mark("bwd_graph")
+                timer.marks.append((None, timer.marks[-1][1]))
+        torch.cuda.synchronize()
+        tot = timer.totals()
+        P = plan.passes
+        return finish(tot, {"fwd_graph": 24 * N * P, "bwd_graph": 16 * N * P}, "sort_u64_f32",
+                      N, {"passes": P, "note": "each graph replays its passes' partition and "
+                          "tile-merge launches; bytes are per pass, times passes"})
+    raise ValueError(args.workload)
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle as a baseline / the reference arm
 # ---------------------------------------------------------------------------
 def _host_inputs(merges):
@@ -446,6 +653,8 @@ def main():
     rank, world, local, dist = dist_setup(args.gpus)
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.workload != WORKLOAD:
+        line = run_row(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, local, dist)
     if rank == 0 and line is not None:

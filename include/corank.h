@@ -83,10 +83,30 @@ const char* cr_last_error(void);
 int cr_abi_version(void);
 
 /* Elements per tile (TILE) the merge kernels use for this key type and
- * payload width: every tile of a merge carries exactly TILE output elements
- * except the last one (per segment, for batched calls).  Returns 0 for an
- * invalid combination. */
+ * payload width under the current tile shape: every tile of a merge carries
+ * exactly TILE output elements except the last one (per segment, for batched
+ * calls).  Returns 0 for an invalid combination. */
 int64_t cr_tile_size(int key_type, int val_bytes);
+
+/* Tile shapes.  A tile is merged by NT consumer threads of IPT elements each
+ * (TILE = NT * IPT; Algorithm 2's equal blocks, one per tile, and equal
+ * per-thread shares inside it, Proposition 2).  Several shapes are compiled;
+ * the one used is chosen per (key size, payload width) -- for example by the
+ * autotuner -- and applies to every later call of that combination in the
+ * process.  Workspace sizes depend on it: query them after choosing, and do
+ * not change the shape between cr_merge_partition and the cr_merge_tiles*
+ * calls that use its table (a table made for another TILE is refused on the
+ * device: CR_EINTERNAL from cr_workspace_status).  Changing the shape while
+ * calls of that combination are being issued on other host threads is a
+ * race. */
+int cr_tile_shape_count(void);
+/* NT and IPT of shape `shape` (CR_EINVAL if out of range). */
+cr_status cr_tile_shape_info(int shape, int* nt, int* ipt);
+/* Select `shape` for this key type and payload width (0, 4, 8);
+ * CR_EUNSUPPORTED if its shared-memory footprint does not fit. */
+cr_status cr_set_tile_shape(int key_type, int val_bytes, int shape);
+/* Current shape for this key type and payload width (-1 if invalid). */
+int cr_get_tile_shape(int key_type, int val_bytes);
 
 /* ------------------------------------------------------------------------
  * co_rank -- Algorithm 1 (Section 2), Lemma 1.
@@ -227,9 +247,10 @@ cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
  *     before any stream capture begins.
- *   - Size limit: m + n at most 131064 tiles (cr_tile_size(key_type, 0)
- *     elements each): 503,285,760 elements for 4-byte keys, 251,642,880 for
- *     8-byte keys.  Larger requests return CR_EINVAL and launch nothing.
+ *   - Size limit: m + n at most 131064 tiles of cr_tile_size(key_type, 0)
+ *     elements each (with the default shapes: 503,285,760 elements for 4-byte
+ *     keys, 234,866,688 for 8-byte keys).  Larger requests return CR_EINVAL
+ *     and launch nothing.
  *   - Every call shares the array; calls whose kernels overlap on the GPU
  *     (other streams, other host threads) race and may give wrong output, so
  *     serialise them on one stream.  Device-side status is not reported for

@@ -13,7 +13,7 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libcorank.so")
 
-_lock = threading.Lock()
+_lock = threading.RLock()
 _lib = None
 
 P = ctypes.c_void_p
@@ -27,6 +27,10 @@ SIGNATURES = {
     "cr_last_error": ([], ctypes.c_char_p),
     "cr_abi_version": ([], INT),
     "cr_tile_size": ([INT, INT], I64),
+    "cr_tile_shape_count": ([], INT),
+    "cr_tile_shape_info": ([INT, ctypes.POINTER(INT), ctypes.POINTER(INT)], INT),
+    "cr_set_tile_shape": ([INT, INT, INT], INT),
+    "cr_get_tile_shape": ([INT, INT], INT),
     "cr_co_rank": ([INT, P, I64, P, I64, I64, P, P], INT),
     "cr_co_rank_many": ([INT, P, I64, P, I64, P, I64, P, P, P], INT),
     "cr_merge_workspace_size": ([INT, INT, I64, I64, ctypes.POINTER(SZ)], INT),
@@ -79,6 +83,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
                 f.argtypes = args
                 f.restype = res
             _lib = lib
+            # select the tile shapes tuned for this GPU, when a table exists
+            from . import autotune
+            autotune.apply(lib)
     return _lib
 
 

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <atomic>
 
 #include <cuda_runtime.h>
 
@@ -173,17 +174,19 @@ cr_status check_backward(int key_type, int vb, const void* Ak, int64_t m, const 
     return check_no_alias(outs, 2, ins, 3);
 }
 
-int64_t single_tiles(int key_type, int vb, int64_t m, int64_t n, int64_t* tile_out) {
-    const int64_t tile = cr::tile_for(key_bytes(key_type), vb);
+int shape_of(int key_type, int vb) { return cr::current_shape(key_bytes(key_type), vb); }
+
+int64_t single_tiles(int shape, int64_t m, int64_t n, int64_t* tile_out) {
+    const int64_t tile = cr::tile_of_shape(shape);
     if (tile_out) *tile_out = tile;
     return (m + n + tile - 1) / tile;
 }
 
 // Grid-level co-rank pass of a single merge (writes the tile table).
-cr_status launch_partition(int key_type, int vb, const void* Ak, int64_t m, const void* Bk,
+cr_status launch_partition(int shape, int key_type, const void* Ak, int64_t m, const void* Bk,
                            int64_t n, void* ws, size_t ws_bytes, cudaStream_t st) {
     int64_t tile = 0;
-    const int64_t ntiles = single_tiles(key_type, vb, m, n, &tile);
+    const int64_t ntiles = single_tiles(shape, m, n, &tile);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     cudaError_t e = by_key(key_type, [&](auto ops) {
         return ops.partition_single(Ak, m, Bk, n, tile, ntiles, ws, st);
@@ -192,10 +195,10 @@ cr_status launch_partition(int key_type, int vb, const void* Ak, int64_t m, cons
     return CR_OK;
 }
 
-cr_status launch_tiles(int key_type, int vb, const void* Ak, const void* Av, int64_t m,
+cr_status launch_tiles(int shape, int key_type, int vb, const void* Ak, const void* Av, int64_t m,
                        const void* Bk, const void* Bv, int64_t n, void* Ck, void* Cv,
                        uint32_t* tag, void* ws, size_t ws_bytes, cudaStream_t st) {
-    const int64_t ntiles = single_tiles(key_type, vb, m, n, nullptr);
+    const int64_t ntiles = single_tiles(shape, m, n, nullptr);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     cr::MergeArgs a{};
     a.ak = Ak;
@@ -211,16 +214,16 @@ cr_status launch_tiles(int key_type, int vb, const void* Ak, const void* Av, int
     a.tag_b = m;
     a.ws = ws;
     cudaError_t e = by_key(key_type, [&](auto ops) {
-        return ops.merge_fwd(vb, tag != nullptr, a, ntiles, st);
+        return ops.merge_fwd(shape, vb, tag != nullptr, a, ntiles, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "tile merge launch");
     return CR_OK;
 }
 
-cr_status launch_tiles_backward(int key_type, int vb, const void* Ak, int64_t m, const void* Bk,
-                                int64_t n, const void* gC, void* gA, void* gB, void* ws,
-                                size_t ws_bytes, cudaStream_t st) {
-    const int64_t ntiles = single_tiles(key_type, vb, m, n, nullptr);
+cr_status launch_tiles_backward(int shape, int key_type, int vb, const void* Ak, int64_t m,
+                                const void* Bk, int64_t n, const void* gC, void* gA, void* gB,
+                                void* ws, size_t ws_bytes, cudaStream_t st) {
+    const int64_t ntiles = single_tiles(shape, m, n, nullptr);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     cr::MergeArgs a{};
     a.ak = Ak;
@@ -232,7 +235,8 @@ cr_status launch_tiles_backward(int key_type, int vb, const void* Ak, int64_t m,
     a.b_total = n;
     a.c_total = m + n;
     a.ws = ws;
-    cudaError_t e = by_key(key_type, [&](auto ops) { return ops.merge_bwd(vb, a, ntiles, st); });
+    cudaError_t e =
+        by_key(key_type, [&](auto ops) { return ops.merge_bwd(shape, vb, a, ntiles, st); });
     if (e != cudaSuccess) return cuda_fail(e, "tile backward launch");
     return CR_OK;
 }
@@ -242,6 +246,14 @@ cr_status launch_tiles_backward(int key_type, int vb, const void* Ak, int64_t m,
 // Lets other translation units of the library report through cr_last_error().
 namespace cr {
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+// Selected tile shape per (key size 4|8, payload width 0|4|8).  Defaults:
+// 256 x 15 for 4-byte keys without payload, 256 x 7 otherwise.
+static std::atomic<int> g_shape[2][3] = {{{0}, {2}, {2}}, {{2}, {2}, {2}}};
+
+int current_shape(int key_bytes, int vb) {
+    return g_shape[key_bytes == 8 ? 1 : 0][vb / 4].load(std::memory_order_relaxed);
+}
 }  // namespace cr
 
 extern "C" {
@@ -269,7 +281,34 @@ int cr_abi_version(void) { return 100; }
 int64_t cr_tile_size(int key_type, int val_bytes) {
     const int ks = key_bytes(key_type);
     if (ks == 0) return 0;
-    return cr::tile_for(ks, val_bytes);
+    if (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) return 0;
+    return cr::tile_of_shape(cr::current_shape(ks, val_bytes));
+}
+
+int cr_tile_shape_count(void) { return cr::kNumShapes; }
+
+cr_status cr_tile_shape_info(int shape, int* nt, int* ipt) {
+    if (shape < 0 || shape >= cr::kNumShapes) return fail(CR_EINVAL, "no tile shape %d", shape);
+    if (nt) *nt = cr::kShapes[shape].nt;
+    if (ipt) *ipt = cr::kShapes[shape].ipt;
+    return ok();
+}
+
+cr_status cr_set_tile_shape(int key_type, int val_bytes, int shape) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, true));
+    const int ks = key_bytes(key_type);
+    if (!cr::shape_available(ks, val_bytes, shape))
+        return fail(CR_EUNSUPPORTED, "tile shape %d does not fit %d-byte keys with %d-byte payloads",
+                    shape, ks, val_bytes);
+    cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4].store(shape, std::memory_order_relaxed);
+    return ok();
+}
+
+int cr_get_tile_shape(int key_type, int val_bytes) {
+    const int ks = key_bytes(key_type);
+    if (ks == 0 || (val_bytes != 0 && val_bytes != 4 && val_bytes != 8)) return -1;
+    return cr::current_shape(ks, val_bytes);
 }
 
 cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int64_t n, int64_t k,
@@ -319,8 +358,7 @@ cr_status cr_merge_workspace_size(int key_type, int val_bytes, int64_t m, int64_
     CR_TRY(check_vb(val_bytes, true));
     if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
     if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
-    const int64_t tile = cr::tile_for(key_bytes(key_type), val_bytes);
-    *bytes = single_ws_bytes((m + n + tile - 1) / tile);
+    *bytes = single_ws_bytes(single_tiles(shape_of(key_type, val_bytes), m, n, nullptr));
     return ok();
 }
 
@@ -337,9 +375,10 @@ cr_status cr_stable_merge_kv(int key_type, int val_bytes, const void* Ak, const 
     CR_TRY(check_forward(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag));
     if (m + n == 0) return ok();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CR_TRY(launch_partition(key_type, val_bytes, Ak, m, Bk, n, ws, ws_bytes, st));
-    CR_TRY(launch_tiles(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag, ws, ws_bytes,
-                        st));
+    const int shape = shape_of(key_type, val_bytes);
+    CR_TRY(launch_partition(shape, key_type, Ak, m, Bk, n, ws, ws_bytes, st));
+    CR_TRY(launch_tiles(shape, key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag, ws,
+                        ws_bytes, st));
     return ok();
 }
 
@@ -349,8 +388,10 @@ cr_status cr_stable_merge_kv_backward(int key_type, int val_bytes, const void* A
     CR_TRY(check_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB));
     if (m + n == 0) return ok();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CR_TRY(launch_partition(key_type, val_bytes, Ak, m, Bk, n, ws, ws_bytes, st));
-    CR_TRY(launch_tiles_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB, ws, ws_bytes, st));
+    const int shape = shape_of(key_type, val_bytes);
+    CR_TRY(launch_partition(shape, key_type, Ak, m, Bk, n, ws, ws_bytes, st));
+    CR_TRY(launch_tiles_backward(shape, key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB, ws,
+                                 ws_bytes, st));
     return ok();
 }
 
@@ -363,7 +404,7 @@ cr_status cr_merge_partition(int key_type, int val_bytes, const void* A, int64_t
     CR_TRY(check_arr({A, m, ks, "A"}));
     CR_TRY(check_arr({B, n, ks, "B"}));
     if (m + n == 0) return ok();
-    CR_TRY(launch_partition(key_type, val_bytes, A, m, B, n, ws, ws_bytes,
+    CR_TRY(launch_partition(shape_of(key_type, val_bytes), key_type, A, m, B, n, ws, ws_bytes,
                             static_cast<cudaStream_t>(stream)));
     return ok();
 }
@@ -373,8 +414,8 @@ cr_status cr_merge_tiles(int key_type, int val_bytes, const void* Ak, const void
                          uint32_t* C_tag, void* ws, size_t ws_bytes, cr_stream stream) {
     CR_TRY(check_forward(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag));
     if (m + n == 0) return ok();
-    CR_TRY(launch_tiles(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag, ws, ws_bytes,
-                        static_cast<cudaStream_t>(stream)));
+    CR_TRY(launch_tiles(shape_of(key_type, val_bytes), key_type, val_bytes, Ak, Av, m, Bk, Bv, n,
+                        Ck, Cv, C_tag, ws, ws_bytes, static_cast<cudaStream_t>(stream)));
     return ok();
 }
 
@@ -383,8 +424,8 @@ cr_status cr_merge_tiles_backward(int key_type, int val_bytes, const void* Ak, i
                                   void* ws, size_t ws_bytes, cr_stream stream) {
     CR_TRY(check_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB));
     if (m + n == 0) return ok();
-    CR_TRY(launch_tiles_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB, ws, ws_bytes,
-                                 static_cast<cudaStream_t>(stream)));
+    CR_TRY(launch_tiles_backward(shape_of(key_type, val_bytes), key_type, val_bytes, Ak, m, Bk,
+                                 n, gC, gA, gB, ws, ws_bytes, static_cast<cudaStream_t>(stream)));
     return ok();
 }
 
@@ -394,7 +435,7 @@ cr_status cr_batched_workspace_size(int key_type, int val_bytes, int64_t nseg, i
     CR_TRY(check_vb(val_bytes, true));
     if (nseg < 0 || a_total < 0 || b_total < 0) return fail(CR_EINVAL, "negative size");
     if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
-    const int64_t tile = cr::tile_for(key_bytes(key_type), val_bytes);
+    const int64_t tile = cr::tile_of_shape(shape_of(key_type, val_bytes));
     *bytes = batched_ws_bytes(batched_max_tiles(tile, nseg, a_total, b_total), nseg);
     return ok();
 }
@@ -431,7 +472,8 @@ cr_status batched_common(bool backward, int key_type, int val_bytes, int64_t nse
         for (const Arr& a : outs) CR_TRY(check_arr(a));
         CR_TRY(check_no_alias(outs, 2, ins, 3));
     }
-    const int64_t tile = cr::tile_for(ks, vb);
+    const int shape = shape_of(key_type, vb);
+    const int64_t tile = cr::tile_of_shape(shape);
     const int64_t max_tiles = batched_max_tiles(tile, nseg, a_total, b_total);
     CR_TRY(check_ws(ws, ws_bytes, batched_ws_bytes(max_tiles, nseg)));
     int64_t* prefix = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + cr::kHeaderBytes +
@@ -454,8 +496,8 @@ cr_status batched_common(bool backward, int key_type, int val_bytes, int64_t nse
         cudaError_t r = ops.partition_batched(Ak, Bk, a_off, b_off, nseg, a_total, b_total, tile,
                                               max_tiles, ws, prefix, st);
         if (r != cudaSuccess) return r;
-        return backward ? ops.merge_bwd(vb, a, max_tiles, st)
-                        : ops.merge_fwd(vb, false, a, max_tiles, st);
+        return backward ? ops.merge_bwd(shape, vb, a, max_tiles, st)
+                        : ops.merge_fwd(shape, vb, false, a, max_tiles, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "batched merge launch");
     return ok();
@@ -484,7 +526,8 @@ cr_status pass_common(bool backward, int key_type, int val_bytes, const void* X,
         CR_TRY(check_no_alias(outs, 1, ins, 2));
     }
     if (N == 0) return ok();
-    const int64_t tile = cr::tile_for(ks, vb);
+    const int shape = shape_of(key_type, vb);
+    const int64_t tile = cr::tile_of_shape(shape);
     const int64_t ntiles = cr::pass_tiles(N, width, tile, nullptr, nullptr);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -505,7 +548,8 @@ cr_status pass_common(bool backward, int key_type, int val_bytes, const void* X,
         int64_t nt = 0;
         cudaError_t r = ops.partition_pass(X, N, width, tile, ws, &nt, st);
         if (r != cudaSuccess) return r;
-        return backward ? ops.merge_bwd(vb, a, nt, st) : ops.merge_fwd(vb, false, a, nt, st);
+        return backward ? ops.merge_bwd(shape, vb, a, nt, st)
+                        : ops.merge_fwd(shape, vb, false, a, nt, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "merge pass launch");
     return ok();
@@ -538,7 +582,7 @@ cr_status cr_merge_pass_workspace_size(int key_type, int val_bytes, int64_t N, i
     CR_TRY(check_vb(val_bytes, true));
     if (N < 0 || width < 1) return fail(CR_EINVAL, "bad size or width");
     if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
-    const int64_t tile = cr::tile_for(key_bytes(key_type), val_bytes);
+    const int64_t tile = cr::tile_of_shape(shape_of(key_type, val_bytes));
     *bytes = single_ws_bytes(cr::pass_tiles(N, width, tile, nullptr, nullptr));
     return ok();
 }

@@ -18,7 +18,7 @@ constexpr int kHeaderBytes = 256;
 
 struct WsHeader {
     int32_t status;      // device status (kDev*), 0 = ok
-    int32_t pad0;
+    int32_t tile;        // TILE the table was made for (checked by the merge kernel)
     int64_t ntiles;      // tiles of the current call (written by the partition kernel)
 };
 

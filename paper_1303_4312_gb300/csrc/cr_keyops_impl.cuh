@@ -44,44 +44,62 @@ cudaError_t launch_shape(Kern kern, int threads, size_t smem, LaunchShape* cache
     return cudaSuccess;
 }
 
-template <class K, int VB, bool TAG, bool BWD>
-cudaError_t launch_merge(const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
-    constexpr int NT = TileShape<int(sizeof(K)), VB>::NT;
-    constexpr int IPT = TileShape<int(sizeof(K)), VB>::IPT;
-    constexpr int NS = Stages<int(sizeof(K)), VB, TAG, BWD>::NS;
-    constexpr int MINB = Stages<int(sizeof(K)), VB, TAG, BWD>::MINB;
-    using L = Layout<K, VB, TAG, NT, IPT, NS, BWD>;
-    auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, NS, MINB, BWD>;
-    static LaunchShape cache[kMaxDevices];
-    static std::once_flag once[kMaxDevices];
-    LaunchShape sh;
-    cudaError_t e = launch_shape(kern, NT + 32, L::TOTAL, cache, once, sh);
-    if (e != cudaSuccess) return e;
-    if (max_tiles <= 0) return cudaSuccess;
-    int64_t grid = int64_t(sh.sms) * sh.blocks_per_sm;
-    if (grid > max_tiles) grid = max_tiles;
-    kern<<<unsigned(grid), NT + 32, L::TOTAL, st>>>(a);
-    return cudaGetLastError();
+template <class K, int VB, bool TAG, bool BWD, int S>
+cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
+    constexpr int KS = int(sizeof(K));
+    if constexpr (!Stages<KS, VB, TAG, BWD, S>::FITS) {
+        return cudaErrorInvalidConfiguration;
+    } else {
+        constexpr int NT = ShapeAt<S>::NT;
+        constexpr int IPT = ShapeAt<S>::IPT;
+        constexpr int NS = Stages<KS, VB, TAG, BWD, S>::NS;
+        constexpr int MINB = Stages<KS, VB, TAG, BWD, S>::MINB;
+        using L = Layout<K, VB, TAG, NT, IPT, NS, BWD>;
+        auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, NS, MINB, BWD>;
+        static LaunchShape cache[kMaxDevices];
+        static std::once_flag once[kMaxDevices];
+        LaunchShape sh;
+        cudaError_t e = launch_shape(kern, NT + 32, L::TOTAL, cache, once, sh);
+        if (e != cudaSuccess) return e;
+        if (max_tiles <= 0) return cudaSuccess;
+        int64_t grid = int64_t(sh.sms) * sh.blocks_per_sm;
+        if (grid > max_tiles) grid = max_tiles;
+        kern<<<unsigned(grid), NT + 32, L::TOTAL, st>>>(a);
+        return cudaGetLastError();
+    }
 }
 
-template <class K>
-cudaError_t KeyOps<K>::merge_fwd(int vb, bool tag, const MergeArgs& a, int64_t max_tiles,
-                                 cudaStream_t st) {
-    switch (vb * 2 + (tag ? 1 : 0)) {
-        case 0: return launch_merge<K, 0, false, false>(a, max_tiles, st);
-        case 1: return launch_merge<K, 0, true, false>(a, max_tiles, st);
-        case 8: return launch_merge<K, 4, false, false>(a, max_tiles, st);
-        case 9: return launch_merge<K, 4, true, false>(a, max_tiles, st);
-        case 16: return launch_merge<K, 8, false, false>(a, max_tiles, st);
-        case 17: return launch_merge<K, 8, true, false>(a, max_tiles, st);
+template <class K, int VB, bool TAG, bool BWD>
+cudaError_t launch_merge(int shape, const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
+    static_assert(kNumShapes == 4, "dispatch below lists every shape");
+    switch (shape) {
+        case 0: return launch_merge_shape<K, VB, TAG, BWD, 0>(a, max_tiles, st);
+        case 1: return launch_merge_shape<K, VB, TAG, BWD, 1>(a, max_tiles, st);
+        case 2: return launch_merge_shape<K, VB, TAG, BWD, 2>(a, max_tiles, st);
+        case 3: return launch_merge_shape<K, VB, TAG, BWD, 3>(a, max_tiles, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <class K>
-cudaError_t KeyOps<K>::merge_bwd(int vb, const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
-    if (vb == 4) return launch_merge<K, 4, false, true>(a, max_tiles, st);
-    if (vb == 8) return launch_merge<K, 8, false, true>(a, max_tiles, st);
+cudaError_t KeyOps<K>::merge_fwd(int shape, int vb, bool tag, const MergeArgs& a,
+                                 int64_t max_tiles, cudaStream_t st) {
+    switch (vb * 2 + (tag ? 1 : 0)) {
+        case 0: return launch_merge<K, 0, false, false>(shape, a, max_tiles, st);
+        case 1: return launch_merge<K, 0, true, false>(shape, a, max_tiles, st);
+        case 8: return launch_merge<K, 4, false, false>(shape, a, max_tiles, st);
+        case 9: return launch_merge<K, 4, true, false>(shape, a, max_tiles, st);
+        case 16: return launch_merge<K, 8, false, false>(shape, a, max_tiles, st);
+        case 17: return launch_merge<K, 8, true, false>(shape, a, max_tiles, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_bwd(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                 cudaStream_t st) {
+    if (vb == 4) return launch_merge<K, 4, false, true>(shape, a, max_tiles, st);
+    if (vb == 8) return launch_merge<K, 8, false, true>(shape, a, max_tiles, st);
     return cudaErrorInvalidValue;
 }
 

@@ -10,46 +10,70 @@
 
 namespace cr {
 
-// Tile shape per key size and payload width: consumer threads NT and items per
-// thread IPT (odd, so that a warp's stride-IPT shared-memory accesses fall in
-// distinct banks).  TILE = NT * IPT is the same for the forward and the
-// backward kernel of a (key, payload) pair.
-template <int KS, int VB> struct TileShape { static constexpr int NT = 256, IPT = 7; };
-template <> struct TileShape<4, 0> { static constexpr int NT = 256, IPT = 15; };
+// Tile shapes: NT consumer threads times IPT items per thread (IPT odd, so
+// that a warp's stride-IPT shared-memory accesses fall in distinct banks).
+// Every shape is compiled for every key and payload width it fits; which one
+// a call uses is a runtime choice per (key size, payload width), set through
+// cr_set_tile_shape (the autotuner sweeps them).  TILE = NT * IPT is shared
+// by the forward and the backward kernel of a (key, payload) pair, so one
+// tile table serves both.
+struct ShapeDesc {
+    int nt, ipt;
+};
+constexpr int kNumShapes = 4;
+constexpr ShapeDesc kShapes[kNumShapes] = {{256, 15}, {128, 31}, {256, 7}, {128, 15}};
 
-// Stages in the shared-memory ring and the CTAs per SM they leave room for:
-// four stages when a stage is at most 16 KB (three CTAs per SM), else three.
-template <int KS, int VB, bool TAG, bool BWD> struct Stages {
-    static constexpr int TILE = TileShape<KS, VB>::NT * TileShape<KS, VB>::IPT;
-    static constexpr int BYTES = TILE * (KS + VB + (TAG && !BWD ? 4 : 0));
-    static constexpr int NS = BYTES <= 16384 ? 4 : 3;
-    static constexpr int MINB = NS == 4 ? 3 : 2;
+template <int S> struct ShapeAt {
+    static constexpr int NT = kShapes[S].nt;
+    static constexpr int IPT = kShapes[S].ipt;
+    static constexpr int TILE = NT * IPT;
 };
 
-template <int KS, int VB> constexpr int64_t tile_of() {
-    return int64_t(TileShape<KS, VB>::NT) * TileShape<KS, VB>::IPT;
+// Shared-memory stages of a (key, payload, tag, direction, shape) kernel and
+// the CTAs per SM they leave room for: four stages when four fit in about a
+// third of the SM's shared memory, else three; FITS is false when even three
+// exceed a CTA's 227 KB.
+template <int KS, int VB, bool TAG, bool BWD, int S> struct Stages {
+    static constexpr int TILE = ShapeAt<S>::TILE;
+    static constexpr int BYTES = (TILE + 32) * (KS + VB + (TAG && !BWD ? 4 : 0));
+    static constexpr int NS = 4 * BYTES <= 75 * 1024 ? 4 : 3;
+    static constexpr int MINB = NS == 4 ? 3 : (3 * BYTES <= 110 * 1024 ? 2 : 1);
+    static constexpr bool FITS = NS * BYTES <= 220 * 1024;
+};
+
+// A shape is offered for (KS, VB) when the forward kernel with tags and, for
+// payloads, the backward kernel fit.
+template <int KS, int VB, int S> constexpr bool shape_fits() {
+    return Stages<KS, VB, true, false, S>::FITS && (VB == 0 || Stages<KS, VB, false, true, S>::FITS);
 }
 
-inline int64_t tile_for(int key_bytes, int vb) {
-    if (key_bytes == 4) {
-        if (vb == 0) return tile_of<4, 0>();
-        if (vb == 4) return tile_of<4, 4>();
-        if (vb == 8) return tile_of<4, 8>();
-    } else if (key_bytes == 8) {
-        if (vb == 0) return tile_of<8, 0>();
-        if (vb == 4) return tile_of<8, 4>();
-        if (vb == 8) return tile_of<8, 8>();
+inline bool shape_available(int key_bytes, int vb, int s) {
+    if (s < 0 || s >= kNumShapes) return false;
+#define CR_FIT(KS, VB)                                                                       \
+    if (key_bytes == KS && vb == VB) {                                                        \
+        constexpr bool f[kNumShapes] = {shape_fits<KS, VB, 0>(), shape_fits<KS, VB, 1>(),     \
+                                        shape_fits<KS, VB, 2>(), shape_fits<KS, VB, 3>()};    \
+        return f[s];                                                                          \
     }
-    return 0;
+    CR_FIT(4, 0) CR_FIT(4, 4) CR_FIT(4, 8) CR_FIT(8, 0) CR_FIT(8, 4) CR_FIT(8, 8)
+#undef CR_FIT
+    return false;
 }
+
+// Current shape per (key size, payload width) (cr_abi.cu owns the table).
+int current_shape(int key_bytes, int vb);
+
+inline int64_t tile_of_shape(int s) { return int64_t(kShapes[s].nt) * kShapes[s].ipt; }
 
 template <class K>
 struct KeyOps {
-    // Forward merge of the tiles listed in the workspace.  vb in {0,4,8}.
-    static cudaError_t merge_fwd(int vb, bool tag, const MergeArgs& a, int64_t max_tiles,
-                                 cudaStream_t st);
+    // Forward merge of the tiles listed in the workspace.  vb in {0,4,8};
+    // shape: index into kShapes (must match the tile size of the table).
+    static cudaError_t merge_fwd(int shape, int vb, bool tag, const MergeArgs& a,
+                                 int64_t max_tiles, cudaStream_t st);
     // Payload backward (vb in {4,8}).
-    static cudaError_t merge_bwd(int vb, const MergeArgs& a, int64_t max_tiles, cudaStream_t st);
+    static cudaError_t merge_bwd(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                 cudaStream_t st);
     static cudaError_t partition_single(const void* A, int64_t m, const void* B, int64_t n,
                                         int64_t tile, int64_t ntiles, void* ws, cudaStream_t st);
     static cudaError_t partition_pass(const void* X, int64_t N, int64_t w, int64_t tile,

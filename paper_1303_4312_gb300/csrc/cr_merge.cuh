@@ -21,8 +21,8 @@
 //      interior and a few threads store the ragged ends.  A stage is handed
 //      back to the producer one tile later, once its bulk store has read it.
 //
-// The in-tile split is the unique co-rank of Lemma 1, found by bisection on
-// the first Lemma condition (A[j-1] <= B[d-j] holds exactly for j <= j*):
+// The in-tile split is the unique co-rank of Lemma 1, found by binary lifting
+// on the first Lemma condition (A[j-1] <= B[d-j] holds exactly for j <= j*):
 // one comparison per step instead of Algorithm 1's two-sided test, which
 // matters here because every consumer thread runs it once per tile.
 #pragma once
@@ -32,6 +32,7 @@
 namespace cr {
 
 template <int VB> struct VBits { using T = uint32_t; };
+template <bool B> struct BoolC { static constexpr bool value = B; };
 template <> struct VBits<8> { using T = uint64_t; };
 
 __host__ __device__ constexpr size_t align_up_sz(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -148,20 +149,25 @@ __device__ __forceinline__ void store_edges(T* gbase, const T* buf, int64_t g0, 
 }
 
 // Number of A elements among the first d outputs of the stable merge of
-// sA[0, alen) and sB[0, blen): the co-rank j of Lemma 1, by bisection on
-// its first condition.
-template <class K>
+// sA[0, alen) and sB[0, blen): the co-rank j of Lemma 1, found on its first
+// condition (A[x] <= B[d-1-x] holds exactly for x < j) by binary lifting:
+// LOG fixed steps of decreasing size, so all threads of a warp run the same
+// instruction stream.  Loads are issued only for in-range probes.
+template <int LOG, class K>
 __device__ __forceinline__ int split_in_tile(const K* sA, int alen, const K* sB, int blen, int d) {
-    int lo = d - blen > 0 ? d - blen : 0;
-    int hi = d < alen ? d : alen;
-#pragma unroll 1
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (!(sB[d - 1 - mid] < sA[mid])) lo = mid + 1;   // A[mid] <= B[d-1-mid]: A[mid] is in
-        else hi = mid;
+    const int lo = d - blen > 0 ? d - blen : 0;
+    const int hi = d < alen ? d : alen;
+    int pos = lo;
+#pragma unroll
+    for (int step = 1 << (LOG - 1); step > 0; step >>= 1) {
+        const int np = pos + step;
+        if (np <= hi && !(sB[d - np] < sA[np - 1])) pos = np;
     }
-    return lo;
+    return pos;
 }
+
+template <int X> struct Log2Ceil { static constexpr int v = 1 + Log2Ceil<(X + 1) / 2>::v; };
+template <> struct Log2Ceil<1> { static constexpr int v = 0; };
 
 // ---------------------------------------------------------------------------
 // Forward (BWD = false): C keys [+ payloads] [+ tags].
@@ -210,6 +216,12 @@ __global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeA
     }
     __syncthreads();
 
+    // A table made for another tile size (the shape was changed between the
+    // partition and this launch) is refused as a whole.
+    if (hdr->tile != TILE) {
+        if (tid == 0) set_status(&hdr->status, kDevInternal);
+        return;
+    }
     const int64_t ntiles = hdr->ntiles;
 
     if (tid >= NT) {
@@ -311,7 +323,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeA
         K* sk = stage_k(s);
         const K* sA = sk + in.ak;
         const K* sB = sk + in.bk;
-        int j = split_in_tile(sA, alen, sB, blen, d);
+        int j = split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d);
         int k = d - j;
         K a = K(0), b = K(0);
         if (cnt > 0) {
@@ -324,18 +336,29 @@ __global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeA
             uint32_t otag[TAG ? IPT : 1];
             const V* sv = stage_v(s);
             const int avo = in.av, bvo = in.bv;
+            // One merge step (ties take A).  GUARD: some side may run out
+            // within this thread's IPT steps (only near the windows' ends).
+            auto step = [&](int q, auto guard) {
+                const bool takeA = decltype(guard)::value
+                                       ? (k >= blen) || (j < alen && !(b < a))
+                                       : !(b < a);
+                okey[q] = takeA ? a : b;
+                if constexpr (VB != 0) oval[q] = sv[takeA ? avo + j : bvo + k];
+                if constexpr (TAG)
+                    otag[q] = takeA ? uint32_t(in.ga + j) : uint32_t(p.tag_b + in.gb + k);
+                j += takeA ? 1 : 0;
+                k += takeA ? 0 : 1;
+                const K nx = takeA ? sA[j] : sB[k];
+                a = takeA ? nx : a;
+                b = takeA ? b : nx;
+            };
+            if (cnt == IPT && j + IPT <= alen && k + IPT <= blen) {
 #pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                if (q < cnt) {
-                    const bool takeA = (k >= blen) || (j < alen && !(b < a));   // ties: A first
-                    okey[q] = takeA ? a : b;
-                    if constexpr (VB != 0) oval[q] = sv[takeA ? avo + j : bvo + k];
-                    if constexpr (TAG)
-                        otag[q] = takeA ? uint32_t(in.ga + j) : uint32_t(p.tag_b + in.gb + k);
-                    if (takeA) ++j; else ++k;
-                    const K nx = takeA ? sA[j] : sB[k];
-                    if (takeA) a = nx; else b = nx;
-                }
+                for (int q = 0; q < IPT; ++q) step(q, BoolC<false>{});
+            } else {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if (q < cnt) step(q, BoolC<true>{});
             }
             named_sync(1, NT);   // every input of stage s has been read
             const int ph = int(in.gc & (EK - 1));
@@ -362,16 +385,25 @@ __global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeA
             const V* sg = stage_g(s) + in.av;
             const int pha = int(in.ga & (EV - 1));
             const int boff = ((pha + alen + EV - 1) / EV) * EV + int(in.gb & (EV - 1));
+            auto step = [&](int q, auto guard) {
+                const bool takeA = decltype(guard)::value
+                                       ? (k >= blen) || (j < alen && !(b < a))
+                                       : !(b < a);
+                gval[q] = sg[d + q];
+                dst[q] = takeA ? pha + j : boff + k;
+                j += takeA ? 1 : 0;
+                k += takeA ? 0 : 1;
+                const K nx = takeA ? sA[j] : sB[k];
+                a = takeA ? nx : a;
+                b = takeA ? b : nx;
+            };
+            if (cnt == IPT && j + IPT <= alen && k + IPT <= blen) {
 #pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                if (q < cnt) {
-                    const bool takeA = (k >= blen) || (j < alen && !(b < a));
-                    gval[q] = sg[d + q];
-                    dst[q] = takeA ? pha + j : boff + k;
-                    if (takeA) ++j; else ++k;
-                    const K nx = takeA ? sA[j] : sB[k];
-                    if (takeA) a = nx; else b = nx;
-                }
+                for (int q = 0; q < IPT; ++q) step(q, BoolC<false>{});
+            } else {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if (q < cnt) step(q, BoolC<true>{});
             }
             named_sync(1, NT);   // every input of stage s has been read
             V* og = stage_g(s);

@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(256) partition_single_kernel(const K* A, int64
     if (t == 0) {
         WsHeader* h = static_cast<WsHeader*>(ws);
         h->status = kDevOk;
+        h->tile = int32_t(tile);
         h->ntiles = ntiles;
     }
     if (threadIdx.x < 32) {
@@ -184,6 +185,7 @@ __global__ void partition_pass_kernel(const K* X, int64_t N, int64_t w, int64_t 
     if (t == 0) {
         WsHeader* h = static_cast<WsHeader*>(ws);
         h->status = kDevOk;
+        h->tile = int32_t(tile);
         h->ntiles = ntiles;
     }
     if (t >= ntiles) return;
@@ -270,6 +272,7 @@ static __global__ void __launch_bounds__(1024) segment_scan_kernel(const int64_t
         prefix[nseg] = s_carry;
         WsHeader* h = static_cast<WsHeader*>(ws);
         h->status = s_bad ? kDevBadSeg : kDevOk;
+        h->tile = int32_t(tile);
         h->ntiles = s_bad ? 0 : s_carry;
     }
 }

@@ -101,3 +101,33 @@ def test_workspace_sizes(lib):
     assert lib.cr_merge_pass_workspace_size(3, 4, 1 << 20, 1024, ctypes.byref(out)) == 0
     t8 = lib.cr_tile_size(3, 4)
     assert out.value == 256 + 32 * ((1 << 20) // 2048) * ((2048 + t8 - 1) // t8)
+
+
+def test_tile_shapes(lib):
+    """Shapes are listed, selectable per (key size, payload width), reflected
+    in cr_tile_size, and refused where they do not fit shared memory."""
+    n = lib.cr_tile_shape_count()
+    assert n >= 2
+    nt, ipt = ctypes.c_int(), ctypes.c_int()
+    shapes = []
+    for s in range(n):
+        assert lib.cr_tile_shape_info(s, ctypes.byref(nt), ctypes.byref(ipt)) == 0
+        assert nt.value % 32 == 0 and ipt.value % 2 == 1
+        shapes.append(nt.value * ipt.value)
+    assert lib.cr_tile_shape_info(n, ctypes.byref(nt), ctypes.byref(ipt)) == 1
+    for kt in range(4):
+        for vb in (0, 4, 8):
+            before = lib.cr_get_tile_shape(kt, vb)
+            assert 0 <= before < n
+            try:
+                for s in range(n):
+                    st = lib.cr_set_tile_shape(kt, vb, s)
+                    assert st in (0, 7)
+                    if st == 0:
+                        assert lib.cr_get_tile_shape(kt, vb) == s
+                        assert lib.cr_tile_size(kt, vb) == shapes[s]
+            finally:
+                assert lib.cr_set_tile_shape(kt, vb, before) == 0
+    # the largest tiles do not fit 8-byte keys with 8-byte payloads and tags
+    assert lib.cr_set_tile_shape(3, 8, 0) == 7
+    assert lib.cr_get_tile_shape(9, 0) == -1

@@ -292,3 +292,84 @@ def test_streaming_merge_block_edges(dt):
             want, src = oracle.merge(A, B)
             assert same_bits(host(C, dt), want), (total, frac)
             assert np.array_equal(host(T, np.uint32).astype(np.int64), src), (total, frac)
+
+
+def test_every_tile_shape():
+    """Every compiled tile shape gives the oracle's output (forward keys with
+    tags, key-value forward and backward, batched), not only the default."""
+    from paper_1303_4312_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(107)
+    combos = [(np.int32, None), (np.int32, np.float32), (np.uint64, None), (np.uint64, np.float64),
+              (np.int64, np.float32)]
+    for dt, vdt in combos:
+        kt = key_type(np.empty(0, dt))
+        vb = np.dtype(vdt).itemsize if vdt else 0
+        code = _lib.KEY_TYPES[kt]
+        before = lib.cr_get_tile_shape(code, vb)
+        try:
+            for shape in range(lib.cr_tile_shape_count()):
+                if lib.cr_set_tile_shape(code, vb, shape) != 0:
+                    continue
+                t = cr.tile_size(kt, vb)
+                m, n = 3 * t + 17, 2 * t - 3
+                A = sorted_keys(rng, m, dt, 100)
+                B = sorted_keys(rng, n, dt, 100)
+                if vdt is None:
+                    C, T = cr.merge(dev(A), dev(B), key_type=kt, tag=True)
+                    torch.cuda.synchronize()
+                    want, src = oracle.merge(A, B)
+                    assert same_bits(host(C, dt), want), shape
+                    assert np.array_equal(host(T, np.uint32).astype(np.int64), src), shape
+                    continue
+                Av = rng.standard_normal(m).astype(vdt)
+                Bv = rng.standard_normal(n).astype(vdt)
+                Ck, Cv = cr.merge_kv(dev(A), dev(Av), dev(B), dev(Bv), key_type=kt)
+                gC = rng.standard_normal(m + n).astype(vdt)
+                gA, gB = cr.merge_kv_backward(dev(A), dev(B), dev(gC), key_type=kt)
+                a_off = np.array([0, m // 3, m // 3, m], np.int64)
+                b_off = np.array([0, 5, n // 2, n], np.int64)
+                Bk, Bkv = cr.batched_merge_kv(a_off, b_off, dev(A), dev(Av), dev(B), dev(Bv),
+                                              key_type=kt)
+                torch.cuda.synchronize()
+                wk, wv, _ = oracle.merge_kv(A, Av, B, Bv)
+                ga, gb = oracle.merge_grad(A, B, gC)
+                bk, bv = oracle.batched_merge_kv(a_off, b_off, A, Av, B, Bv)
+                assert same_bits(host(Ck, dt), wk), shape
+                assert same_bits(host(Cv, vdt), wv), shape
+                assert same_bits(host(gA, vdt), ga), shape
+                assert same_bits(host(gB, vdt), gb), shape
+                assert same_bits(host(Bk, dt), bk), shape
+                assert same_bits(host(Bkv, vdt), bv), shape
+        finally:
+            assert lib.cr_set_tile_shape(code, vb, before) == 0
+
+
+def test_table_for_another_shape_is_refused():
+    """A tile table made under one shape and merged under another is refused
+    on the device (status CR_EINTERNAL) instead of being misread."""
+    import ctypes
+    from paper_1303_4312_gb300 import _lib
+    lib = _lib.load()
+    code = _lib.KEY_TYPES["i32"]
+    before = lib.cr_get_tile_shape(code, 0)
+    other = next(s for s in range(lib.cr_tile_shape_count())
+                 if s != before and lib.cr_set_tile_shape(code, 0, s) == 0)
+    try:
+        A = torch.arange(0, 200000, 2, dtype=torch.int32, device="cuda")
+        B = torch.arange(1, 200001, 2, dtype=torch.int32, device="cuda")
+        C = torch.empty(200000, dtype=torch.int32, device="cuda")
+        ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream
+        _lib.check(lib.cr_set_tile_shape(code, 0, before))
+        _lib.check(lib.cr_merge_partition(code, 0, A.data_ptr(), 100000, B.data_ptr(), 100000,
+                                          ws.data_ptr(), ws.numel(), s))
+        _lib.check(lib.cr_set_tile_shape(code, 0, other))
+        _lib.check(lib.cr_merge_tiles(code, 0, A.data_ptr(), None, 100000, B.data_ptr(), None,
+                                      100000, C.data_ptr(), None, None, ws.data_ptr(),
+                                      ws.numel(), s))
+        with pytest.raises(cr.CorankError) as e:
+            cr.workspace_status(ws)
+        assert e.value.name == "CR_EINTERNAL"
+    finally:
+        _lib.check(lib.cr_set_tile_shape(code, 0, before))
