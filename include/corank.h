@@ -83,14 +83,15 @@ const char* cr_last_error(void);
 int cr_abi_version(void);
 
 /* Elements per tile (TILE) the merge kernels use for this key type and
- * payload width under the current tile shape: every tile of a merge carries
+ * payload width under the current (balanced-class) tile shape: every tile of a merge carries
  * exactly TILE output elements except the last one (per segment, for batched
  * calls).  Returns 0 for an invalid combination. */
 int64_t cr_tile_size(int key_type, int val_bytes);
 
-/* Tile shapes.  A tile is merged by NT consumer threads of IPT elements each
- * (TILE = NT * IPT; Algorithm 2's equal blocks, one per tile, and equal
- * per-thread shares inside it, Proposition 2).  Several shapes are compiled;
+/* Tile shapes.  A tile is merged by NT consumer threads, each merging ILP
+ * interleaved runs of IPT elements (TILE = NT * IPT * ILP; Algorithm 2's equal
+ * blocks, one per tile, and equal per-thread shares inside it,
+ * Proposition 2).  Several shapes are compiled;
  * the one used is chosen per (key size, payload width) -- for example by the
  * autotuner -- and applies to every later call of that combination in the
  * process.  Workspace sizes depend on it: query them after choosing, and do
@@ -100,13 +101,24 @@ int64_t cr_tile_size(int key_type, int val_bytes);
  * calls of that combination are being issued on other host threads is a
  * race. */
 int cr_tile_shape_count(void);
-/* NT and IPT of shape `shape` (CR_EINVAL if out of range). */
-cr_status cr_tile_shape_info(int shape, int* nt, int* ipt);
+/* NT, IPT and ILP of shape `shape` (CR_EINVAL if out of range; each output
+ * pointer may be NULL). */
+cr_status cr_tile_shape_info(int shape, int* nt, int* ipt, int* ilp);
 /* Select `shape` for this key type and payload width (0, 4, 8);
  * CR_EUNSUPPORTED if its shared-memory footprint does not fit. */
 cr_status cr_set_tile_shape(int key_type, int val_bytes, int shape);
 /* Current shape for this key type and payload width (-1 if invalid). */
 int cr_get_tile_shape(int key_type, int val_bytes);
+
+/* Single merges choose between two shapes per key type and payload width by
+ * geometry: "skewed" when one input is more than 16 times longer than the
+ * other (16 * min(m, n) < max(m, n)), else "balanced".  Batched and merge-pass
+ * calls use the balanced shape.  cr_set_tile_shape sets both classes; these
+ * set and read one (skewed = 0 or 1). */
+cr_status cr_set_tile_shape_for(int key_type, int val_bytes, int skewed, int shape);
+int cr_get_tile_shape_for(int key_type, int val_bytes, int skewed);
+/* TILE a single merge of m and n elements uses (0 for invalid arguments). */
+int64_t cr_tile_size_for(int key_type, int val_bytes, int64_t m, int64_t n);
 
 /* ------------------------------------------------------------------------
  * co_rank -- Algorithm 1 (Section 2), Lemma 1.

@@ -28,9 +28,13 @@ SIGNATURES = {
     "cr_abi_version": ([], INT),
     "cr_tile_size": ([INT, INT], I64),
     "cr_tile_shape_count": ([], INT),
-    "cr_tile_shape_info": ([INT, ctypes.POINTER(INT), ctypes.POINTER(INT)], INT),
+    "cr_tile_shape_info": ([INT, ctypes.POINTER(INT), ctypes.POINTER(INT),
+                            ctypes.POINTER(INT)], INT),
     "cr_set_tile_shape": ([INT, INT, INT], INT),
     "cr_get_tile_shape": ([INT, INT], INT),
+    "cr_set_tile_shape_for": ([INT, INT, INT, INT], INT),
+    "cr_get_tile_shape_for": ([INT, INT, INT], INT),
+    "cr_tile_size_for": ([INT, INT, I64, I64], I64),
     "cr_co_rank": ([INT, P, I64, P, I64, I64, P, P], INT),
     "cr_co_rank_many": ([INT, P, I64, P, I64, P, I64, P, P, P], INT),
     "cr_merge_workspace_size": ([INT, INT, I64, I64, ctypes.POINTER(SZ)], INT),

@@ -144,6 +144,90 @@ def merge(A: torch.Tensor, B: torch.Tensor, key_type: str | None = None, tag: bo
     return (C, T) if tag else C
 
 
+class MergeMany:
+    """Stable merges of several independent (A, B) pairs, with each pair's
+    grid-level co-rank pass (cr_merge_partition) issued on a side stream
+    ahead of the tile merges, which run in order on the caller's stream.
+
+    The partition is latency-bound and co-resides with a running tile-merge
+    kernel on the same SMs, so all but the first pair's partition overlap a
+    previous merge.  Tile tables are double-buffered per pair, so calling
+    ``run`` again (e.g. every step of a loop) lets the side stream run one
+    call ahead.  Results are bit-identical to ``merge`` on each pair.
+    """
+
+    def __init__(self, pairs, key_types=None, device=None):
+        self.pairs = list(pairs)
+        self.key_types = list(key_types) if key_types else [None] * len(self.pairs)
+        dev = device or self.pairs[0][0].device
+        self.dev = torch.device(dev)
+        lib = _lib.load()
+        self.codes = []
+        self.outs = []
+        self.ws = []
+        for (A, B), kt in zip(self.pairs, self.key_types):
+            _dev(A, B)
+            code = _key_code(A, kt)
+            m, n = A.numel(), B.numel()
+            need = _size(lib.cr_merge_workspace_size, code, 0, m, n)
+            self.codes.append(code)
+            self.outs.append(torch.empty(m + n, dtype=A.dtype, device=self.dev))
+            self.ws.append([torch.zeros(max(need, 256), dtype=torch.uint8, device=self.dev)
+                            for _ in range(2)])
+        self.side = torch.cuda.Stream(self.dev)
+        self.part_done = [None] * len(self.pairs)
+        self.tile_done = [[None, None] for _ in self.pairs]
+        self.calls = 0
+
+    def run(self, events=None):
+        """Issue every merge once; returns the outputs (valid in stream order
+        on the current stream).  `events`, if given, is a list receiving
+        (start, end) CUDA events around each tile merge."""
+        lib = _lib.load()
+        main = torch.cuda.current_stream(self.dev)
+        buf = self.calls & 1
+        sp, mp = self.side.cuda_stream, main.cuda_stream
+        for q, ((A, B), code) in enumerate(zip(self.pairs, self.codes)):
+            ws = self.ws[q][buf]
+            if self.tile_done[q][buf] is not None:
+                self.side.wait_event(self.tile_done[q][buf])   # table buffer is free again
+            _lib.check(lib.cr_merge_partition(code, 0, _ptr(A), A.numel(), _ptr(B), B.numel(),
+                                              _ptr(ws), ws.numel(), sp))
+            ev = torch.cuda.Event()
+            ev.record(self.side)
+            self.part_done[q] = ev
+        for q, ((A, B), code) in enumerate(zip(self.pairs, self.codes)):
+            ws = self.ws[q][buf]
+            main.wait_event(self.part_done[q])
+            e0 = e1 = None
+            if events is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(main)
+            _lib.check(lib.cr_merge_tiles(code, 0, _ptr(A), None, A.numel(), _ptr(B), None,
+                                          B.numel(), _ptr(self.outs[q]), None, None, _ptr(ws),
+                                          ws.numel(), mp))
+            done = torch.cuda.Event(enable_timing=events is not None)
+            done.record(main)
+            self.tile_done[q][buf] = done
+            if events is not None:
+                events.append((e0, done))
+        self.calls += 1
+        return self.outs
+
+    def check(self):
+        """Synchronise and raise if any device-side status was recorded."""
+        torch.cuda.synchronize(self.dev)
+        for pair in self.ws:
+            for ws in pair:
+                _lib.check(_lib.load().cr_workspace_status(_ptr(ws), _stream(self.dev)))
+
+
+def merge_many(pairs, key_types=None):
+    """Stable merges of independent (A, B) pairs with overlapped partitions
+    (see MergeMany).  Returns the list of outputs."""
+    return MergeMany(pairs, key_types).run()
+
+
 def merge_kv(Ak, Av, Bk, Bv, key_type: str | None = None, tag: bool = False, ws=None):
     """Key-value stable merge; payload bits follow their keys.
     Returns (Ck, Cv) or (Ck, Cv, tags)."""

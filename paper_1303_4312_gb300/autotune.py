@@ -1,9 +1,11 @@
 """Autotuner for the tile shape of the merge kernels.
 
-For every (key size, payload width) combination it times the forward merge
-(and, with payloads, the backward) of a seeded random problem under each tile
-shape the library offers for that combination, keeps the fastest, and writes
-a JSON table keyed by GPU name and compute capability.  ``apply()`` loads the
+For every (key size, payload width) combination and both geometry classes
+(balanced: m = n; skewed: one input 512 times longer than the other) it times
+the forward merge (and, with payloads, the backward) of a seeded random
+problem under each tile shape the library offers for that combination, keeps
+the fastest, and writes a JSON table keyed by GPU name and compute
+capability.  ``apply()`` loads the
 table for the current GPU (if one exists) and selects those shapes through
 ``cr_set_tile_shape``; the package does this on first use.
 
@@ -25,6 +27,7 @@ TABLE_DIR = os.path.join(HERE, "tuning")
 # (key type name, payload bytes) combinations; uint keys share the kernels'
 # shapes with the int keys of the same width.
 COMBOS = [("i32", 0), ("i32", 4), ("i32", 8), ("i64", 0), ("i64", 4), ("i64", 8)]
+CLASSES = (("balanced", 0), ("skewed", 1))
 
 
 def _slug(name: str) -> str:
@@ -56,46 +59,51 @@ def apply(lib=None, gpu_name: str | None = None, cc: str | None = None) -> dict 
         return None
     for key, entry in table.get("shapes", {}).items():
         kt, vb = key.split(":")
-        _lib.check(lib.cr_set_tile_shape(_lib.KEY_TYPES[kt], int(vb), int(entry["shape"])))
+        for cls, skewed in CLASSES:
+            if cls in entry:
+                _lib.check(lib.cr_set_tile_shape_for(_lib.KEY_TYPES[kt], int(vb), skewed,
+                                                     int(entry[cls]["shape"])))
     return table
 
 
-def _time_combo(lib, kt: str, vb: int, log2_size: int, reps: int):
+def _time_combo(lib, kt: str, vb: int, log2_size: int, reps: int, skewed: int):
     import torch
     code = _lib.KEY_TYPES[kt]
     dev = torch.device("cuda")
     g = torch.Generator(device=dev).manual_seed(1234)
-    n = 1 << (log2_size - 1)
+    total = 1 << log2_size
+    m = total // 513 if skewed else total // 2
+    n = total - m
     kdt = torch.int32 if kt == "i32" else torch.int64
     lo, hi = (-(1 << 31), 1 << 31) if kt == "i32" else (-(1 << 62), 1 << 62)
-    A = torch.sort(torch.randint(lo, hi, (n,), generator=g, device=dev, dtype=torch.int64)
+    A = torch.sort(torch.randint(lo, hi, (m,), generator=g, device=dev, dtype=torch.int64)
                    .to(kdt)).values
     B = torch.sort(torch.randint(lo, hi, (n,), generator=g, device=dev, dtype=torch.int64)
                    .to(kdt)).values
     vdt = {4: torch.float32, 8: torch.float64}.get(vb)
-    Av = torch.randn(n, generator=g, device=dev, dtype=vdt) if vb else None
+    Av = torch.randn(m, generator=g, device=dev, dtype=vdt) if vb else None
     Bv = torch.randn(n, generator=g, device=dev, dtype=vdt) if vb else None
-    C = torch.empty(2 * n, dtype=kdt, device=dev)
-    Cv = torch.empty(2 * n, dtype=vdt, device=dev) if vb else None
-    gC = torch.randn(2 * n, device=dev, dtype=vdt) if vb else None
-    gA = torch.empty(n, device=dev, dtype=vdt) if vb else None
+    C = torch.empty(m + n, dtype=kdt, device=dev)
+    Cv = torch.empty(m + n, dtype=vdt, device=dev) if vb else None
+    gC = torch.randn(m + n, device=dev, dtype=vdt) if vb else None
+    gA = torch.empty(m, device=dev, dtype=vdt) if vb else None
     gB = torch.empty(n, device=dev, dtype=vdt) if vb else None
     p = lambda t: None if t is None else t.data_ptr()
     s = torch.cuda.current_stream().cuda_stream
     results = {}
     for shape in range(lib.cr_tile_shape_count()):
-        if lib.cr_set_tile_shape(code, vb, shape) != 0:
+        if lib.cr_set_tile_shape_for(code, vb, skewed, shape) != 0:
             continue
         need = ctypes.c_size_t()
-        _lib.check(lib.cr_merge_workspace_size(code, vb, n, n, ctypes.byref(need)))
+        _lib.check(lib.cr_merge_workspace_size(code, vb, m, n, ctypes.byref(need)))
         ws = torch.empty(need.value, dtype=torch.uint8, device=dev)
 
         def fwd():
-            _lib.check(lib.cr_stable_merge_kv(code, vb, p(A), p(Av), n, p(B), p(Bv), n, p(C),
+            _lib.check(lib.cr_stable_merge_kv(code, vb, p(A), p(Av), m, p(B), p(Bv), n, p(C),
                                               p(Cv), None, p(ws), ws.numel(), s))
 
         def bwd():
-            _lib.check(lib.cr_stable_merge_kv_backward(code, vb, p(A), n, p(B), n, p(gC), p(gA),
+            _lib.check(lib.cr_stable_merge_kv_backward(code, vb, p(A), m, p(B), n, p(gC), p(gA),
                                                        p(gB), p(ws), ws.numel(), s))
 
         row = {}
@@ -124,15 +132,19 @@ def tune(log2_size: int = 26, reps: int = 10, write: bool = True,
              "shapes": {}}
     for kt, vb in COMBOS:
         code = _lib.KEY_TYPES[kt]
-        before = lib.cr_get_tile_shape(code, vb)
-        res = _time_combo(lib, kt, vb, log2_size, reps)
-        best = min(res, key=lambda s: sum(res[s].values()))
-        nt, ipt = ctypes.c_int(), ctypes.c_int()
-        _lib.check(lib.cr_tile_shape_info(best, ctypes.byref(nt), ctypes.byref(ipt)))
-        table["shapes"][f"{kt}:{vb}"] = {
-            "shape": best, "nt": nt.value, "ipt": ipt.value,
-            "ms": {str(s): {k: round(v, 4) for k, v in r.items()} for s, r in res.items()}}
-        _lib.check(lib.cr_set_tile_shape(code, vb, before))
+        entry = {}
+        for cls, skewed in CLASSES:
+            before = lib.cr_get_tile_shape_for(code, vb, skewed)
+            res = _time_combo(lib, kt, vb, log2_size, reps, skewed)
+            best = min(res, key=lambda s: sum(res[s].values()))
+            nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            _lib.check(lib.cr_tile_shape_info(best, ctypes.byref(nt), ctypes.byref(ipt),
+                                              ctypes.byref(ilp)))
+            entry[cls] = {
+                "shape": best, "nt": nt.value, "ipt": ipt.value, "ilp": ilp.value,
+                "ms": {str(s): {k: round(v, 4) for k, v in r.items()} for s, r in res.items()}}
+            _lib.check(lib.cr_set_tile_shape_for(code, vb, skewed, before))
+        table["shapes"][f"{kt}:{vb}"] = entry
     if write:
         path = out or table_path(name)
         os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -174,7 +174,11 @@ cr_status check_backward(int key_type, int vb, const void* Ak, int64_t m, const 
     return check_no_alias(outs, 2, ins, 3);
 }
 
-int shape_of(int key_type, int vb) { return cr::current_shape(key_bytes(key_type), vb); }
+// Shape for a merge of these sizes (batched and pass calls use the
+// balanced class: their segments are not known on the host).
+int shape_of(int key_type, int vb, int64_t m = 1, int64_t n = 1) {
+    return cr::current_shape(key_bytes(key_type), vb, cr::geometry_class(m, n));
+}
 
 int64_t single_tiles(int shape, int64_t m, int64_t n, int64_t* tile_out) {
     const int64_t tile = cr::tile_of_shape(shape);
@@ -247,12 +251,14 @@ cr_status launch_tiles_backward(int shape, int key_type, int vb, const void* Ak,
 namespace cr {
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
-// Selected tile shape per (key size 4|8, payload width 0|4|8).  Defaults:
-// 256 x 15 for 4-byte keys without payload, 256 x 7 otherwise.
-static std::atomic<int> g_shape[2][3] = {{{0}, {2}, {2}}, {{2}, {2}, {2}}};
+// Selected tile shape per (key size 4|8, payload width 0|4|8, geometry
+// class balanced|skewed).  Defaults: 256 x 15 for keys without payload
+// (128 x 31 for skewed 8-byte merges), 256 x 7 otherwise.
+static std::atomic<int> g_shape[2][3][2] = {{{{0}, {0}}, {{2}, {2}}, {{2}, {2}}},
+                                            {{{0}, {1}}, {{2}, {2}}, {{2}, {2}}}};
 
-int current_shape(int key_bytes, int vb) {
-    return g_shape[key_bytes == 8 ? 1 : 0][vb / 4].load(std::memory_order_relaxed);
+int current_shape(int key_bytes, int vb, int cls) {
+    return g_shape[key_bytes == 8 ? 1 : 0][vb / 4][cls ? 1 : 0].load(std::memory_order_relaxed);
 }
 }  // namespace cr
 
@@ -282,15 +288,16 @@ int64_t cr_tile_size(int key_type, int val_bytes) {
     const int ks = key_bytes(key_type);
     if (ks == 0) return 0;
     if (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) return 0;
-    return cr::tile_of_shape(cr::current_shape(ks, val_bytes));
+    return cr::tile_of_shape(cr::current_shape(ks, val_bytes, 0));
 }
 
 int cr_tile_shape_count(void) { return cr::kNumShapes; }
 
-cr_status cr_tile_shape_info(int shape, int* nt, int* ipt) {
+cr_status cr_tile_shape_info(int shape, int* nt, int* ipt, int* ilp) {
     if (shape < 0 || shape >= cr::kNumShapes) return fail(CR_EINVAL, "no tile shape %d", shape);
     if (nt) *nt = cr::kShapes[shape].nt;
     if (ipt) *ipt = cr::kShapes[shape].ipt;
+    if (ilp) *ilp = cr::kShapes[shape].ilp;
     return ok();
 }
 
@@ -301,14 +308,38 @@ cr_status cr_set_tile_shape(int key_type, int val_bytes, int shape) {
     if (!cr::shape_available(ks, val_bytes, shape))
         return fail(CR_EUNSUPPORTED, "tile shape %d does not fit %d-byte keys with %d-byte payloads",
                     shape, ks, val_bytes);
-    cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4].store(shape, std::memory_order_relaxed);
+    for (int cls = 0; cls < 2; ++cls)
+        cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4][cls].store(shape, std::memory_order_relaxed);
     return ok();
 }
 
 int cr_get_tile_shape(int key_type, int val_bytes) {
+    return cr_get_tile_shape_for(key_type, val_bytes, 0);
+}
+
+cr_status cr_set_tile_shape_for(int key_type, int val_bytes, int skewed, int shape) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, true));
+    const int ks = key_bytes(key_type);
+    if (!cr::shape_available(ks, val_bytes, shape))
+        return fail(CR_EUNSUPPORTED, "tile shape %d does not fit %d-byte keys with %d-byte payloads",
+                    shape, ks, val_bytes);
+    cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4][skewed ? 1 : 0].store(shape,
+                                                                    std::memory_order_relaxed);
+    return ok();
+}
+
+int cr_get_tile_shape_for(int key_type, int val_bytes, int skewed) {
     const int ks = key_bytes(key_type);
     if (ks == 0 || (val_bytes != 0 && val_bytes != 4 && val_bytes != 8)) return -1;
-    return cr::current_shape(ks, val_bytes);
+    return cr::current_shape(ks, val_bytes, skewed ? 1 : 0);
+}
+
+int64_t cr_tile_size_for(int key_type, int val_bytes, int64_t m, int64_t n) {
+    const int ks = key_bytes(key_type);
+    if (ks == 0 || (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) || m < 0 || n < 0)
+        return 0;
+    return cr::tile_of_shape(cr::current_shape(ks, val_bytes, cr::geometry_class(m, n)));
 }
 
 cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int64_t n, int64_t k,
@@ -358,7 +389,7 @@ cr_status cr_merge_workspace_size(int key_type, int val_bytes, int64_t m, int64_
     CR_TRY(check_vb(val_bytes, true));
     if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
     if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
-    *bytes = single_ws_bytes(single_tiles(shape_of(key_type, val_bytes), m, n, nullptr));
+    *bytes = single_ws_bytes(single_tiles(shape_of(key_type, val_bytes, m, n), m, n, nullptr));
     return ok();
 }
 
@@ -375,7 +406,7 @@ cr_status cr_stable_merge_kv(int key_type, int val_bytes, const void* Ak, const 
     CR_TRY(check_forward(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag));
     if (m + n == 0) return ok();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int shape = shape_of(key_type, val_bytes);
+    const int shape = shape_of(key_type, val_bytes, m, n);
     CR_TRY(launch_partition(shape, key_type, Ak, m, Bk, n, ws, ws_bytes, st));
     CR_TRY(launch_tiles(shape, key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag, ws,
                         ws_bytes, st));
@@ -388,7 +419,7 @@ cr_status cr_stable_merge_kv_backward(int key_type, int val_bytes, const void* A
     CR_TRY(check_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB));
     if (m + n == 0) return ok();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int shape = shape_of(key_type, val_bytes);
+    const int shape = shape_of(key_type, val_bytes, m, n);
     CR_TRY(launch_partition(shape, key_type, Ak, m, Bk, n, ws, ws_bytes, st));
     CR_TRY(launch_tiles_backward(shape, key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB, ws,
                                  ws_bytes, st));
@@ -404,7 +435,7 @@ cr_status cr_merge_partition(int key_type, int val_bytes, const void* A, int64_t
     CR_TRY(check_arr({A, m, ks, "A"}));
     CR_TRY(check_arr({B, n, ks, "B"}));
     if (m + n == 0) return ok();
-    CR_TRY(launch_partition(shape_of(key_type, val_bytes), key_type, A, m, B, n, ws, ws_bytes,
+    CR_TRY(launch_partition(shape_of(key_type, val_bytes, m, n), key_type, A, m, B, n, ws, ws_bytes,
                             static_cast<cudaStream_t>(stream)));
     return ok();
 }
@@ -414,7 +445,7 @@ cr_status cr_merge_tiles(int key_type, int val_bytes, const void* Ak, const void
                          uint32_t* C_tag, void* ws, size_t ws_bytes, cr_stream stream) {
     CR_TRY(check_forward(key_type, val_bytes, Ak, Av, m, Bk, Bv, n, Ck, Cv, C_tag));
     if (m + n == 0) return ok();
-    CR_TRY(launch_tiles(shape_of(key_type, val_bytes), key_type, val_bytes, Ak, Av, m, Bk, Bv, n,
+    CR_TRY(launch_tiles(shape_of(key_type, val_bytes, m, n), key_type, val_bytes, Ak, Av, m, Bk, Bv, n,
                         Ck, Cv, C_tag, ws, ws_bytes, static_cast<cudaStream_t>(stream)));
     return ok();
 }
@@ -424,7 +455,7 @@ cr_status cr_merge_tiles_backward(int key_type, int val_bytes, const void* Ak, i
                                   void* ws, size_t ws_bytes, cr_stream stream) {
     CR_TRY(check_backward(key_type, val_bytes, Ak, m, Bk, n, gC, gA, gB));
     if (m + n == 0) return ok();
-    CR_TRY(launch_tiles_backward(shape_of(key_type, val_bytes), key_type, val_bytes, Ak, m, Bk,
+    CR_TRY(launch_tiles_backward(shape_of(key_type, val_bytes, m, n), key_type, val_bytes, Ak, m, Bk,
                                  n, gC, gA, gB, ws, ws_bytes, static_cast<cudaStream_t>(stream)));
     return ok();
 }

@@ -52,31 +52,35 @@ cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream
     } else {
         constexpr int NT = ShapeAt<S>::NT;
         constexpr int IPT = ShapeAt<S>::IPT;
+        constexpr int ILP = ShapeAt<S>::ILP;
         constexpr int NS = Stages<KS, VB, TAG, BWD, S>::NS;
         constexpr int MINB = Stages<KS, VB, TAG, BWD, S>::MINB;
-        using L = Layout<K, VB, TAG, NT, IPT, NS, BWD>;
-        auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, NS, MINB, BWD>;
+        using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD>;
+        auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, ILP, NS, MINB, BWD>;
         static LaunchShape cache[kMaxDevices];
         static std::once_flag once[kMaxDevices];
         LaunchShape sh;
-        cudaError_t e = launch_shape(kern, NT + 32, L::TOTAL, cache, once, sh);
+        constexpr int THREADS = merge_block_threads<NT>();
+        cudaError_t e = launch_shape(kern, THREADS, L::TOTAL, cache, once, sh);
         if (e != cudaSuccess) return e;
         if (max_tiles <= 0) return cudaSuccess;
         int64_t grid = int64_t(sh.sms) * sh.blocks_per_sm;
         if (grid > max_tiles) grid = max_tiles;
-        kern<<<unsigned(grid), NT + 32, L::TOTAL, st>>>(a);
+        kern<<<unsigned(grid), THREADS, L::TOTAL, st>>>(a);
         return cudaGetLastError();
     }
 }
 
 template <class K, int VB, bool TAG, bool BWD>
 cudaError_t launch_merge(int shape, const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
-    static_assert(kNumShapes == 4, "dispatch below lists every shape");
+    static_assert(kNumShapes == 6, "dispatch below lists every shape");
     switch (shape) {
         case 0: return launch_merge_shape<K, VB, TAG, BWD, 0>(a, max_tiles, st);
         case 1: return launch_merge_shape<K, VB, TAG, BWD, 1>(a, max_tiles, st);
         case 2: return launch_merge_shape<K, VB, TAG, BWD, 2>(a, max_tiles, st);
         case 3: return launch_merge_shape<K, VB, TAG, BWD, 3>(a, max_tiles, st);
+        case 4: return launch_merge_shape<K, VB, TAG, BWD, 4>(a, max_tiles, st);
+        case 5: return launch_merge_shape<K, VB, TAG, BWD, 5>(a, max_tiles, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -162,3 +166,26 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
 }
 
 }  // namespace cr
+
+// Explicit instantiation, split so that the forward kernels and the rest of a
+// key type compile in separate translation units.
+#define CR_INSTANTIATE_FORWARD(K)                                                              \
+    template cudaError_t cr::KeyOps<K>::merge_fwd(int, int, bool, const cr::MergeArgs&,        \
+                                                  int64_t, cudaStream_t);
+#define CR_INSTANTIATE_REST(K)                                                                 \
+    template cudaError_t cr::KeyOps<K>::merge_bwd(int, int, const cr::MergeArgs&, int64_t,     \
+                                                  cudaStream_t);                               \
+    template cudaError_t cr::KeyOps<K>::partition_single(const void*, int64_t, const void*,    \
+                                                         int64_t, int64_t, int64_t, void*,     \
+                                                         cudaStream_t);                        \
+    template cudaError_t cr::KeyOps<K>::partition_pass(const void*, int64_t, int64_t, int64_t, \
+                                                       void*, int64_t*, cudaStream_t);         \
+    template cudaError_t cr::KeyOps<K>::partition_batched(                                     \
+        const void*, const void*, const int64_t*, const int64_t*, int64_t, int64_t, int64_t,   \
+        int64_t, int64_t, void*, int64_t*, cudaStream_t);                                      \
+    template cudaError_t cr::KeyOps<K>::co_rank_many(const void*, int64_t, const void*,        \
+                                                     int64_t, const int64_t*, int64_t,         \
+                                                     int64_t*, int64_t*, cudaStream_t);        \
+    template cudaError_t cr::KeyOps<K>::co_rank_one(const void*, int64_t, const void*,         \
+                                                    int64_t, int64_t, int64_t*, cudaStream_t);
+

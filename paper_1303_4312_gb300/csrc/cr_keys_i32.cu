@@ -1,4 +1,4 @@
-// Kernels and launchers for int32_t keys.
+// Backward kernels, partitions and co-rank kernels for int32_t keys.
 #include "cr_keyops_impl.cuh"
 
-template struct cr::KeyOps<int32_t>;
+CR_INSTANTIATE_REST(int32_t)

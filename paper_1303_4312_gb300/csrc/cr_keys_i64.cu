@@ -1,4 +1,4 @@
-// Kernels and launchers for int64_t keys.
+// Backward kernels, partitions and co-rank kernels for int64_t keys.
 #include "cr_keyops_impl.cuh"
 
-template struct cr::KeyOps<int64_t>;
+CR_INSTANTIATE_REST(int64_t)

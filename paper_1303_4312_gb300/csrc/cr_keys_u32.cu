@@ -1,4 +1,4 @@
-// Kernels and launchers for uint32_t keys.
+// Backward kernels, partitions and co-rank kernels for uint32_t keys.
 #include "cr_keyops_impl.cuh"
 
-template struct cr::KeyOps<uint32_t>;
+CR_INSTANTIATE_REST(uint32_t)

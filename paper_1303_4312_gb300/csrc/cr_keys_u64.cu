@@ -1,4 +1,4 @@
-// Kernels and launchers for uint64_t keys.
+// Backward kernels, partitions and co-rank kernels for uint64_t keys.
 #include "cr_keyops_impl.cuh"
 
-template struct cr::KeyOps<uint64_t>;
+CR_INSTANTIATE_REST(uint64_t)

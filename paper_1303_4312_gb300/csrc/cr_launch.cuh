@@ -10,23 +10,26 @@
 
 namespace cr {
 
-// Tile shapes: NT consumer threads times IPT items per thread (IPT odd, so
-// that a warp's stride-IPT shared-memory accesses fall in distinct banks).
+// Tile shapes: NT consumer threads, each merging ILP interleaved chains of IPT
+// items (IPT odd, so that a warp's stride-IPT shared-memory accesses fall in
+// distinct banks); TILE = NT * IPT * ILP.
 // Every shape is compiled for every key and payload width it fits; which one
 // a call uses is a runtime choice per (key size, payload width), set through
 // cr_set_tile_shape (the autotuner sweeps them).  TILE = NT * IPT is shared
 // by the forward and the backward kernel of a (key, payload) pair, so one
 // tile table serves both.
 struct ShapeDesc {
-    int nt, ipt;
+    int nt, ipt, ilp;   // consumer threads, items per chain, chains per thread
 };
-constexpr int kNumShapes = 4;
-constexpr ShapeDesc kShapes[kNumShapes] = {{256, 15}, {128, 31}, {256, 7}, {128, 15}};
+constexpr int kNumShapes = 6;
+constexpr ShapeDesc kShapes[kNumShapes] = {{256, 15, 1}, {128, 31, 1}, {256, 7, 1},
+                                           {128, 15, 1}, {128, 15, 2}, {128, 7, 2}};
 
 template <int S> struct ShapeAt {
     static constexpr int NT = kShapes[S].nt;
     static constexpr int IPT = kShapes[S].ipt;
-    static constexpr int TILE = NT * IPT;
+    static constexpr int ILP = kShapes[S].ilp;
+    static constexpr int TILE = NT * IPT * ILP;
 };
 
 // Shared-memory stages of a (key, payload, tag, direction, shape) kernel and
@@ -52,7 +55,8 @@ inline bool shape_available(int key_bytes, int vb, int s) {
 #define CR_FIT(KS, VB)                                                                       \
     if (key_bytes == KS && vb == VB) {                                                        \
         constexpr bool f[kNumShapes] = {shape_fits<KS, VB, 0>(), shape_fits<KS, VB, 1>(),     \
-                                        shape_fits<KS, VB, 2>(), shape_fits<KS, VB, 3>()};    \
+                                        shape_fits<KS, VB, 2>(), shape_fits<KS, VB, 3>(),     \
+                                        shape_fits<KS, VB, 4>(), shape_fits<KS, VB, 5>()};    \
         return f[s];                                                                          \
     }
     CR_FIT(4, 0) CR_FIT(4, 4) CR_FIT(4, 8) CR_FIT(8, 0) CR_FIT(8, 4) CR_FIT(8, 8)
@@ -60,10 +64,21 @@ inline bool shape_available(int key_bytes, int vb, int s) {
     return false;
 }
 
-// Current shape per (key size, payload width) (cr_abi.cu owns the table).
-int current_shape(int key_bytes, int vb);
+// Geometry class of a merge: skewed (1) when one input is more than 16 times
+// longer than the other, else balanced (0).  Skewed merges take nearly whole
+// tiles from one input, so their best tile shape differs.
+inline int geometry_class(int64_t m, int64_t n) {
+    const int64_t lo = m < n ? m : n, hi = m < n ? n : m;
+    return 16 * lo < hi ? 1 : 0;
+}
 
-inline int64_t tile_of_shape(int s) { return int64_t(kShapes[s].nt) * kShapes[s].ipt; }
+// Current shape per (key size, payload width, geometry class) (cr_abi.cu
+// owns the table).
+int current_shape(int key_bytes, int vb, int cls);
+
+inline int64_t tile_of_shape(int s) {
+    return int64_t(kShapes[s].nt) * kShapes[s].ipt * kShapes[s].ilp;
+}
 
 template <class K>
 struct KeyOps {

@@ -1,9 +1,9 @@
 // cr_merge.cuh -- the persistent tile-merge kernel (forward and payload
 // backward) for sm_103a, driven by a table of tile records.
 //
-// Each CTA runs one producer warp and NT consumer threads and walks the
-// output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...  Every tile
-// carries exactly TILE = NT*IPT output elements (the last one of a merge or
+// Each CTA runs NT consumer threads, one producer warp and one storer warp,
+// and walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// Every tile carries exactly TILE = NT*IPT*ILP output elements (the last one of a merge or
 // segment fewer), so the static round-robin schedule is balanced
 // (Algorithm 2 with equal blocks, Proposition 2).
 //
@@ -13,13 +13,17 @@
 //      cp.async.bulk completing on the stage's mbarrier).  Windows start at
 //      arbitrary element offsets: the copy covers the 16-byte aligned
 //      superset and the consumers index from the head offset.
-//  consumers (NT threads): thread s finds the split of diagonal s*IPT of
-//      the tile inside the shared-memory windows, merges exactly IPT
-//      elements serially into registers (ties take A), and after a barrier
+//  consumers (NT threads): each thread owns ILP diagonals of the tile
+//      (chain c of thread s starts at (c*NT + s)*IPT), finds their splits
+//      inside the shared-memory windows, merges exactly IPT elements per
+//      chain serially into registers (ties take A; the chains interleave
+//      so their shared-memory latencies overlap), and after a barrier
 //      writes them back into the same stage, which then serves as the output
-//      staging buffer; one thread issues bulk stores of the 16-byte aligned
-//      interior and a few threads store the ragged ends.  A stage is handed
-//      back to the producer one tile later, once its bulk store has read it.
+//      staging buffer, and signals the stage's "staged" mbarrier.
+//  storer (one warp): waits for a staged tile, issues the bulk store of its
+//      16-byte aligned interior, stores the ragged ends with plain stores,
+//      and hands the stage back to the producer as soon as the bulk store has
+//      read it.  The consumers never wait on stores.
 //
 // The in-tile split is the unique co-rank of Lemma 1, found by binary lifting
 // on the first Lemma condition (A[j-1] <= B[d-j] holds exactly for j <= j*):
@@ -49,9 +53,9 @@ static_assert(sizeof(StageInfo) == 48, "StageInfo size");
 // Shared-memory layout of one kernel instantiation (host and device agree).
 // A stage holds the input windows and, after the consumers have read them,
 // the tile's output (forward: keys, payloads, tags; backward: gA, gB).
-template <class K, int VB, bool TAG, int NT, int IPT, int NS, bool BWD>
+template <class K, int VB, bool TAG, int NT, int IPT, int ILP, int NS, bool BWD>
 struct Layout {
-    static constexpr int TILE = NT * IPT;
+    static constexpr int TILE = NT * IPT * ILP;
     static constexpr int KS = sizeof(K);
     static constexpr int EK = 16 / KS;
     static constexpr int VS = VB ? VB : 4;
@@ -65,12 +69,12 @@ struct Layout {
     static constexpr size_t STAGE_T = align_up_sz(size_t(ST) * 4, 128);
     static constexpr size_t STAGE_G = align_up_sz(size_t(SG) * VS, 128);
     static constexpr size_t STAGE = STAGE_K + STAGE_V + STAGE_T + STAGE_G;
-    static constexpr size_t BAR_OFF = 0;                       // full[NS], empty[NS], flags
+    static constexpr size_t BAR_OFF = 0;              // full, staged, empty [NS]; flags
     static constexpr size_t INFO_OFF = 256;
     static constexpr size_t STAGE_OFF = align_up_sz(INFO_OFF + NS * sizeof(StageInfo), 128);
     static constexpr size_t TOTAL = STAGE_OFF + NS * STAGE + 128;  // + slack for one-past reads
-    static_assert(NS >= 3, "the consumers hold two stages at a time");
-    static_assert(2 * NS * 8 + 16 <= INFO_OFF, "barrier area");
+    static_assert(NS >= 2, "at least one stage can load while another is merged");
+    static_assert(3 * NS * 8 + 16 <= INFO_OFF, "barrier area");
     static_assert(TILE % EK == 0 && TILE % EV == 0 && TILE % 4 == 0, "tile alignment");
     static_assert(TOTAL <= 232448, "exceeds 227 KB of shared memory per CTA");
 };
@@ -152,18 +156,25 @@ __device__ __forceinline__ void store_edges(T* gbase, const T* buf, int64_t g0, 
 // sA[0, alen) and sB[0, blen): the co-rank j of Lemma 1, found on its first
 // condition (A[x] <= B[d-1-x] holds exactly for x < j) by binary lifting:
 // LOG fixed steps of decreasing size, so all threads of a warp run the same
-// instruction stream.  Loads are issued only for in-range probes.
-template <int LOG, class K>
-__device__ __forceinline__ int split_in_tile(const K* sA, int alen, const K* sB, int blen, int d) {
-    const int lo = d - blen > 0 ? d - blen : 0;
-    const int hi = d < alen ? d : alen;
-    int pos = lo;
+// instruction stream.  Loads are issued only for in-range probes.  ILP
+// independent diagonals are searched in lock step (their loads overlap).
+template <int LOG, int ILP, class K>
+__device__ __forceinline__ void split_in_tile(const K* sA, int alen, const K* sB, int blen,
+                                              const int (&d)[ILP], int (&pos)[ILP]) {
+    int hi[ILP];
+#pragma unroll
+    for (int c = 0; c < ILP; ++c) {
+        pos[c] = d[c] - blen > 0 ? d[c] - blen : 0;
+        hi[c] = d[c] < alen ? d[c] : alen;
+    }
 #pragma unroll
     for (int step = 1 << (LOG - 1); step > 0; step >>= 1) {
-        const int np = pos + step;
-        if (np <= hi && !(sB[d - np] < sA[np - 1])) pos = np;
+#pragma unroll
+        for (int c = 0; c < ILP; ++c) {
+            const int np = pos[c] + step;
+            if (np <= hi[c] && !(sB[d[c] - np] < sA[np - 1])) pos[c] = np;
+        }
     }
-    return pos;
 }
 
 template <int X> struct Log2Ceil { static constexpr int v = 1 + Log2Ceil<(X + 1) / 2>::v; };
@@ -173,9 +184,12 @@ template <> struct Log2Ceil<1> { static constexpr int v = 0; };
 // Forward (BWD = false): C keys [+ payloads] [+ tags].
 // Backward (BWD = true): gA / gB from gC, routed by the same merge decisions.
 // ---------------------------------------------------------------------------
-template <class K, int VB, bool TAG, int NT, int IPT, int NS, int MINB, bool BWD>
-__global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeArgs p) {
-    using L = Layout<K, VB, TAG, NT, IPT, NS, BWD>;
+// Block: NT consumer threads, then one producer warp, then one storer warp.
+template <int NT> constexpr int merge_block_threads() { return NT + 64; }
+
+template <class K, int VB, bool TAG, int NT, int IPT, int ILP, int NS, int MINB, bool BWD>
+__global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeArgs p) {
+    using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD>;
     using V = typename VBits<VB>::T;
     constexpr int TILE = L::TILE;
     constexpr int EK = L::EK;
@@ -183,12 +197,14 @@ __global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeA
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
-    uint64_t* empty = full + NS;
-    // s_abort: written only by consumer threads between their two named
-    // barriers of an iteration and read by all of them after the second one,
-    // so every consumer takes the same exit decision.
+    uint64_t* staged = full + NS;
+    uint64_t* empty = staged + NS;
+    // s_abort[it & 1]: written only by consumer threads of iteration it before
+    // that iteration's barrier and read by all of them after it (the other
+    // slot belongs to the neighbouring iterations), so every consumer takes
+    // the same exit decision.
     volatile int32_t* s_abort = reinterpret_cast<volatile int32_t*>(empty + NS);
-    volatile int32_t* s_issued = s_abort + 1;
+    volatile int32_t* s_issued = s_abort + 2;
     StageInfo* info = reinterpret_cast<StageInfo*>(smem + L::INFO_OFF);
 
     auto base = [&](int s) { return smem + L::STAGE_OFF + size_t(s) * L::STAGE; };
@@ -208,9 +224,11 @@ __global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeA
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
+            mbar_init(&staged[s], NT);
             mbar_init(&empty[s], 1);
         }
-        *s_abort = 0;
+        s_abort[0] = 0;
+        s_abort[1] = 0;
         *s_issued = 0;
         fence_barrier_init();
     }
@@ -224,6 +242,57 @@ __global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeA
     }
     const int64_t ntiles = hdr->ntiles;
 
+    if (tid >= NT + 32) {
+        // -------------------------------------------------------------- storer
+        const int lane = tid - NT - 32;
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int s = it % NS;
+            // the decision is made warp-uniform so that every lane reaches
+            // the __syncwarp below
+            if (!__all_sync(0xffffffffu, mbar_wait(&staged[s], (it / NS) & 1))) {
+                if (lane == 0) set_status(&hdr->status, kDevTimeout);
+                break;
+            }
+            const StageInfo in = info[s];
+            const int len = in.alen + in.blen;
+            if constexpr (!BWD) {
+                K* C = static_cast<K*>(p.ck);
+                if (lane == 0) {
+                    store_bulk(C, stage_k(s), in.gc, len, EK);
+                    if constexpr (VB != 0)
+                        store_bulk(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV);
+                    if constexpr (TAG) store_bulk(p.ctag, stage_t(s), in.gc, len, 4);
+                    bulk_commit();
+                } else if (lane <= 2 * EK) {
+                    store_edges(C, stage_k(s), in.gc, len, EK, lane - 1);
+                } else if (VB != 0 && lane >= 9 && lane < 9 + 2 * EV) {
+                    store_edges(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV, lane - 9);
+                } else if (TAG && lane >= 17 && lane < 17 + 8) {
+                    store_edges(p.ctag, stage_t(s), in.gc, len, 4, lane - 17);
+                }
+            } else {
+                V* gA = static_cast<V*>(p.cv);
+                V* gB = static_cast<V*>(p.cv2);
+                const int pha = int(in.ga & (EV - 1));
+                const int ob = ((pha + in.alen + EV - 1) / EV) * EV;
+                if (lane == 0) {
+                    store_bulk(gA, stage_g(s), in.ga, in.alen, EV);
+                    store_bulk(gB, stage_g(s) + ob, in.gb, in.blen, EV);
+                    bulk_commit();
+                } else if (lane <= 2 * EV) {
+                    store_edges(gA, stage_g(s), in.ga, in.alen, EV, lane - 1);
+                } else if (lane >= 9 && lane < 9 + 2 * EV) {
+                    store_edges(gB, stage_g(s) + ob, in.gb, in.blen, EV, lane - 9);
+                }
+            }
+            if (lane == 0) bulk_wait_read<0>();   // the bulk store has read the stage
+            __syncwarp();                          // and so have the edge stores
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+        if (lane == 0) bulk_wait_all<0>();
+        return;
+    }
     if (tid >= NT) {
         // ------------------------------------------------------------ producer
         if (tid != NT) return;
@@ -306,156 +375,153 @@ __global__ void __launch_bounds__(NT + 32, MINB) merge_tiles_kernel(const MergeA
     }
 
     // ---------------------------------------------------------------- consumers
+    // Thread tid merges ILP chains; chain c starts at diagonal (c*NT + tid)*IPT
+    // and the chains run interleaved, so each thread has ILP independent
+    // dependency chains of shared-memory loads in flight.
     int it = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int s = it % NS;
         const bool ready = mbar_wait(&full[s], (it / NS) & 1);
         if (!ready) {
             set_status(&hdr->status, kDevTimeout);
-            *s_abort = 1;
+            s_abort[it & 1] = 1;
         }
         const StageInfo in = info[s];
         const int alen = ready ? in.alen : 0;
         const int blen = ready ? in.blen : 0;
         const int len = alen + blen;
-        const int d = min(tid * IPT, len);
-        const int cnt = min(IPT, len - d);
         K* sk = stage_k(s);
-        const K* sA = sk + in.ak;
-        const K* sB = sk + in.bk;
-        int j = split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d);
-        int k = d - j;
-        K a = K(0), b = K(0);
-        if (cnt > 0) {
-            a = sA[j];   // may be one past A's window: never taken then
-            b = sB[k];
+        const int ao = in.ak, bo = in.bk;   // A[0] and B[0] of the tile in the stage
+        const K* sA = sk + ao;
+        const K* sB = sk + bo;
+        int d[ILP], cnt[ILP], j[ILP], k[ILP];
+        K a[ILP], b[ILP];
+        bool fast = true;
+#pragma unroll
+        for (int c = 0; c < ILP; ++c) {
+            d[c] = min((c * NT + tid) * IPT, len);
+            cnt[c] = min(IPT, len - d[c]);
         }
+        split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d, j);
+#pragma unroll
+        for (int c = 0; c < ILP; ++c) {
+            k[c] = d[c] - j[c];
+            a[c] = K(0);
+            b[c] = K(0);
+            if (cnt[c] > 0) {
+                a[c] = sA[j[c]];   // may be one past A's window: never taken then
+                b[c] = sB[k[c]];
+            }
+            fast = fast && cnt[c] == IPT && j[c] + IPT <= alen && k[c] + IPT <= blen;
+        }
+        // One loop version per warp: a warp whose threads disagree would run both.
+        fast = __all_sync(0xffffffffu, fast);
         if constexpr (!BWD) {
-            K okey[IPT];
-            V oval[VB ? IPT : 1];
-            uint32_t otag[TAG ? IPT : 1];
+            K okey[ILP][IPT];
+            V oval[ILP][VB ? IPT : 1];
+            uint32_t otag[ILP][TAG ? IPT : 1];
             const V* sv = stage_v(s);
             const int avo = in.av, bvo = in.bv;
-            // One merge step (ties take A).  GUARD: some side may run out
-            // within this thread's IPT steps (only near the windows' ends).
-            auto step = [&](int q, auto guard) {
+            // One merge step of chain c (ties take A).  GUARD: some side may
+            // run out within the chain's IPT steps (only near the windows' ends).
+            auto step = [&](int c, int q, auto guard) {
                 const bool takeA = decltype(guard)::value
-                                       ? (k >= blen) || (j < alen && !(b < a))
-                                       : !(b < a);
-                okey[q] = takeA ? a : b;
-                if constexpr (VB != 0) oval[q] = sv[takeA ? avo + j : bvo + k];
+                                       ? (k[c] >= blen) || (j[c] < alen && !(b[c] < a[c]))
+                                       : !(b[c] < a[c]);
+                okey[c][q] = takeA ? a[c] : b[c];
+                if constexpr (VB != 0) oval[c][q] = sv[takeA ? avo + j[c] : bvo + k[c]];
                 if constexpr (TAG)
-                    otag[q] = takeA ? uint32_t(in.ga + j) : uint32_t(p.tag_b + in.gb + k);
-                j += takeA ? 1 : 0;
-                k += takeA ? 0 : 1;
-                const K nx = takeA ? sA[j] : sB[k];
-                a = takeA ? nx : a;
-                b = takeA ? b : nx;
+                    otag[c][q] = takeA ? uint32_t(in.ga + j[c]) : uint32_t(p.tag_b + in.gb + k[c]);
+                j[c] += takeA ? 1 : 0;
+                k[c] += takeA ? 0 : 1;
+                const K nx = sk[takeA ? ao + j[c] : bo + k[c]];   // one load from either window
+                a[c] = takeA ? nx : a[c];
+                b[c] = takeA ? b[c] : nx;
             };
-            if (cnt == IPT && j + IPT <= alen && k + IPT <= blen) {
+            if (fast) {
 #pragma unroll
-                for (int q = 0; q < IPT; ++q) step(q, BoolC<false>{});
+                for (int q = 0; q < IPT; ++q)
+#pragma unroll
+                    for (int c = 0; c < ILP; ++c) step(c, q, BoolC<false>{});
             } else {
 #pragma unroll
                 for (int q = 0; q < IPT; ++q)
-                    if (q < cnt) step(q, BoolC<true>{});
+#pragma unroll
+                    for (int c = 0; c < ILP; ++c)
+                        if (q < cnt[c]) step(c, q, BoolC<true>{});
             }
             named_sync(1, NT);   // every input of stage s has been read
             const int ph = int(in.gc & (EK - 1));
 #pragma unroll
-            for (int q = 0; q < IPT; ++q)
-                if (q < cnt) sk[ph + d + q] = okey[q];
+            for (int c = 0; c < ILP; ++c)
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if (q < cnt[c]) sk[ph + d[c] + q] = okey[c][q];
             if constexpr (VB != 0) {
                 V* ov = stage_v(s);
                 const int phv = int(in.gc & (EV - 1));
 #pragma unroll
-                for (int q = 0; q < IPT; ++q)
-                    if (q < cnt) ov[phv + d + q] = oval[q];
+                for (int c = 0; c < ILP; ++c)
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+                        if (q < cnt[c]) ov[phv + d[c] + q] = oval[c][q];
             }
             if constexpr (TAG) {
                 uint32_t* ot = stage_t(s);
                 const int pht = int(in.gc & 3);
 #pragma unroll
-                for (int q = 0; q < IPT; ++q)
-                    if (q < cnt) ot[pht + d + q] = otag[q];
+                for (int c = 0; c < ILP; ++c)
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+                        if (q < cnt[c]) ot[pht + d[c] + q] = otag[c][q];
             }
         } else {
-            V gval[IPT];
-            int dst[IPT];
+            V gval[ILP][IPT];
+            int dst[ILP][IPT];
             const V* sg = stage_g(s) + in.av;
             const int pha = int(in.ga & (EV - 1));
             const int boff = ((pha + alen + EV - 1) / EV) * EV + int(in.gb & (EV - 1));
-            auto step = [&](int q, auto guard) {
+            auto step = [&](int c, int q, auto guard) {
                 const bool takeA = decltype(guard)::value
-                                       ? (k >= blen) || (j < alen && !(b < a))
-                                       : !(b < a);
-                gval[q] = sg[d + q];
-                dst[q] = takeA ? pha + j : boff + k;
-                j += takeA ? 1 : 0;
-                k += takeA ? 0 : 1;
-                const K nx = takeA ? sA[j] : sB[k];
-                a = takeA ? nx : a;
-                b = takeA ? b : nx;
+                                       ? (k[c] >= blen) || (j[c] < alen && !(b[c] < a[c]))
+                                       : !(b[c] < a[c]);
+                gval[c][q] = sg[d[c] + q];
+                dst[c][q] = takeA ? pha + j[c] : boff + k[c];
+                j[c] += takeA ? 1 : 0;
+                k[c] += takeA ? 0 : 1;
+                const K nx = sk[takeA ? ao + j[c] : bo + k[c]];   // one load from either window
+                a[c] = takeA ? nx : a[c];
+                b[c] = takeA ? b[c] : nx;
             };
-            if (cnt == IPT && j + IPT <= alen && k + IPT <= blen) {
+            if (fast) {
 #pragma unroll
-                for (int q = 0; q < IPT; ++q) step(q, BoolC<false>{});
+                for (int q = 0; q < IPT; ++q)
+#pragma unroll
+                    for (int c = 0; c < ILP; ++c) step(c, q, BoolC<false>{});
             } else {
 #pragma unroll
                 for (int q = 0; q < IPT; ++q)
-                    if (q < cnt) step(q, BoolC<true>{});
+#pragma unroll
+                    for (int c = 0; c < ILP; ++c)
+                        if (q < cnt[c]) step(c, q, BoolC<true>{});
             }
             named_sync(1, NT);   // every input of stage s has been read
             V* og = stage_g(s);
 #pragma unroll
-            for (int q = 0; q < IPT; ++q)
-                if (q < cnt) og[dst[q]] = gval[q];
+            for (int c = 0; c < ILP; ++c)
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if (q < cnt[c]) og[dst[c][q]] = gval[c][q];
         }
-        fence_proxy_async_smem();
-        named_sync(1, NT);       // the tile's output is staged
-        if (*s_abort) break;
-        if constexpr (!BWD) {
-            K* C = static_cast<K*>(p.ck);
-            if (tid == 0) {
-                store_bulk(C, sk, in.gc, len, EK);
-                if constexpr (VB != 0) store_bulk(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV);
-                if constexpr (TAG) store_bulk(p.ctag, stage_t(s), in.gc, len, 4);
-                bulk_commit();
-            } else if (tid <= 2 * EK) {
-                store_edges(C, sk, in.gc, len, EK, tid - 1);
-            } else if (VB != 0 && tid >= 32 && tid < 32 + 2 * EV) {
-                store_edges(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV, tid - 32);
-            } else if (TAG && tid >= 64 && tid < 64 + 8) {
-                store_edges(p.ctag, stage_t(s), in.gc, len, 4, tid - 64);
-            }
-        } else {
-            V* gA = static_cast<V*>(p.cv);
-            V* gB = static_cast<V*>(p.cv2);
-            const int pha = int(in.ga & (EV - 1));
-            const int ob = ((pha + in.alen + EV - 1) / EV) * EV;
-            if (tid == 0) {
-                store_bulk(gA, stage_g(s), in.ga, in.alen, EV);
-                store_bulk(gB, stage_g(s) + ob, in.gb, in.blen, EV);
-                bulk_commit();
-            } else if (tid <= 2 * EV) {
-                store_edges(gA, stage_g(s), in.ga, in.alen, EV, tid - 1);
-            } else if (tid >= 32 && tid < 32 + 2 * EV) {
-                store_edges(gB, stage_g(s) + ob, in.gb, in.blen, EV, tid - 32);
-            }
-        }
-        if (tid == 0) {
-            // Hand the previous tile's stage back once its bulk store has read
-            // it (its edge stores finished before this iteration's barriers).
-            bulk_wait_read<1>();
-            if (it > 0) mbar_arrive(&empty[(it - 1) % NS]);
-        }
+        fence_proxy_async_smem();   // the outputs are read by the bulk-store engine
+        mbar_arrive(&staged[s]);
+        if (s_abort[it & 1]) break;
     }
-    if (*s_abort && tid == 0) {
+    if ((s_abort[0] || s_abort[1]) && tid == 0) {
         // Let copies that were issued but never consumed land before exit.
         const int issued = *s_issued;
         for (int q = it; q < issued; ++q) mbar_wait(&full[q % NS], (q / NS) & 1, 100000000ull);
     }
-    if (tid == 0) bulk_wait_all<0>();
 }
 
 }  // namespace cr

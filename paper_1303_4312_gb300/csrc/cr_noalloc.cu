@@ -93,7 +93,7 @@ extern "C" cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_
     if (ks == 0) return na_fail(CR_EINVAL, "unknown key type %d", key_type);
     if (m < 0 || n < 0) return na_fail(CR_EINVAL, "negative size");
     const int64_t mn = m + n;
-    const int shape = cr::current_shape(ks, 0);
+    const int shape = cr::current_shape(ks, 0, cr::geometry_class(m, n));
     const int64_t tile = cr::tile_of_shape(shape);
     const int64_t max_tiles =
         int64_t((kNoAllocScratchBytes - size_t(cr::kHeaderBytes)) / sizeof(cr::TileRec));

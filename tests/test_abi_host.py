@@ -108,13 +108,13 @@ def test_tile_shapes(lib):
     in cr_tile_size, and refused where they do not fit shared memory."""
     n = lib.cr_tile_shape_count()
     assert n >= 2
-    nt, ipt = ctypes.c_int(), ctypes.c_int()
+    nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     shapes = []
     for s in range(n):
-        assert lib.cr_tile_shape_info(s, ctypes.byref(nt), ctypes.byref(ipt)) == 0
-        assert nt.value % 32 == 0 and ipt.value % 2 == 1
-        shapes.append(nt.value * ipt.value)
-    assert lib.cr_tile_shape_info(n, ctypes.byref(nt), ctypes.byref(ipt)) == 1
+        assert lib.cr_tile_shape_info(s, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp)) == 0
+        assert nt.value % 32 == 0 and ipt.value % 2 == 1 and ilp.value >= 1
+        shapes.append(nt.value * ipt.value * ilp.value)
+    assert lib.cr_tile_shape_info(n, ctypes.byref(nt), ctypes.byref(ipt), None) == 1
     for kt in range(4):
         for vb in (0, 4, 8):
             before = lib.cr_get_tile_shape(kt, vb)
@@ -131,3 +131,29 @@ def test_tile_shapes(lib):
     # the largest tiles do not fit 8-byte keys with 8-byte payloads and tags
     assert lib.cr_set_tile_shape(3, 8, 0) == 7
     assert lib.cr_get_tile_shape(9, 0) == -1
+
+
+def test_geometry_classes(lib):
+    """Balanced and skewed merges can use different shapes; cr_tile_size_for
+    and the workspace size follow the class of (m, n)."""
+    kt = 3  # uint64
+    b0, s0 = lib.cr_get_tile_shape_for(kt, 0, 0), lib.cr_get_tile_shape_for(kt, 0, 1)
+    try:
+        assert lib.cr_set_tile_shape_for(kt, 0, 0, 2) == 0
+        assert lib.cr_set_tile_shape_for(kt, 0, 1, 3) == 0
+        nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib.cr_tile_shape_info(2, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
+        t2 = nt.value * ipt.value * ilp.value
+        lib.cr_tile_shape_info(3, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
+        t3 = nt.value * ipt.value * ilp.value
+        assert lib.cr_tile_size_for(kt, 0, 1000, 1000) == t2
+        assert lib.cr_tile_size_for(kt, 0, 1000, 16000) == t2      # 16*min == max: balanced
+        assert lib.cr_tile_size_for(kt, 0, 1000, 16001) == t3      # skewed
+        assert lib.cr_tile_size_for(kt, 0, 16001, 1000) == t3
+        assert lib.cr_tile_size(kt, 0) == t2
+        out = ctypes.c_size_t()
+        assert lib.cr_merge_workspace_size(kt, 0, 10, 100000, ctypes.byref(out)) == 0
+        assert out.value == 256 + 32 * ((100010 + t3 - 1) // t3)
+    finally:
+        lib.cr_set_tile_shape_for(kt, 0, 0, b0)
+        lib.cr_set_tile_shape_for(kt, 0, 1, s0)

@@ -373,3 +373,19 @@ def test_table_for_another_shape_is_refused():
         assert e.value.name == "CR_EINTERNAL"
     finally:
         _lib.check(lib.cr_set_tile_shape(code, 0, before))
+
+
+def test_merge_many_overlapped_partitions():
+    """MergeMany (partitions on a side stream, double-buffered tile tables)
+    gives each pair's oracle merge, on three calls in a row."""
+    rng = np.random.default_rng(108)
+    pairs_h = [(sorted_keys(rng, 200003, np.int32, None), sorted_keys(rng, 150001, np.int32, None)),
+               (sorted_keys(rng, 1000, np.uint64, None), sorted_keys(rng, 400000, np.uint64, None)),
+               (sorted_keys(rng, 300000, np.int32, 16), sorted_keys(rng, 300000, np.int32, 16))]
+    pairs = [(dev(a), dev(b)) for a, b in pairs_h]
+    mm = cr.MergeMany(pairs, [key_type(a) for a, _ in pairs_h])
+    for _ in range(3):
+        outs = mm.run()
+        mm.check()
+        for (a, b), C in zip(pairs_h, outs):
+            assert same_bits(host(C, a.dtype), oracle.merge(a, b)[0])
