@@ -222,6 +222,83 @@ class MergeMany:
                 _lib.check(_lib.load().cr_workspace_status(_ptr(ws), _stream(self.dev)))
 
 
+class HostMerger:
+    """Stable merges of (A, B) pairs that live in pinned host memory.
+
+    Each pair is copied to the device on an input-copy stream, merged on a
+    compute stream and copied back on an output-copy stream; events order
+    the three per pair, so the output copy of one pair overlaps the input
+    copy of the next (the two copy directions run concurrently) and both
+    overlap the merges.  Device buffers and workspaces are allocated once and
+    reused by every ``run``.  The work joins the caller's current stream at
+    both ends, so events recorded on it around ``run`` time the whole
+    pipeline.
+    """
+
+    def __init__(self, shapes, device="cuda"):
+        """shapes: list of (m, n, torch dtype, key_type or None)."""
+        lib = _lib.load()
+        self.dev = torch.device(device)
+        self.items = []
+        for m, n, dtype, kt in shapes:
+            A = torch.empty(m, dtype=dtype, device=self.dev)
+            code = _key_code(A, kt)
+            need = _size(lib.cr_merge_workspace_size, code, 0, m, n)
+            self.items.append({
+                "m": m, "n": n, "code": code, "A": A,
+                "B": torch.empty(n, dtype=dtype, device=self.dev),
+                "C": torch.empty(m + n, dtype=dtype, device=self.dev),
+                "ws": torch.zeros(max(need, 256), dtype=torch.uint8, device=self.dev),
+                "in_free": None, "out_free": None})
+        self.s_in = torch.cuda.Stream(self.dev)
+        self.s_comp = torch.cuda.Stream(self.dev)
+        self.s_out = torch.cuda.Stream(self.dev)
+
+    def run(self, host_pairs, host_outs):
+        """host_pairs[i] = (A, B) pinned CPU tensors; host_outs[i] receives C."""
+        lib = _lib.load()
+        caller = torch.cuda.current_stream(self.dev)
+        start = torch.cuda.Event()
+        start.record(caller)
+        for st in (self.s_in, self.s_comp, self.s_out):
+            st.wait_event(start)
+        done = []
+        for it, (hA, hB), hC in zip(self.items, host_pairs, host_outs):
+            if hA.numel() != it["m"] or hB.numel() != it["n"] or hC.numel() != it["m"] + it["n"]:
+                raise ValueError("host buffers do not match the planned sizes")
+            if it["in_free"] is not None:
+                self.s_in.wait_event(it["in_free"])     # previous merge read the inputs
+            with torch.cuda.stream(self.s_in):
+                it["A"].copy_(hA, non_blocking=True)
+                it["B"].copy_(hB, non_blocking=True)
+            loaded = torch.cuda.Event()
+            loaded.record(self.s_in)
+            self.s_comp.wait_event(loaded)
+            if it["out_free"] is not None:
+                self.s_comp.wait_event(it["out_free"])  # previous output copy finished
+            _lib.check(lib.cr_stable_merge(it["code"], _ptr(it["A"]), it["m"], _ptr(it["B"]),
+                                           it["n"], _ptr(it["C"]), None, _ptr(it["ws"]),
+                                           it["ws"].numel(), self.s_comp.cuda_stream))
+            merged = torch.cuda.Event()
+            merged.record(self.s_comp)
+            it["in_free"] = merged
+            self.s_out.wait_event(merged)
+            with torch.cuda.stream(self.s_out):
+                hC.copy_(it["C"], non_blocking=True)
+            copied = torch.cuda.Event()
+            copied.record(self.s_out)
+            it["out_free"] = copied
+            done.append(copied)
+        for ev in done:
+            caller.wait_event(ev)
+        return host_outs
+
+    def check(self):
+        torch.cuda.synchronize(self.dev)
+        for it in self.items:
+            _lib.check(_lib.load().cr_workspace_status(_ptr(it["ws"]), _stream(self.dev)))
+
+
 def merge_many(pairs, key_types=None):
     """Stable merges of independent (A, B) pairs with overlapped partitions
     (see MergeMany).  Returns the list of outputs."""

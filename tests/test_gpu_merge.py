@@ -389,3 +389,25 @@ def test_merge_many_overlapped_partitions():
         mm.check()
         for (a, b), C in zip(pairs_h, outs):
             assert same_bits(host(C, a.dtype), oracle.merge(a, b)[0])
+
+
+def test_host_merger_pipeline():
+    """HostMerger: pinned host inputs -> device -> merge -> pinned host outputs,
+    pipelined on three streams, equals the oracle on two runs in a row."""
+    rng = np.random.default_rng(109)
+    pairs = [(sorted_keys(rng, 300001, np.int32, None), sorted_keys(rng, 200003, np.int32, None)),
+             (sorted_keys(rng, 5000, np.uint64, None), sorted_keys(rng, 700001, np.uint64, None))]
+    hm = cr.HostMerger([(len(a), len(b), torch.int32 if a.dtype == np.int32 else torch.int64,
+                         key_type(a)) for a, b in pairs])
+    hosts = [(torch.from_numpy(a.view(np.int32 if a.dtype == np.int32 else np.int64)).pin_memory(),
+              torch.from_numpy(b.view(np.int32 if b.dtype == np.int32 else np.int64)).pin_memory())
+             for a, b in pairs]
+    outs = [torch.empty(len(a) + len(b), dtype=hA.dtype).pin_memory()
+            for (a, b), (hA, _) in zip(pairs, hosts)]
+    for _ in range(2):
+        for o in outs:
+            o.fill_(0)
+        hm.run(hosts, outs)
+        hm.check()
+        for (a, b), o in zip(pairs, outs):
+            assert same_bits(o.numpy().view(a.dtype), oracle.merge(a, b)[0])
