@@ -411,3 +411,26 @@ def test_host_merger_pipeline():
         hm.check()
         for (a, b), o in zip(pairs, outs):
             assert same_bits(o.numpy().view(a.dtype), oracle.merge(a, b)[0])
+
+
+def test_sharded_merge_single_rank_nccl():
+    """The sharded merge with the library's own co-rank and merge kernels, in
+    a one-rank NCCL group on this GPU (plan, windows, gather)."""
+    import os
+    import socket
+    import torch.distributed as dist
+    from paper_1303_4312_gb300 import shard
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        rng = np.random.default_rng(112)
+        A = sorted_keys(rng, 123457, np.int32, 500)
+        B = sorted_keys(rng, 98765, np.int32, 500)
+        C, p = shard.sharded_merge(dev(A), dev(B))
+        assert (p.k0, p.k1) == (0, len(A) + len(B))
+        assert same_bits(host(C, np.int32), oracle.merge(A, B)[0])
+    finally:
+        dist.destroy_process_group()
