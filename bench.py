@@ -68,7 +68,8 @@ def parse_args():
     p.add_argument("--shift", type=int, default=0,
                    help="divide every workload size by 2^shift (for quick runs)")
     p.add_argument("--workload", default=WORKLOAD,
-                   choices=[WORKLOAD, "single_tag", "kv", "batched", "merge_sort"],
+                   choices=[WORKLOAD, "single_tag", "kv", "batched", "merge_sort",
+                            "partition_variants"],
                    help="the default is the headline workload; the others measure the "
                         "remaining rows of the path (one JSON line each)")
     return p.parse_args()
@@ -467,6 +468,50 @@ def run_row(args):
         tot = {k: v for k, v in timer.totals().items()}
         return finish(tot, {"tiles_keys_tags": 12 * (m + n)}, "single_i32_tag", m + n,
                       {"l2": "flushed between steps (256 MB write)"})
+
+    if args.workload == "partition_variants":
+        # the paper's two forms of the block co-ranks: shared (computed once
+        # per boundary, cr_merge_partition) and sync-free (every tile co-ranks
+        # both of its ends, cr_merge_partition_alg2); same tile merge after
+        merges = make_inputs(dev, args.shift)
+        out = {}
+        tot_shared = tot_free = 0.0
+        for mg in merges:
+            code = _lib.KEY_TYPES[mg["kt"]]
+            m, n = mg["m"], mg["n"]
+            A, B = mg["A"], mg["B"]
+            C = torch.empty(m + n, dtype=A.dtype, device=dev)
+            ws = torch.empty(api.merge_workspace_bytes(mg["kt"], 0, m, n), dtype=torch.uint8,
+                             device=dev)
+            res = {}
+            for name, fn in (("shared", lib.cr_merge_partition), ("alg2", lib.cr_merge_partition_alg2)):
+                timer = KernelTimer(stream)
+                for k in range(Wm + K):
+                    t = k >= Wm
+                    if t:
+                        timer.mark()
+                    _lib.check(fn(code, 0, ptr(A), m, ptr(B), n, ptr(ws), ws.numel(), sp))
+                    if t:
+                        timer.mark("partition")
+                    _lib.check(lib.cr_merge_tiles(code, 0, ptr(A), None, m, ptr(B), None, n, ptr(C),
+                                                  None, None, ptr(ws), ws.numel(), sp))
+                    if t:
+                        timer.mark("tiles")
+                torch.cuda.synchronize()
+                api.workspace_status(ws)
+                tt = timer.totals()
+                res[name] = {"partition_ms": round(tt["partition"] / K, 4),
+                             "tiles_ms": round(tt["tiles"] / K, 4)}
+            tot_shared += res["shared"]["partition_ms"] + res["shared"]["tiles_ms"]
+            tot_free += res["alg2"]["partition_ms"] + res["alg2"]["tiles_ms"]
+            out[mg["name"]] = res
+        elems = sum(mg["m"] + mg["n"] for mg in merges)
+        r = {"metric": METRIC, "unit": UNIT, "value": elems / (tot_shared / 1e3),
+             "ms_per_step": tot_shared, "ms_per_step_alg2": tot_free,
+             "config": {"workload": "partition_variants", "elements_per_step": elems,
+                        "size_shift": args.shift},
+             "per_merge": out, "steps": K, "warmup": Wm}
+        return r
 
     if args.workload == "kv":
         Ak, Av, Bk, Bv = W.t_kv_u32_f32(device=dev, shift=args.shift)

@@ -190,6 +190,15 @@ cr_status cr_merge_partition(int key_type, int val_bytes, const void* A, int64_t
                              const void* B, int64_t n, void* ws, size_t ws_bytes,
                              cr_stream stream);
 
+/* Same table as cr_merge_partition, computed the way each processing element
+ * of Algorithm 2 (Section 3) does it without synchronisation: every tile
+ * co-ranks both of its ends itself with Algorithm 1, sharing nothing with
+ * its neighbours.  Offered to compare the paper's two forms; the shared form
+ * above is faster on GB300. */
+cr_status cr_merge_partition_alg2(int key_type, int val_bytes, const void* A, int64_t m,
+                                  const void* B, int64_t n, void* ws, size_t ws_bytes,
+                                  cr_stream stream);
+
 cr_status cr_merge_tiles(int key_type, int val_bytes, const void* Ak, const void* Av, int64_t m,
                          const void* Bk, const void* Bv, int64_t n, void* Ck, void* Cv,
                          uint32_t* C_tag, void* ws, size_t ws_bytes, cr_stream stream);
@@ -245,6 +254,24 @@ cr_status cr_merge_pass(int key_type, int val_bytes, const void* X, const void* 
 cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int64_t N,
                                  int64_t width, const void* gY, void* gX,
                                  void* ws, size_t ws_bytes, cr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Run formation for a stable merge sort from unsorted input: every run of
+ * cr_sort_run_length() consecutive elements of X[0, N) (the last one may be
+ * shorter) is stably sorted into Y (payloads follow their keys, equal keys
+ * keep their input order), so that cr_merge_pass can take over with width
+ * cr_sort_run_length().  The paper has no counterpart; it assumes sorted
+ * inputs.  The backward routes gY to gX through the same in-run
+ * permutation, recomputed from the input keys X.  Y must not overlap X;
+ * val_bytes 0, 4 or 8 (4 or 8 for the backward).
+ * ------------------------------------------------------------------------ */
+int64_t cr_sort_run_length(void);
+
+cr_status cr_sort_runs(int key_type, int val_bytes, const void* X, const void* Xv, int64_t N,
+                       void* Y, void* Yv, cr_stream stream);
+
+cr_status cr_sort_runs_backward(int key_type, int val_bytes, const void* X, int64_t N,
+                                const void* gY, void* gX, cr_stream stream);
 
 /* ------------------------------------------------------------------------
  * Allocation-free stable merge (the paper has no counterpart: this is a

@@ -42,6 +42,7 @@ SIGNATURES = {
     "cr_stable_merge_kv": ([INT, INT, P, P, I64, P, P, I64, P, P, P, P, SZ, P], INT),
     "cr_stable_merge_kv_backward": ([INT, INT, P, I64, P, I64, P, P, P, P, SZ, P], INT),
     "cr_merge_partition": ([INT, INT, P, I64, P, I64, P, SZ, P], INT),
+    "cr_merge_partition_alg2": ([INT, INT, P, I64, P, I64, P, SZ, P], INT),
     "cr_merge_tiles": ([INT, INT, P, P, I64, P, P, I64, P, P, P, P, SZ, P], INT),
     "cr_merge_tiles_backward": ([INT, INT, P, I64, P, I64, P, P, P, P, SZ, P], INT),
     "cr_batched_workspace_size": ([INT, INT, I64, I64, I64, ctypes.POINTER(SZ)], INT),
@@ -52,6 +53,9 @@ SIGNATURES = {
     "cr_merge_pass": ([INT, INT, P, P, I64, I64, P, P, P, SZ, P], INT),
     "cr_merge_pass_backward": ([INT, INT, P, I64, I64, P, P, P, SZ, P], INT),
     "cr_workspace_status": ([P, P], INT),
+    "cr_sort_run_length": ([], I64),
+    "cr_sort_runs": ([INT, INT, P, P, I64, P, P, P], INT),
+    "cr_sort_runs_backward": ([INT, INT, P, I64, P, P, P], INT),
     "cr_stable_merge_noalloc": ([INT, P, I64, P, I64, P, P, P], INT),
 }
 

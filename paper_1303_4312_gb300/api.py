@@ -486,20 +486,58 @@ def workspace_status(ws: torch.Tensor) -> None:
 # bottom-up stable merge sort: a chain of merge passes, optionally replayed
 # from CUDA graphs
 # ---------------------------------------------------------------------------
-class MergeSortPlan:
-    """Buffers and (optionally) CUDA graphs for sorting N keys with payloads
-    whose runs of `run` elements are already sorted.
+def sort_run_length() -> int:
+    """Length of the runs cr_sort_runs sorts (the merge sort's first width)."""
+    return int(_lib.load().cr_sort_run_length())
 
+
+def sort_runs(X, Xv=None, key_type: str | None = None, out=None):
+    """Stably sort every run of sort_run_length() elements of X (payload Xv
+    follows).  Returns (Y, Yv)."""
+    lib = _lib.load()
+    dev = _dev(X, Xv)
+    kt = _key_code(X, key_type)
+    vb = Xv.element_size() if Xv is not None else 0
+    if out is None:
+        Y = torch.empty_like(X)
+        Yv = torch.empty_like(Xv) if Xv is not None else None
+    else:
+        Y, Yv = out
+    _lib.check(lib.cr_sort_runs(kt, vb, _ptr(X), _ptr(Xv), X.numel(), _ptr(Y), _ptr(Yv),
+                                _stream(dev)))
+    return Y, Yv
+
+
+def sort_runs_backward(X, gY, key_type: str | None = None, out=None):
+    """Payload gradient of sort_runs; X are its input keys."""
+    lib = _lib.load()
+    dev = _dev(X, gY)
+    kt = _key_code(X, key_type)
+    gX = out if out is not None else torch.empty_like(gY)
+    _lib.check(lib.cr_sort_runs_backward(kt, gY.element_size(), _ptr(X), X.numel(), _ptr(gY),
+                                         _ptr(gX), _stream(dev)))
+    return gX
+
+
+class MergeSortPlan:
+    """Buffers and (optionally) CUDA graphs for a stable merge sort of N keys
+    with payloads.
+
+    With ``run`` given, the input's runs of ``run`` elements must already be
+    sorted; with ``run=None`` the plan first sorts runs of
+    sort_run_length() itself (run formation), so any input is accepted.
     Pass p merges runs of width run * 2^p.  The input keys of every pass are
     kept (they are what the backward pass re-co-ranks), so keys need
-    (passes + 1) * N slots; payloads and gradients ping-pong between two
-    buffers.  Forward and backward are each captured once into a CUDA graph
-    (``graph=True``) and replayed.
+    (passes + 1) * N slots (+ N for the unsorted input); payloads and
+    gradients ping-pong between two buffers.  Forward and backward are each
+    captured once into a CUDA graph (``graph=True``) and replayed.
     """
 
-    def __init__(self, N: int, run: int, key_dtype, val_dtype, device="cuda",
+    def __init__(self, N: int, run: int | None, key_dtype, val_dtype, device="cuda",
                  key_type: str | None = None, graph: bool = True):
-        self.N, self.run = int(N), int(run)
+        self.N = int(N)
+        self.form_runs = run is None
+        self.run = sort_run_length() if run is None else int(run)
         self.device = torch.device(device)
         self.key_type = key_type
         self.widths = []
@@ -511,6 +549,8 @@ class MergeSortPlan:
         self.keys = [torch.empty(self.N, dtype=key_dtype, device=self.device) for _ in range(P + 1)]
         self.vals = [torch.empty(self.N, dtype=val_dtype, device=self.device) for _ in range(2)]
         self.grads = [torch.empty(self.N, dtype=val_dtype, device=self.device) for _ in range(2)]
+        self.input_keys = (torch.empty(self.N, dtype=key_dtype, device=self.device)
+                           if self.form_runs else None)
         kt = key_type or _DTYPE_KEY[key_dtype]
         vb = torch.empty(0, dtype=val_dtype).element_size()
         need = max([merge_pass_workspace_bytes(kt, vb, self.N, w) for w in self.widths] + [256])
@@ -523,7 +563,18 @@ class MergeSortPlan:
     def passes(self) -> int:
         return len(self.widths)
 
+    def _load(self, X, Xv):
+        if self.form_runs:
+            self.input_keys.copy_(X)
+            self.vals[1].copy_(Xv)
+        else:
+            self.keys[0].copy_(X)
+            self.vals[0].copy_(Xv)
+
     def _forward_body(self):
+        if self.form_runs:
+            sort_runs(self.input_keys, self.vals[1], key_type=self.key_type,
+                      out=(self.keys[0], self.vals[0]))
         for p, w in enumerate(self.widths):
             merge_pass(self.keys[p], self.vals[p & 1], w, key_type=self.key_type,
                        out=(self.keys[p + 1], self.vals[(p + 1) & 1]), ws=self.ws)
@@ -533,6 +584,12 @@ class MergeSortPlan:
             src = self.grads[(p + 1) & 1]
             merge_pass_backward(self.keys[p], src, self.widths[p], key_type=self.key_type,
                                 out=self.grads[p & 1], ws=self.ws)
+        if self.form_runs:
+            sort_runs_backward(self.input_keys, self.grads[0], key_type=self.key_type,
+                               out=self.grads[1])
+
+    def _grad_out(self):
+        return self.grads[1] if self.form_runs else self.grads[0]
 
     def _capture(self, body):
         s = torch.cuda.Stream(self.device)
@@ -547,13 +604,11 @@ class MergeSortPlan:
 
     def forward(self, X: torch.Tensor, Xv: torch.Tensor):
         """Sort; returns views of the plan's output buffers (keys, payloads)."""
-        self.keys[0].copy_(X)
-        self.vals[0].copy_(Xv)
-        if self.use_graph and self.passes:
+        self._load(X, Xv)
+        if self.use_graph and (self.passes or self.form_runs):
             if self._gf is None:
                 self._gf = self._capture(self._forward_body)
-                self.keys[0].copy_(X)
-                self.vals[0].copy_(Xv)
+                self._load(X, Xv)
             self._gf.replay()
         else:
             self._forward_body()
@@ -562,14 +617,14 @@ class MergeSortPlan:
     def backward(self, gY: torch.Tensor) -> torch.Tensor:
         """Payload gradient of the sort: gX[perm[t]] = gY[t]."""
         self.grads[self.passes & 1].copy_(gY)
-        if self.use_graph and self.passes:
+        if self.use_graph and (self.passes or self.form_runs):
             if self._gb is None:
                 self._gb = self._capture(self._backward_body)
                 self.grads[self.passes & 1].copy_(gY)
             self._gb.replay()
         else:
             self._backward_body()
-        return self.grads[0]
+        return self._grad_out()
 
 
 class _MergeSortFn(torch.autograd.Function):
@@ -587,10 +642,13 @@ class _MergeSortFn(torch.autograd.Function):
         return None, ctx.plan.backward(gYv.contiguous()).clone(), None
 
 
-def merge_sort(X: torch.Tensor, Xv: torch.Tensor, run: int = 1024, key_type: str | None = None,
-               graph: bool = True, plan: MergeSortPlan | None = None):
-    """Stable merge sort of X (runs of `run` already sorted) carrying payloads
-    Xv; differentiable in Xv.  Returns (keys, payloads)."""
+def merge_sort(X: torch.Tensor, Xv: torch.Tensor, run: int | None = None,
+               key_type: str | None = None, graph: bool = True,
+               plan: MergeSortPlan | None = None):
+    """Stable merge sort of X carrying payloads Xv; differentiable in Xv.
+    run=None sorts any input (runs are formed on the GPU first); an integer
+    run declares that X's runs of that width are already sorted.  Returns
+    (keys, payloads)."""
     _dev(X, Xv)
     if plan is None:
         plan = MergeSortPlan(X.numel(), run, X.dtype, Xv.dtype, X.device, key_type, graph)

@@ -440,6 +440,27 @@ cr_status cr_merge_partition(int key_type, int val_bytes, const void* A, int64_t
     return ok();
 }
 
+cr_status cr_merge_partition_alg2(int key_type, int val_bytes, const void* A, int64_t m,
+                                  const void* B, int64_t n, void* ws, size_t ws_bytes,
+                                  cr_stream stream) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, true));
+    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    const int ks = key_bytes(key_type);
+    CR_TRY(check_arr({A, m, ks, "A"}));
+    CR_TRY(check_arr({B, n, ks, "B"}));
+    if (m + n == 0) return ok();
+    int64_t tile = 0;
+    const int64_t ntiles = single_tiles(shape_of(key_type, val_bytes, m, n), m, n, &tile);
+    CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = by_key(key_type, [&](auto ops) {
+        return ops.partition_single_free(A, m, B, n, tile, ntiles, ws, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "partition launch");
+    return ok();
+}
+
 cr_status cr_merge_tiles(int key_type, int val_bytes, const void* Ak, const void* Av, int64_t m,
                          const void* Bk, const void* Bv, int64_t n, void* Ck, void* Cv,
                          uint32_t* C_tag, void* ws, size_t ws_bytes, cr_stream stream) {
@@ -630,6 +651,47 @@ cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int
                                  size_t ws_bytes, cr_stream stream) {
     return pass_common(true, key_type, val_bytes, X, nullptr, N, width, gY, nullptr, nullptr, gX,
                        ws, ws_bytes, stream);
+}
+
+int64_t cr_sort_run_length(void) { return cr::kSortRun; }
+
+cr_status cr_sort_runs(int key_type, int val_bytes, const void* X, const void* Xv, int64_t N,
+                       void* Y, void* Yv, cr_stream stream) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, true));
+    if (N < 0) return fail(CR_EINVAL, "negative size");
+    const int ks = key_bytes(key_type);
+    const int vb = val_bytes;
+    const Arr ins[2] = {{X, N, ks, "X"}, {vb ? Xv : nullptr, vb ? N : 0, vb, "X payload"}};
+    const Arr outs[2] = {{Y, N, ks, "Y"}, {vb ? Yv : nullptr, vb ? N : 0, vb, "Y payload"}};
+    for (const Arr& a : ins) CR_TRY(check_arr(a));
+    for (const Arr& a : outs) CR_TRY(check_arr(a));
+    CR_TRY(check_no_alias(outs, 2, ins, 2));
+    if (N == 0) return ok();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = by_key(key_type, [&](auto ops) { return ops.sort_runs(vb, X, Xv, N, Y, Yv, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "run sort launch");
+    return ok();
+}
+
+cr_status cr_sort_runs_backward(int key_type, int val_bytes, const void* X, int64_t N,
+                                const void* gY, void* gX, cr_stream stream) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, false));
+    if (N < 0) return fail(CR_EINVAL, "negative size");
+    const int ks = key_bytes(key_type);
+    const Arr ins[2] = {{X, N, ks, "X"}, {gY, N, val_bytes, "gY"}};
+    const Arr outs[1] = {{gX, N, val_bytes, "gX"}};
+    for (const Arr& a : ins) CR_TRY(check_arr(a));
+    CR_TRY(check_arr(outs[0]));
+    CR_TRY(check_no_alias(outs, 1, ins, 2));
+    if (N == 0) return ok();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = by_key(key_type, [&](auto ops) {
+        return ops.sort_runs_backward(val_bytes, X, N, gY, gX, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "run sort backward launch");
+    return ok();
 }
 
 cr_status cr_workspace_status(const void* ws, cr_stream stream) {

@@ -7,6 +7,7 @@
 #include "cr_launch.cuh"
 #include "cr_merge.cuh"
 #include "cr_partition.cuh"
+#include "cr_sort.cuh"
 
 namespace cr {
 
@@ -122,6 +123,17 @@ cudaError_t KeyOps<K>::partition_single(const void* A, int64_t m, const void* B,
 }
 
 template <class K>
+cudaError_t KeyOps<K>::partition_single_free(const void* A, int64_t m, const void* B, int64_t n,
+                                             int64_t tile, int64_t ntiles, void* ws,
+                                             cudaStream_t st) {
+    const unsigned g = blocks_for(ntiles > 0 ? ntiles : 1, 256);
+    partition_single_free_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(A), m,
+                                                        static_cast<const K*>(B), n, tile, ntiles,
+                                                        ws);
+    return cudaGetLastError();
+}
+
+template <class K>
 cudaError_t KeyOps<K>::partition_pass(const void* X, int64_t N, int64_t w, int64_t tile,
                                       void* ws, int64_t* ntiles_out, cudaStream_t st) {
     int64_t tpp = 1, npairs = 0;
@@ -145,6 +157,40 @@ cudaError_t KeyOps<K>::partition_batched(const void* A, const void* B, const int
     partition_batched_kernel<K><<<blocks_for(max_tiles, 256), 256, 0, st>>>(
         static_cast<const K*>(A), static_cast<const K*>(B), a_off, b_off, nseg, tile, prefix, ws);
     return cudaGetLastError();
+}
+
+template <class K, int VB, bool BWD>
+cudaError_t launch_sort_runs(const void* X, const void* Xv, int64_t N, void* Y, void* Yv,
+                             const void* gY, void* gX, cudaStream_t st) {
+    using L = SortLayout<K, VB, BWD, kSortNT, kSortIPT>;
+    auto kern = sort_runs_kernel<K, VB, BWD, kSortNT, kSortIPT>;
+    static LaunchShape cache[kMaxDevices];
+    static std::once_flag once[kMaxDevices];
+    LaunchShape sh;
+    cudaError_t e = launch_shape(kern, kSortNT, L::TOTAL, cache, once, sh);
+    if (e != cudaSuccess) return e;
+    if (N <= 0) return cudaSuccess;
+    const unsigned grid = unsigned((N + kSortRun - 1) / kSortRun);
+    kern<<<grid, kSortNT, L::TOTAL, st>>>(static_cast<const K*>(X), Xv, N, static_cast<K*>(Y), Yv,
+                                          gY, gX);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t KeyOps<K>::sort_runs(int vb, const void* X, const void* Xv, int64_t N, void* Y,
+                                 void* Yv, cudaStream_t st) {
+    if (vb == 0) return launch_sort_runs<K, 0, false>(X, Xv, N, Y, Yv, nullptr, nullptr, st);
+    if (vb == 4) return launch_sort_runs<K, 4, false>(X, Xv, N, Y, Yv, nullptr, nullptr, st);
+    if (vb == 8) return launch_sort_runs<K, 8, false>(X, Xv, N, Y, Yv, nullptr, nullptr, st);
+    return cudaErrorInvalidValue;
+}
+
+template <class K>
+cudaError_t KeyOps<K>::sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
+                                          void* gX, cudaStream_t st) {
+    if (vb == 4) return launch_sort_runs<K, 4, true>(X, nullptr, N, nullptr, nullptr, gY, gX, st);
+    if (vb == 8) return launch_sort_runs<K, 8, true>(X, nullptr, N, nullptr, nullptr, gY, gX, st);
+    return cudaErrorInvalidValue;
 }
 
 template <class K>
@@ -178,6 +224,9 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
     template cudaError_t cr::KeyOps<K>::partition_single(const void*, int64_t, const void*,    \
                                                          int64_t, int64_t, int64_t, void*,     \
                                                          cudaStream_t);                        \
+    template cudaError_t cr::KeyOps<K>::partition_single_free(const void*, int64_t, const void*,\
+                                                              int64_t, int64_t, int64_t, void*, \
+                                                              cudaStream_t);                    \
     template cudaError_t cr::KeyOps<K>::partition_pass(const void*, int64_t, int64_t, int64_t, \
                                                        void*, int64_t*, cudaStream_t);         \
     template cudaError_t cr::KeyOps<K>::partition_batched(                                     \
@@ -187,5 +236,9 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
                                                      int64_t, const int64_t*, int64_t,         \
                                                      int64_t*, int64_t*, cudaStream_t);        \
     template cudaError_t cr::KeyOps<K>::co_rank_one(const void*, int64_t, const void*,         \
-                                                    int64_t, int64_t, int64_t*, cudaStream_t);
+                                                    int64_t, int64_t, int64_t*, cudaStream_t); \
+    template cudaError_t cr::KeyOps<K>::sort_runs(int, const void*, const void*, int64_t,      \
+                                                  void*, void*, cudaStream_t);                 \
+    template cudaError_t cr::KeyOps<K>::sort_runs_backward(int, const void*, int64_t,          \
+                                                           const void*, void*, cudaStream_t);
 

@@ -76,6 +76,10 @@ inline int geometry_class(int64_t m, int64_t n) {
 // owns the table).
 int current_shape(int key_bytes, int vb, int cls);
 
+// Run formation shape: 256 threads x 7 elements per run.
+constexpr int kSortNT = 256, kSortIPT = 7;
+constexpr int64_t kSortRun = int64_t(kSortNT) * kSortIPT;
+
 inline int64_t tile_of_shape(int s) {
     return int64_t(kShapes[s].nt) * kShapes[s].ipt * kShapes[s].ilp;
 }
@@ -91,6 +95,10 @@ struct KeyOps {
                                  cudaStream_t st);
     static cudaError_t partition_single(const void* A, int64_t m, const void* B, int64_t n,
                                         int64_t tile, int64_t ntiles, void* ws, cudaStream_t st);
+    // Same table, every tile co-ranking both of its ends (Algorithm 1).
+    static cudaError_t partition_single_free(const void* A, int64_t m, const void* B, int64_t n,
+                                             int64_t tile, int64_t ntiles, void* ws,
+                                             cudaStream_t st);
     static cudaError_t partition_pass(const void* X, int64_t N, int64_t w, int64_t tile,
                                       void* ws, int64_t* ntiles_out, cudaStream_t st);
     static cudaError_t partition_batched(const void* A, const void* B, const int64_t* a_off,
@@ -102,6 +110,12 @@ struct KeyOps {
                                     cudaStream_t st);
     static cudaError_t co_rank_one(const void* A, int64_t m, const void* B, int64_t n, int64_t r,
                                    int64_t* out, cudaStream_t st);
+    // Run formation: stably sort runs of kSortRun elements (vb 0, 4, 8);
+    // backward (vb 4, 8): gX from gY through the same in-run permutation.
+    static cudaError_t sort_runs(int vb, const void* X, const void* Xv, int64_t N, void* Y,
+                                 void* Yv, cudaStream_t st);
+    static cudaError_t sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
+                                          void* gX, cudaStream_t st);
 };
 
 // Tiles of a merge pass over N elements with run width w.

@@ -175,6 +175,29 @@ __global__ void __launch_bounds__(256) partition_single_kernel(const K* A, int64
     }
 }
 
+// Single merge, sync-free form of Algorithm 2: tile t co-ranks both of its
+// ends itself with Algorithm 1 as printed (the two searches in lock step),
+// sharing nothing with other tiles.  Same records as partition_single_kernel.
+template <class K>
+__global__ void __launch_bounds__(256) partition_single_free_kernel(const K* A, int64_t m,
+                                                                    const K* B, int64_t n,
+                                                                    int64_t tile, int64_t ntiles,
+                                                                    void* ws) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        WsHeader* h = static_cast<WsHeader*>(ws);
+        h->status = kDevOk;
+        h->tile = int32_t(tile);
+        h->ntiles = ntiles;
+    }
+    if (t >= ntiles) return;
+    const int64_t r0 = t * tile;
+    const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
+    int64_t j0, j1;
+    co_rank_pair(r0, r1, A, m, B, n, j0, j1);
+    ws_recs(ws)[t] = make_rec(0, 0, 0, r0, r1, j0, j1);
+}
+
 // One bottom-up merge-sort pass over X[0, N): pair q merges the runs
 // X[2qw, 2qw+w) and X[2qw+w, 2qw+2w) (cut at N).  Tiles never straddle pairs;
 // every pair but the last has tpp = ceil(2w / tile) tiles.

@@ -434,3 +434,91 @@ def test_sharded_merge_single_rank_nccl():
         assert same_bits(host(C, np.int32), oracle.merge(A, B)[0])
     finally:
         dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+def test_partition_alg2_table_matches(dt):
+    """The sync-free partition (every tile co-ranks both ends with Algorithm 1)
+    writes the same tile table as the shared partition: the merge is equal."""
+    import ctypes
+    from paper_1303_4312_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(113)
+    kt = key_type(np.empty(0, dt))
+    code = _lib.KEY_TYPES[kt]
+    for m, n, spread in [(300001, 200003, None), (5, 400000, None), (250000, 250000, 4)]:
+        A = sorted_keys(rng, m, dt, spread)
+        B = sorted_keys(rng, n, dt, spread)
+        Ad, Bd = dev(A), dev(B)
+        need = ctypes.c_size_t()
+        _lib.check(lib.cr_merge_workspace_size(code, 0, m, n, ctypes.byref(need)))
+        s = torch.cuda.current_stream().cuda_stream
+        tables = []
+        for fn in (lib.cr_merge_partition, lib.cr_merge_partition_alg2):
+            ws = torch.zeros(need.value, dtype=torch.uint8, device="cuda")
+            _lib.check(fn(code, 0, Ad.data_ptr(), m, Bd.data_ptr(), n, ws.data_ptr(), ws.numel(), s))
+            C = torch.empty(m + n, dtype=Ad.dtype, device="cuda")
+            _lib.check(lib.cr_merge_tiles(code, 0, Ad.data_ptr(), None, m, Bd.data_ptr(), None, n,
+                                          C.data_ptr(), None, None, ws.data_ptr(), ws.numel(), s))
+            torch.cuda.synchronize()
+            cr.workspace_status(ws)
+            assert same_bits(host(C, dt), oracle.merge(A, B)[0])
+            tables.append(ws.cpu())
+        assert torch.equal(tables[0][8:], tables[1][8:])   # same records (header tile/ntiles too)
+
+
+@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+@pytest.mark.parametrize("vdt", [None, np.float32, np.float64])
+def test_sort_runs_and_backward(dt, vdt):
+    """Run formation: every run of sort_run_length() elements stably sorted
+    (payloads follow; equal keys keep input order), and its backward."""
+    rng = np.random.default_rng(114)
+    R = cr.sort_run_length()
+    kt = key_type(np.empty(0, dt))
+    for N in (1, 5, R - 1, R, R + 1, 7 * R + 333):
+        for spread in (None, 3):
+            info = np.iinfo(dt)
+            X = (rng.integers(info.min, info.max, N, dtype=dt, endpoint=True) if spread is None
+                 else rng.integers(0, spread, N).astype(dt))
+            Xv = rng.standard_normal(N).astype(vdt or np.float32)
+            Y, Yv = cr.sort_runs(dev(X), dev(Xv) if vdt else None, key_type=kt)
+            torch.cuda.synchronize()
+            want = np.empty_like(X)
+            wantv = np.empty_like(Xv)
+            perm = np.empty(N, np.int64)
+            for a0 in range(0, N, R):
+                o = np.argsort(X[a0:a0 + R], kind="stable")
+                want[a0:a0 + R] = X[a0:a0 + R][o]
+                wantv[a0:a0 + R] = Xv[a0:a0 + R][o]
+                perm[a0:a0 + R] = a0 + o
+            assert same_bits(host(Y, dt), want), (N, spread)
+            if vdt:
+                assert same_bits(host(Yv, vdt), wantv), (N, spread)
+                gY = rng.standard_normal(N).astype(vdt)
+                gX = cr.sort_runs_backward(dev(X), dev(gY), key_type=kt)
+                torch.cuda.synchronize()
+                g = np.empty_like(gY)
+                g[perm] = gY
+                assert same_bits(host(gX, vdt), g), (N, spread)
+
+
+def test_merge_sort_from_unsorted_input():
+    """Full stable sort of unsorted input (run formation, then merge passes in
+    CUDA graphs) and its payload gradient, against numpy's stable argsort."""
+    rng = np.random.default_rng(115)
+    for N in (1, 1000, 100003, 1 << 20):
+        vals = rng.integers(0, 2**64, 4000, dtype=np.uint64)
+        X = vals[rng.integers(0, len(vals), N)]
+        Xv = rng.standard_normal(N).astype(np.float32)
+        Xt = dev(X)
+        Xvt = dev(Xv).requires_grad_(True)
+        Y, Yv = cr.merge_sort(Xt, Xvt, key_type="u64")
+        gY = rng.standard_normal(N).astype(np.float32)
+        Yv.backward(dev(gY))
+        torch.cuda.synchronize()
+        o = np.argsort(X, kind="stable")
+        assert same_bits(host(Y, np.uint64), X[o])
+        assert same_bits(host(Yv.detach(), np.float32), Xv[o])
+        g = np.empty_like(gY)
+        g[o] = gY
+        assert same_bits(host(Xvt.grad, np.float32), g)
