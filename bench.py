@@ -618,9 +618,33 @@ def run_row(args):
         torch.cuda.synchronize()
         tot = timer.totals()
         P = plan.passes
+        # per-pass breakdown outside the graphs: partition and tile kernel of
+        # every pass, forward and backward
+        code = _lib.KEY_TYPES["u64"]
+        per_pass = []
+        ws = plan.ws
+        for p_, w in enumerate(plan.widths):
+            X_, Y_ = plan.keys[p_], plan.keys[p_ + 1]
+            Xv_, Yv_ = plan.vals[p_ & 1], plan.vals[(p_ + 1) & 1]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            for rep in range(2):
+                ev[0].record(stream)
+                _lib.check(lib.cr_merge_pass(code, 4, ptr(X_), ptr(Xv_), N, w, ptr(Y_), ptr(Yv_),
+                                             ptr(ws), ws.numel(), sp))
+                ev[1].record(stream)
+                _lib.check(lib.cr_merge_pass_backward(code, 4, ptr(X_), N, w, ptr(gY),
+                                                      ptr(plan.grads[0]), ptr(ws), ws.numel(), sp))
+                ev[2].record(stream)
+            torch.cuda.synchronize()
+            f = ev[0].elapsed_time(ev[1])
+            b = ev[1].elapsed_time(ev[2])
+            per_pass.append({"width": w, "fwd_ms": round(f, 4), "bwd_ms": round(b, 4),
+                             "fwd_gbs": round(24 * N / (f / 1e3) / 1e9, 1),
+                             "bwd_gbs": round(16 * N / (b / 1e3) / 1e9, 1)})
         return finish(tot, {"fwd_graph": 24 * N * P, "bwd_graph": 16 * N * P}, "sort_u64_f32",
-                      N, {"passes": P, "note": "each graph replays its passes' partition and "
-                          "tile-merge launches; bytes are per pass, times passes"})
+                      N, {"passes": P, "per_pass": per_pass,
+                          "note": "each graph replays its passes' partition and tile-merge "
+                                  "launches; bytes are per pass, times passes"})
     raise ValueError(args.workload)
 
 

@@ -578,6 +578,7 @@ cr_status pass_common(bool backward, int key_type, int val_bytes, const void* X,
         CR_TRY(check_no_alias(outs, 1, ins, 2));
     }
     if (N == 0) return ok();
+    if (width > N) width = N;   // one pair with an empty second run: the same result
     const int shape = shape_of(key_type, vb);
     const int64_t tile = cr::tile_of_shape(shape);
     const int64_t ntiles = cr::pass_tiles(N, width, tile, nullptr, nullptr);
@@ -635,6 +636,7 @@ cr_status cr_merge_pass_workspace_size(int key_type, int val_bytes, int64_t N, i
     if (N < 0 || width < 1) return fail(CR_EINVAL, "bad size or width");
     if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
     const int64_t tile = cr::tile_of_shape(shape_of(key_type, val_bytes));
+    if (width > N) width = N > 0 ? N : 1;
     *bytes = single_ws_bytes(cr::pass_tiles(N, width, tile, nullptr, nullptr));
     return ok();
 }

@@ -139,7 +139,8 @@ cudaError_t KeyOps<K>::partition_pass(const void* X, int64_t N, int64_t w, int64
     int64_t tpp = 1, npairs = 0;
     const int64_t ntiles = pass_tiles(N, w, tile, &tpp, &npairs);
     if (ntiles_out) *ntiles_out = ntiles;
-    const unsigned g = blocks_for(ntiles > 0 ? ntiles : 1, 256);
+    // 256 threads co-rank 256 consecutive tile starts = 255 tiles per block
+    const unsigned g = unsigned(((ntiles > 0 ? ntiles : 1) + 254) / 255);
     partition_pass_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(X), N, w, tile, tpp,
                                                  npairs, ntiles, ws);
     return cudaGetLastError();

@@ -201,29 +201,89 @@ __global__ void __launch_bounds__(256) partition_single_free_kernel(const K* A, 
 // One bottom-up merge-sort pass over X[0, N): pair q merges the runs
 // X[2qw, 2qw+w) and X[2qw+w, 2qw+2w) (cut at N).  Tiles never straddle pairs;
 // every pair but the last has tpp = ceil(2w / tile) tiles.
+//
+// The two steps of partition_single_kernel, applied pair by pair: a block of
+// 256 threads owns tiles tb .. tb+254 and the 256 tile starts tb .. tb+255.
+//  1. warp 0 co-ranks the first and the last of those starts inside their
+//     own pairs (16 lanes each, co_rank_group);
+//  2. every thread bisects for its own start between the trivial bounds of
+//     its pair, [max(0, r-n), min(r, m)], narrowed by step 1's co-ranks when
+//     it shares their pair (co-ranks grow with the rank inside a pair).
+// A tile ends where the next tile of its pair starts, or at the pair's end,
+// whose co-rank is m.
+struct PassPos {
+    int64_t q, r, m, n;   // pair, rank inside the pair, run lengths
+};
+
+__device__ __forceinline__ PassPos pass_locate(int64_t tt, int64_t N, int64_t w, int64_t tile,
+                                               int64_t tpp, int64_t npairs) {
+    PassPos p;
+    p.q = tt / tpp;
+    if (p.q > npairs - 1) p.q = npairs - 1;   // tt == ntiles: end of the last pair
+    const int64_t a0 = 2 * p.q * w;
+    p.m = w < N - a0 ? w : N - a0;
+    const int64_t nb = N - a0 - p.m;
+    p.n = w < nb ? w : nb;
+    p.r = (tt - p.q * tpp) * tile;
+    if (p.r > p.m + p.n) p.r = p.m + p.n;
+    return p;
+}
+
 template <class K>
-__global__ void partition_pass_kernel(const K* X, int64_t N, int64_t w, int64_t tile, int64_t tpp,
-                                      int64_t npairs, int64_t ntiles, void* ws) {
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t == 0) {
+__global__ void __launch_bounds__(256) partition_pass_kernel(const K* X, int64_t N, int64_t w,
+                                                             int64_t tile, int64_t tpp,
+                                                             int64_t npairs, int64_t ntiles,
+                                                             void* ws) {
+    __shared__ int64_t s_j[256];
+    __shared__ int64_t s_jb[2];
+    __shared__ int64_t s_qb[2];
+    const int64_t tb = int64_t(blockIdx.x) * 255;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         WsHeader* h = static_cast<WsHeader*>(ws);
         h->status = kDevOk;
         h->tile = int32_t(tile);
         h->ntiles = ntiles;
     }
-    if (t >= ntiles) return;
-    int64_t q = t / tpp;
-    if (q > npairs - 1) q = npairs - 1;
-    const int64_t a0 = 2 * q * w;
-    const int64_t m = w < N - a0 ? w : N - a0;
-    const int64_t b0 = a0 + m;
-    const int64_t nb = N - b0;
-    const int64_t n = w < nb ? w : nb;
-    const int64_t r0 = (t - q * tpp) * tile;
-    const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
-    int64_t j0, j1;
-    co_rank_pair(r0, r1, X + a0, m, X + b0, n, j0, j1);
-    ws_recs(ws)[t] = make_rec(a0, b0, a0, r0, r1, j0, j1);
+    if (threadIdx.x < 32) {
+        const int grp = threadIdx.x >> 4;
+        const int64_t tt = grp == 0 ? tb : (tb + 255 < ntiles ? tb + 255 : ntiles);
+        const PassPos p = pass_locate(tt, N, w, tile, tpp, npairs);
+        const K* A = X + 2 * p.q * w;
+        const int64_t j = co_rank_group<K, 16>(A, p.m, A + p.m, p.n, p.r, threadIdx.x & 15,
+                                               0xFFFFu << (16 * grp), 16 * grp);
+        if ((threadIdx.x & 15) == 0) {
+            s_jb[grp] = j;
+            s_qb[grp] = p.q;
+        }
+    }
+    __syncthreads();
+    const int64_t tt = tb + threadIdx.x;
+    if (tt <= ntiles) {
+        const PassPos p = pass_locate(tt, N, w, tile, tpp, npairs);
+        const K* A = X + 2 * p.q * w;
+        const K* B = A + p.m;
+        int64_t lo = p.r - p.n > 0 ? p.r - p.n : 0;
+        int64_t hi = p.r < p.m ? p.r : p.m;
+        if (p.q == s_qb[0] && s_jb[0] > lo) lo = s_jb[0];
+        if (p.q == s_qb[1] && s_jb[1] < hi) hi = s_jb[1];
+        // largest j in [lo, hi] with the first condition true at (j, r-j)
+#pragma unroll 1
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;   // > lo >= 0
+            const int64_t k = p.r - mid;
+            const bool c1 = k >= p.n || (k >= 0 && !(B[k] < A[mid - 1]));
+            if (c1) lo = mid; else hi = mid - 1;
+        }
+        s_j[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < 255 && tt < ntiles) {
+        const PassPos p = pass_locate(tt, N, w, tile, tpp, npairs);
+        const int64_t r1 = p.r + tile < p.m + p.n ? p.r + tile : p.m + p.n;
+        const int64_t j1 = r1 == p.m + p.n ? p.m : s_j[threadIdx.x + 1];
+        const int64_t a0 = 2 * p.q * w;
+        ws_recs(ws)[tt] = make_rec(a0, a0 + p.m, a0, p.r, r1, s_j[threadIdx.x], j1);
+    }
 }
 
 // Batched merge, step 1 (one CTA of 1024 threads): validate the segment
