@@ -72,7 +72,34 @@ def parse_args():
                             "partition_variants"],
                    help="the default is the headline workload; the others measure the "
                         "remaining rows of the path (one JSON line each)")
+    p.add_argument("--tile-shape", type=int, default=None,
+                   help="force tile shape S (cr_tile_shape_info) for every key type and "
+                        "payload width it fits, instead of the tuned table")
     return p.parse_args()
+
+
+def force_tile_shape(lib, shape):
+    """--tile-shape: select `shape` wherever it fits (others keep theirs)."""
+    if shape is None:
+        return
+    for code in range(4):
+        for vb in (0, 4, 8):
+            lib.cr_set_tile_shape(code, vb, shape)
+
+
+def tile_shapes(lib, combos):
+    """NTxIPTxILP of the balanced and skewed shape for each (label, key code, vb)."""
+    import ctypes
+    out = {}
+    for label, code, vb in combos:
+        row = []
+        for cls in (0, 1):
+            s = lib.cr_get_tile_shape_for(code, vb, cls)
+            nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            lib.cr_tile_shape_info(s, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
+            row.append(f"{nt.value}x{ipt.value}x{ilp.value}")
+        out[label] = row if row[0] != row[1] else row[0]
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -224,6 +251,7 @@ def run_ours(args, rank, world, local, dist):
 
     build.build()
     lib = _lib.load()
+    force_tile_shape(lib, args.tile_shape)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
@@ -315,7 +343,8 @@ def run_ours(args, rank, world, local, dist):
         "data": "synthetic (seeded, sorted; device-generated)",
         "config": {"workload": WORKLOAD, "merges": [f"{m[0]}" for m in MERGES],
                    "elements_per_step": elems, "l2": "inputs larger than L2 (no flush)",
-                   "size_shift": args.shift, "parallelism": f"replicas x{world}"},
+                   "size_shift": args.shift, "parallelism": f"replicas x{world}",
+                   "tile_shapes": tile_shapes(lib, [("int32", 0, 0), ("uint64", 3, 0)])},
         "hbm_gbs_step": round(step_gbs, 1),
         "frac_of_peak_step": round(step_gbs / peak, 4),
         "per_merge": per_merge,
@@ -413,6 +442,7 @@ def run_row(args):
     from paper_1303_4312_gb300 import workloads as W
     build.build()
     lib = _lib.load()
+    force_tile_shape(lib, args.tile_shape)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -423,11 +453,12 @@ def run_row(args):
            "higher_is_better": True, "data": "synthetic (seeded)", "peak_gbs": peak,
            "peak_source": peak_kind}
 
-    def finish(timer_totals, alg, name, elems, extra=None):
+    def finish(timer_totals, alg, name, elems, extra=None, combos=()):
         step_ms = sum(timer_totals.values()) / K
         res.update({"value": elems / (step_ms / 1e3), "ms_per_step": step_ms,
                     "config": {"workload": name, "elements_per_step": elems,
-                               "size_shift": args.shift}})
+                               "size_shift": args.shift,
+                               "tile_shapes": tile_shapes(lib, combos)}})
         kern = {}
         for label, ms in timer_totals.items():
             b = alg.get(label)
@@ -467,7 +498,8 @@ def run_row(args):
         api.workspace_status(ws)
         tot = {k: v for k, v in timer.totals().items()}
         return finish(tot, {"tiles_keys_tags": 12 * (m + n)}, "single_i32_tag", m + n,
-                      {"l2": "flushed between steps (256 MB write)"})
+                      {"l2": "flushed between steps (256 MB write)"},
+                      combos=[("int32", 0, 0)])
 
     if args.workload == "partition_variants":
         # the paper's two forms of the block co-ranks: shared (computed once
@@ -553,7 +585,8 @@ def run_row(args):
                       {"fwd": {"ms": round(fwd_ms, 4), "elements_per_s": N / (fwd_ms / 1e3),
                                "gbs": round(16 * N / (fwd_ms / 1e3) / 1e9, 1)},
                        "bwd": {"ms": round(bwd_ms, 4), "elements_per_s": N / (bwd_ms / 1e3),
-                               "gbs": round(12 * N / (bwd_ms / 1e3) / 1e9, 1)}})
+                               "gbs": round(12 * N / (bwd_ms / 1e3) / 1e9, 1)}},
+                      combos=[("uint32+f32", 1, 4)])
 
     if args.workload == "batched":
         a_off, b_off, A, Av, B, Bv = W.t_batched_i32_f32(device=dev)
@@ -591,7 +624,8 @@ def run_row(args):
         N = at + bt
         return finish(tot, {"fwd": 16 * N, "bwd": 12 * N}, "batched_i32_f32", N,
                       {"segments": nseg, "note": "fwd/bwd include the segment scan and "
-                       "partition launches (3 kernels each)"})
+                       "partition launches (3 kernels each)"},
+                      combos=[("int32+f32", 0, 4)])
 
     if args.workload == "merge_sort":
         X, Xv = W.t_sort_u64_f32(device=dev, shift=args.shift)
@@ -644,7 +678,8 @@ def run_row(args):
         return finish(tot, {"fwd_graph": 24 * N * P, "bwd_graph": 16 * N * P}, "sort_u64_f32",
                       N, {"passes": P, "per_pass": per_pass,
                           "note": "each graph replays its passes' partition and tile-merge "
-                                  "launches; bytes are per pass, times passes"})
+                                  "launches; bytes are per pass, times passes"},
+                      combos=[("uint64+f32", 3, 4)])
     raise ValueError(args.workload)
 
 
