@@ -628,58 +628,92 @@ def run_row(args):
                       combos=[("int32+f32", 0, 4)])
 
     if args.workload == "merge_sort":
+        # Both backward forms of the merge-sort chain: "record" (each forward
+        # pass records its merge decisions, one bit per element, and the
+        # backward routes gradients from them) and "recompute" (the backward
+        # re-merges every pass's saved input keys).
         X, Xv = W.t_sort_u64_f32(device=dev, shift=args.shift)
         N = X.numel()
-        plan = api.MergeSortPlan(N, 1024, X.dtype, Xv.dtype, dev, key_type="u64", graph=True)
         gY = torch.randn(N, device=dev)
-        plan.forward(X, Xv)       # captures the forward graph
-        plan.backward(gY)         # captures the backward graph
-        timer = KernelTimer(stream)
-        for k in range(Wm + K):
-            t = k >= Wm
+        # algorithmic bytes per element and pass: forward keys + payloads in
+        # and out (+ one flag bit recorded); backward gY in, gX out (+ the
+        # flag bit, or the pass's input keys re-read)
+        fwd_b = {"record": 24 + 1 / 8, "recompute": 24}
+        bwd_b = {"record": 8 + 1 / 8, "recompute": 16}
+        rows, per_pass = {}, {}
+        for mode in ("record", "recompute"):
+            plan = api.MergeSortPlan(N, 1024, X.dtype, Xv.dtype, dev, key_type="u64",
+                                     graph=True, record=mode == "record")
+            plan.forward(X, Xv)       # captures the forward graph
+            plan.backward(gY)         # captures the backward graph
+            timer = KernelTimer(stream)
+            for k in range(Wm + K):
+                t = k >= Wm
+                plan.keys[0].copy_(X)
+                plan.vals[0].copy_(Xv)
+                plan.grads[plan.passes & 1].copy_(gY)
+                if t:
+                    timer.mark()
+                plan._gf.replay()
+                if t:
+                    timer.mark("fwd_graph")
+                plan._gb.replay()
+                if t:
+                    timer.mark("bwd_graph")
+                    timer.marks.append((None, timer.marks[-1][1]))
+            torch.cuda.synchronize()
+            rows[mode] = timer.totals()
+            # per-pass breakdown: the same chain pass by pass outside the
+            # graphs (partition + tile kernel, or the routing kernel)
+            P = plan.passes
             plan.keys[0].copy_(X)
             plan.vals[0].copy_(Xv)
-            plan.grads[plan.passes & 1].copy_(gY)
-            if t:
-                timer.mark()
-            plan._gf.replay()
-            if t:
-                timer.mark("fwd_graph")
-            plan._gb.replay()
-            if t:
-                timer.mark("bwd_graph")
-                timer.marks.append((None, timer.marks[-1][1]))
-        torch.cuda.synchronize()
-        tot = timer.totals()
-        P = plan.passes
-        # per-pass breakdown outside the graphs: partition and tile kernel of
-        # every pass, forward and backward
-        code = _lib.KEY_TYPES["u64"]
-        per_pass = []
-        ws = plan.ws
-        for p_, w in enumerate(plan.widths):
-            X_, Y_ = plan.keys[p_], plan.keys[p_ + 1]
-            Xv_, Yv_ = plan.vals[p_ & 1], plan.vals[(p_ + 1) & 1]
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-            for rep in range(2):
-                ev[0].record(stream)
-                _lib.check(lib.cr_merge_pass(code, 4, ptr(X_), ptr(Xv_), N, w, ptr(Y_), ptr(Yv_),
-                                             ptr(ws), ws.numel(), sp))
-                ev[1].record(stream)
-                _lib.check(lib.cr_merge_pass_backward(code, 4, ptr(X_), N, w, ptr(gY),
-                                                      ptr(plan.grads[0]), ptr(ws), ws.numel(), sp))
-                ev[2].record(stream)
+            plan.grads[P & 1].copy_(gY)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * P + 2)]
+            for p_, w in enumerate(plan.widths):
+                ev[p_].record(stream)
+                kin, kout = plan._key_buf(p_), plan._key_buf(p_ + 1)
+                out = (kout, plan.vals[(p_ + 1) & 1])
+                if mode == "record":
+                    api.merge_pass_record(kin, plan.vals[p_ & 1], w, key_type="u64", out=out,
+                                          record=plan.records[p_])
+                else:
+                    api.merge_pass(kin, plan.vals[p_ & 1], w, key_type="u64", out=out,
+                                   ws=plan.ws)
+            ev[P].record(stream)
+            for p_ in reversed(range(P)):
+                src, dst = plan.grads[(p_ + 1) & 1], plan.grads[p_ & 1]
+                if mode == "record":
+                    api.merge_pass_backward_recorded(plan.records[p_], src, out=dst)
+                else:
+                    api.merge_pass_backward(plan.keys[p_], src, plan.widths[p_],
+                                            key_type="u64", out=dst, ws=plan.ws)
+                ev[2 * P - p_].record(stream)
             torch.cuda.synchronize()
-            f = ev[0].elapsed_time(ev[1])
-            b = ev[1].elapsed_time(ev[2])
-            per_pass.append({"width": w, "fwd_ms": round(f, 4), "bwd_ms": round(b, 4),
-                             "fwd_gbs": round(24 * N / (f / 1e3) / 1e9, 1),
-                             "bwd_gbs": round(16 * N / (b / 1e3) / 1e9, 1)})
-        return finish(tot, {"fwd_graph": 24 * N * P, "bwd_graph": 16 * N * P}, "sort_u64_f32",
-                      N, {"passes": P, "per_pass": per_pass,
-                          "note": "each graph replays its passes' partition and tile-merge "
-                                  "launches; bytes are per pass, times passes"},
-                      combos=[("uint64+f32", 3, 4)])
+            pp = []
+            for p_, w in enumerate(plan.widths):
+                f = ev[p_].elapsed_time(ev[p_ + 1])
+                b = ev[2 * P - p_ - 1].elapsed_time(ev[2 * P - p_])
+                pp.append({"width": w, "fwd_ms": round(f, 4), "bwd_ms": round(b, 4),
+                           "fwd_gbs": round(fwd_b[mode] * N / (f / 1e3) / 1e9, 1),
+                           "bwd_gbs": round(bwd_b[mode] * N / (b / 1e3) / 1e9, 1)})
+            per_pass[mode] = pp
+            del plan
+            torch.cuda.empty_cache()
+        P = len(per_pass["record"])
+        rec = rows["record"]
+        extra = {"passes": P, "backward": "record",
+                 "recompute": {}, "per_pass": per_pass,
+                 "note": "each graph replays its passes' launches; bytes are per pass, times "
+                         "passes; value and the kernels rows are the recorded form"}
+        for label, ms in rows["recompute"].items():
+            b = (fwd_b if label == "fwd_graph" else bwd_b)["recompute"] * N * P
+            gbs = b / (ms / K / 1e3) / 1e9
+            extra["recompute"][label] = {"ms": round(ms / K, 4), "gbs": round(gbs, 1),
+                                         "frac": round(gbs / peak, 4)}
+        return finish(rec, {"fwd_graph": int(fwd_b["record"] * N * P),
+                            "bwd_graph": int(bwd_b["record"] * N * P)}, "sort_u64_f32", N,
+                      extra, combos=[("uint64+f32", 3, 4)])
     raise ValueError(args.workload)
 
 

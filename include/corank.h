@@ -255,6 +255,39 @@ cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int
                                  int64_t width, const void* gY, void* gX,
                                  void* ws, size_t ws_bytes, cr_stream stream);
 
+/* Recorded merge pass: the same forward as cr_merge_pass (val_bytes 4 or 8),
+ * which also leaves in ws the pass's tile table and in `flags` one bit per
+ * output telling which run of its pair it came from.  The backward
+ * (cr_merge_pass_backward_recorded) then routes gradients from those bits
+ * and reads no keys: per element it moves gY in, gX out and one bit, instead
+ * of re-merging the keys.  The paper has no counterpart; it describes only
+ * the forward merge.
+ *
+ * Layout of `flags` (uint32 words, 16-byte aligned, flag_words words): tile
+ * t of the pass owns words [t*TILE/32, (t+1)*TILE/32); bit x % 32 of word
+ * t*TILE/32 + x/32 is set when the tile's output x came from the pair's
+ * second run (TILE is the key type's current tile size, cr_tile_size_for).
+ * Sizes: cr_merge_pass_record_size gives the workspace bytes and flag words
+ * for (key_type, val_bytes, N, width) under the current tile shape.
+ *
+ * The backward must get the N, width, key_type and val_bytes of the forward,
+ * with ws and flags untouched since and the tile shape unchanged; a table
+ * made for another tile size or tile count is refused on the device
+ * (CR_EINTERNAL via cr_workspace_status).  flags must not overlap Y, Yv or
+ * the inputs (CR_EALIAS); too few words: CR_ENOSPACE. */
+cr_status cr_merge_pass_record_size(int key_type, int val_bytes, int64_t N, int64_t width,
+                                    size_t* ws_bytes, size_t* flag_words);
+
+cr_status cr_merge_pass_record(int key_type, int val_bytes, const void* X, const void* Xv,
+                               int64_t N, int64_t width, void* Y, void* Yv, uint32_t* flags,
+                               size_t flag_words, void* ws, size_t ws_bytes, cr_stream stream);
+
+/* gY (N payload gradients of the recorded pass's output) -> gX (N). */
+cr_status cr_merge_pass_backward_recorded(int key_type, int val_bytes, int64_t N, int64_t width,
+                                          const uint32_t* flags, size_t flag_words,
+                                          const void* gY, void* gX, void* ws, size_t ws_bytes,
+                                          cr_stream stream);
+
 /* ------------------------------------------------------------------------
  * Run formation for a stable merge sort from unsorted input: every run of
  * cr_sort_run_length() consecutive elements of X[0, N) (the last one may be

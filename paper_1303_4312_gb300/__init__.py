@@ -15,7 +15,9 @@ __all__ = [
     "co_rank", "co_rank_many", "merge", "merge_kv", "merge_kv_backward", "MergeKV",
     "merge_kv_autograd", "batched_merge_kv", "batched_merge_kv_backward", "merge_pass",
     "merge_pass_backward", "workspace_status", "tile_size", "CorankError", "merge_sort",
-    "MergeSortPlan", "MergeMany", "merge_many", "HostMerger", "sort_runs", "sort_runs_backward", "sort_run_length",
+    "MergeSortPlan", "MergeMany", "merge_many", "HostMerger", "sort_runs", "sort_runs_backward",
+    "sort_run_length", "PassRecord", "merge_pass_record", "merge_pass_backward_recorded",
+    "merge_pass_record_bytes",
 ]
 
 

@@ -52,6 +52,10 @@ SIGNATURES = {
     "cr_merge_pass_workspace_size": ([INT, INT, I64, I64, ctypes.POINTER(SZ)], INT),
     "cr_merge_pass": ([INT, INT, P, P, I64, I64, P, P, P, SZ, P], INT),
     "cr_merge_pass_backward": ([INT, INT, P, I64, I64, P, P, P, SZ, P], INT),
+    "cr_merge_pass_record_size": ([INT, INT, I64, I64, ctypes.POINTER(SZ), ctypes.POINTER(SZ)],
+                                  INT),
+    "cr_merge_pass_record": ([INT, INT, P, P, I64, I64, P, P, P, SZ, P, SZ, P], INT),
+    "cr_merge_pass_backward_recorded": ([INT, INT, I64, I64, P, SZ, P, P, P, SZ, P], INT),
     "cr_workspace_status": ([P, P], INT),
     "cr_sort_run_length": ([], I64),
     "cr_sort_runs": ([INT, INT, P, P, I64, P, P, P], INT),

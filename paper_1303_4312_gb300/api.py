@@ -15,6 +15,7 @@ Notation: the paper's (rank i; co-ranks j, k) is this API's (k; i, j).
 from __future__ import annotations
 
 import ctypes
+from dataclasses import dataclass
 
 import torch
 
@@ -475,6 +476,69 @@ def merge_pass_backward(X, gY, width: int, key_type: str | None = None, out=None
     return gX
 
 
+@dataclass
+class PassRecord:
+    """What a recorded merge pass leaves for its backward: the pass's tile
+    table (ws) and one source bit per output (flags), for N elements merged
+    with run width `width`."""
+    ws: torch.Tensor
+    flags: torch.Tensor
+    N: int
+    width: int
+    key_code: int
+    val_bytes: int
+
+
+def merge_pass_record_bytes(key_type: str, val_bytes: int, N: int, width: int):
+    """(workspace bytes, flag words) of a recorded pass under the current tile shape."""
+    lib = _lib.load()
+    wsb, fw = ctypes.c_size_t(), ctypes.c_size_t()
+    _lib.check(lib.cr_merge_pass_record_size(_lib.KEY_TYPES[key_type], int(val_bytes), int(N),
+                                             int(width), ctypes.byref(wsb), ctypes.byref(fw)))
+    return wsb.value, fw.value
+
+
+def new_pass_record(key_type: str, val_bytes: int, N: int, width: int, device) -> PassRecord:
+    wsb, fw = merge_pass_record_bytes(key_type, val_bytes, N, width)
+    dev = torch.device(device)
+    return PassRecord(_ws(wsb, dev),
+                      torch.empty(max(fw, 4), dtype=torch.int32, device=dev),
+                      int(N), int(width), _lib.KEY_TYPES[key_type], int(val_bytes))
+
+
+def merge_pass_record(X, Xv, width: int, key_type: str | None = None, out=None,
+                      record: PassRecord | None = None):
+    """merge_pass that also records the merge decisions for
+    merge_pass_backward_recorded.  Returns (Y, Yv, record)."""
+    lib = _lib.load()
+    dev = _dev(X, Xv)
+    kt = _key_code(X, key_type)
+    vb = Xv.element_size()
+    N = X.numel()
+    Y, Yv = out if out is not None else (torch.empty_like(X), torch.empty_like(Xv))
+    if record is None:
+        name = next(k for k, v in _lib.KEY_TYPES.items() if v == kt)
+        record = new_pass_record(name, vb, N, width, dev)
+    _lib.check(lib.cr_merge_pass_record(kt, vb, _ptr(X), _ptr(Xv), N, int(width), _ptr(Y),
+                                        _ptr(Yv), _ptr(record.flags), record.flags.numel(),
+                                        _ptr(record.ws), record.ws.numel(), _stream(dev)))
+    record.N, record.width, record.key_code, record.val_bytes = N, int(width), kt, vb
+    return Y, Yv, record
+
+
+def merge_pass_backward_recorded(record: PassRecord, gY, out=None):
+    """Payload gradient of a recorded merge pass, routed from its record
+    (no keys are read)."""
+    lib = _lib.load()
+    dev = _dev(gY)
+    gX = out if out is not None else torch.empty_like(gY)
+    _lib.check(lib.cr_merge_pass_backward_recorded(
+        record.key_code, gY.element_size(), record.N, record.width, _ptr(record.flags),
+        record.flags.numel(), _ptr(gY), _ptr(gX), _ptr(record.ws), record.ws.numel(),
+        _stream(dev)))
+    return gX
+
+
 def workspace_status(ws: torch.Tensor) -> None:
     """Synchronise the current stream and raise if the last call that used
     `ws` recorded a device-side error."""
@@ -526,35 +590,52 @@ class MergeSortPlan:
     With ``run`` given, the input's runs of ``run`` elements must already be
     sorted; with ``run=None`` the plan first sorts runs of
     sort_run_length() itself (run formation), so any input is accepted.
-    Pass p merges runs of width run * 2^p.  The input keys of every pass are
-    kept (they are what the backward pass re-co-ranks), so keys need
-    (passes + 1) * N slots (+ N for the unsorted input); payloads and
-    gradients ping-pong between two buffers.  Forward and backward are each
-    captured once into a CUDA graph (``graph=True``) and replayed.
+    Pass p merges runs of width run * 2^p.
+
+    The backward needs every pass's merge decisions.  With ``record=True``
+    (default) each forward pass records them (cr_merge_pass_record: its tile
+    table plus one bit per element) and the backward routes gradients from
+    those records without reading keys; keys then ping-pong between two
+    buffers.  With ``record=False`` the input keys of every pass are kept
+    ((passes + 1) * N key slots) and the backward re-merges them
+    (cr_merge_pass_backward).  Payloads and gradients ping-pong between two
+    buffers; with run formation the unsorted input keys are kept too.
+    Forward and backward are each captured once into a CUDA graph
+    (``graph=True``) and replayed.  The tile shape must not change between
+    a recorded forward and its backward.
     """
 
     def __init__(self, N: int, run: int | None, key_dtype, val_dtype, device="cuda",
-                 key_type: str | None = None, graph: bool = True):
+                 key_type: str | None = None, graph: bool = True, record: bool = True):
         self.N = int(N)
         self.form_runs = run is None
         self.run = sort_run_length() if run is None else int(run)
         self.device = torch.device(device)
         self.key_type = key_type
+        self.record = bool(record)
         self.widths = []
         w = self.run
         while w < self.N:
             self.widths.append(w)
             w *= 2
         P = len(self.widths)
-        self.keys = [torch.empty(self.N, dtype=key_dtype, device=self.device) for _ in range(P + 1)]
+        nkeys = 2 if self.record else P + 1
+        self.keys = [torch.empty(self.N, dtype=key_dtype, device=self.device)
+                     for _ in range(nkeys)]
         self.vals = [torch.empty(self.N, dtype=val_dtype, device=self.device) for _ in range(2)]
         self.grads = [torch.empty(self.N, dtype=val_dtype, device=self.device) for _ in range(2)]
         self.input_keys = (torch.empty(self.N, dtype=key_dtype, device=self.device)
                            if self.form_runs else None)
         kt = key_type or _DTYPE_KEY[key_dtype]
         vb = torch.empty(0, dtype=val_dtype).element_size()
-        need = max([merge_pass_workspace_bytes(kt, vb, self.N, w) for w in self.widths] + [256])
-        self.ws = _ws(need, self.device)
+        if self.record:
+            self.records = [new_pass_record(kt, vb, self.N, w, self.device) for w in self.widths]
+            self.ws = None
+        else:
+            self.records = []
+            need = max([merge_pass_workspace_bytes(kt, vb, self.N, w) for w in self.widths]
+                       + [256])
+            self.ws = _ws(need, self.device)
         self.use_graph = graph
         self._gf = None
         self._gb = None
@@ -562,6 +643,10 @@ class MergeSortPlan:
     @property
     def passes(self) -> int:
         return len(self.widths)
+
+    def _key_buf(self, p: int) -> torch.Tensor:
+        """Input keys of pass p (p == passes: the sorted output)."""
+        return self.keys[p & 1] if self.record else self.keys[p]
 
     def _load(self, X, Xv):
         if self.form_runs:
@@ -576,14 +661,22 @@ class MergeSortPlan:
             sort_runs(self.input_keys, self.vals[1], key_type=self.key_type,
                       out=(self.keys[0], self.vals[0]))
         for p, w in enumerate(self.widths):
-            merge_pass(self.keys[p], self.vals[p & 1], w, key_type=self.key_type,
-                       out=(self.keys[p + 1], self.vals[(p + 1) & 1]), ws=self.ws)
+            out = (self._key_buf(p + 1), self.vals[(p + 1) & 1])
+            if self.record:
+                merge_pass_record(self._key_buf(p), self.vals[p & 1], w, key_type=self.key_type,
+                                  out=out, record=self.records[p])
+            else:
+                merge_pass(self._key_buf(p), self.vals[p & 1], w, key_type=self.key_type,
+                           out=out, ws=self.ws)
 
     def _backward_body(self):
         for p in reversed(range(self.passes)):
             src = self.grads[(p + 1) & 1]
-            merge_pass_backward(self.keys[p], src, self.widths[p], key_type=self.key_type,
-                                out=self.grads[p & 1], ws=self.ws)
+            if self.record:
+                merge_pass_backward_recorded(self.records[p], src, out=self.grads[p & 1])
+            else:
+                merge_pass_backward(self.keys[p], src, self.widths[p], key_type=self.key_type,
+                                    out=self.grads[p & 1], ws=self.ws)
         if self.form_runs:
             sort_runs_backward(self.input_keys, self.grads[0], key_type=self.key_type,
                                out=self.grads[1])
@@ -612,7 +705,7 @@ class MergeSortPlan:
             self._gf.replay()
         else:
             self._forward_body()
-        return self.keys[self.passes], self.vals[self.passes & 1]
+        return self._key_buf(self.passes), self.vals[self.passes & 1]
 
     def backward(self, gY: torch.Tensor) -> torch.Tensor:
         """Payload gradient of the sort: gX[perm[t]] = gY[t]."""
@@ -644,12 +737,13 @@ class _MergeSortFn(torch.autograd.Function):
 
 def merge_sort(X: torch.Tensor, Xv: torch.Tensor, run: int | None = None,
                key_type: str | None = None, graph: bool = True,
-               plan: MergeSortPlan | None = None):
+               plan: MergeSortPlan | None = None, record: bool = True):
     """Stable merge sort of X carrying payloads Xv; differentiable in Xv.
     run=None sorts any input (runs are formed on the GPU first); an integer
     run declares that X's runs of that width are already sorted.  Returns
     (keys, payloads)."""
     _dev(X, Xv)
     if plan is None:
-        plan = MergeSortPlan(X.numel(), run, X.dtype, Xv.dtype, X.device, key_type, graph)
+        plan = MergeSortPlan(X.numel(), run, X.dtype, Xv.dtype, X.device, key_type, graph,
+                             record)
     return _MergeSortFn.apply(X, Xv, plan)

@@ -555,23 +555,38 @@ cr_status batched_common(bool backward, int key_type, int val_bytes, int64_t nse
     return ok();
 }
 
-cr_status pass_common(bool backward, int key_type, int val_bytes, const void* X, const void* Xv,
+// Merge-pass modes: plain forward, backward that re-merges the keys,
+// forward that records source flags, backward from those flags.
+enum class Pass { kForward, kBackward, kRecord, kReplay };
+
+cr_status pass_common(Pass mode, int key_type, int val_bytes, const void* X, const void* Xv,
                       int64_t N, int64_t width, const void* gY, void* Y, void* Yv, void* gX,
-                      void* ws, size_t ws_bytes, cr_stream stream) {
+                      uint32_t* flags, size_t flag_words, void* ws, size_t ws_bytes,
+                      cr_stream stream) {
     CR_TRY(check_key_type(key_type));
-    CR_TRY(check_vb(val_bytes, !backward));
+    CR_TRY(check_vb(val_bytes, mode == Pass::kForward));
     if (N < 0) return fail(CR_EINVAL, "negative size");
     if (width < 1) return fail(CR_EINVAL, "run width must be >= 1");
+    if (flag_words > size_t(INT64_MAX / 4)) return fail(CR_EINVAL, "flag_words too large");
     const int ks = key_bytes(key_type);
     const int vb = val_bytes;
-    if (!backward) {
+    const bool rec = mode == Pass::kRecord || mode == Pass::kReplay;
+    const Arr fl = {rec ? flags : nullptr, rec ? int64_t(flag_words) : 0, 4, "flags"};
+    if (mode == Pass::kForward || mode == Pass::kRecord) {
         const Arr ins[2] = {{X, N, ks, "X"}, {vb ? Xv : nullptr, vb ? N : 0, vb, "X payload"}};
-        const Arr outs[2] = {{Y, N, ks, "Y"}, {vb ? Yv : nullptr, vb ? N : 0, vb, "Y payload"}};
+        const Arr outs[3] = {{Y, N, ks, "Y"}, {vb ? Yv : nullptr, vb ? N : 0, vb, "Y payload"},
+                             fl};
         for (const Arr& a : ins) CR_TRY(check_arr(a));
         for (const Arr& a : outs) CR_TRY(check_arr(a));
-        CR_TRY(check_no_alias(outs, 2, ins, 2));
-    } else {
+        CR_TRY(check_no_alias(outs, 3, ins, 2));
+    } else if (mode == Pass::kBackward) {
         const Arr ins[2] = {{X, N, ks, "X"}, {gY, N, vb, "gY"}};
+        const Arr outs[1] = {{gX, N, vb, "gX"}};
+        for (const Arr& a : ins) CR_TRY(check_arr(a));
+        CR_TRY(check_arr(outs[0]));
+        CR_TRY(check_no_alias(outs, 1, ins, 2));
+    } else {
+        const Arr ins[2] = {{gY, N, vb, "gY"}, fl};
         const Arr outs[1] = {{gX, N, vb, "gX"}};
         for (const Arr& a : ins) CR_TRY(check_arr(a));
         CR_TRY(check_arr(outs[0]));
@@ -583,7 +598,18 @@ cr_status pass_common(bool backward, int key_type, int val_bytes, const void* X,
     const int64_t tile = cr::tile_of_shape(shape);
     const int64_t ntiles = cr::pass_tiles(N, width, tile, nullptr, nullptr);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
+    if (rec) {
+        const size_t need = size_t(ntiles) * size_t(tile / 32);
+        if (flag_words < need)
+            return fail(CR_ENOSPACE, "flags hold %zu words, need %zu", flag_words, need);
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (mode == Pass::kReplay) {
+        const cudaError_t e =
+            cr::route_recorded(vb, ws, flags, int64_t(flag_words), N, width, tile, gY, gX, st);
+        if (e != cudaSuccess) return cuda_fail(e, "recorded pass backward launch");
+        return ok();
+    }
     cr::MergeArgs a{};
     a.ak = X;
     a.bk = X;
@@ -591,8 +617,9 @@ cr_status pass_common(bool backward, int key_type, int val_bytes, const void* X,
     a.bv = Xv;
     a.gc_in = gY;
     a.ck = Y;
-    a.cv = backward ? gX : Yv;
+    a.cv = mode == Pass::kBackward ? gX : Yv;
     a.cv2 = gX;
+    a.flags = flags;
     a.a_total = N;
     a.b_total = N;
     a.c_total = N;
@@ -601,8 +628,11 @@ cr_status pass_common(bool backward, int key_type, int val_bytes, const void* X,
         int64_t nt = 0;
         cudaError_t r = ops.partition_pass(X, N, width, tile, ws, &nt, st);
         if (r != cudaSuccess) return r;
-        return backward ? ops.merge_bwd(shape, vb, a, nt, st)
-                        : ops.merge_fwd(shape, vb, false, a, nt, st);
+        switch (mode) {
+            case Pass::kBackward: return ops.merge_bwd(shape, vb, a, nt, st);
+            case Pass::kRecord: return ops.merge_fwd_rec(shape, vb, a, nt, st);
+            default: return ops.merge_fwd(shape, vb, false, a, nt, st);
+        }
     });
     if (e != cudaSuccess) return cuda_fail(e, "merge pass launch");
     return ok();
@@ -644,15 +674,45 @@ cr_status cr_merge_pass_workspace_size(int key_type, int val_bytes, int64_t N, i
 cr_status cr_merge_pass(int key_type, int val_bytes, const void* X, const void* Xv, int64_t N,
                         int64_t width, void* Y, void* Yv, void* ws, size_t ws_bytes,
                         cr_stream stream) {
-    return pass_common(false, key_type, val_bytes, X, Xv, N, width, nullptr, Y, Yv, nullptr, ws,
-                       ws_bytes, stream);
+    return pass_common(Pass::kForward, key_type, val_bytes, X, Xv, N, width, nullptr, Y, Yv,
+                       nullptr, nullptr, 0, ws, ws_bytes, stream);
 }
 
 cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int64_t N,
                                  int64_t width, const void* gY, void* gX, void* ws,
                                  size_t ws_bytes, cr_stream stream) {
-    return pass_common(true, key_type, val_bytes, X, nullptr, N, width, gY, nullptr, nullptr, gX,
-                       ws, ws_bytes, stream);
+    return pass_common(Pass::kBackward, key_type, val_bytes, X, nullptr, N, width, gY, nullptr,
+                       nullptr, gX, nullptr, 0, ws, ws_bytes, stream);
+}
+
+cr_status cr_merge_pass_record_size(int key_type, int val_bytes, int64_t N, int64_t width,
+                                    size_t* ws_bytes, size_t* flag_words) {
+    CR_TRY(check_key_type(key_type));
+    CR_TRY(check_vb(val_bytes, false));
+    if (N < 0 || width < 1) return fail(CR_EINVAL, "bad size or width");
+    if (!ws_bytes || !flag_words) return fail(CR_EINVAL, "output pointer is NULL");
+    const int64_t tile = cr::tile_of_shape(shape_of(key_type, val_bytes));
+    if (width > N) width = N > 0 ? N : 1;
+    const int64_t nt = cr::pass_tiles(N, width, tile, nullptr, nullptr);
+    *ws_bytes = single_ws_bytes(nt);
+    *flag_words = size_t(nt) * size_t(tile / 32);
+    return ok();
+}
+
+cr_status cr_merge_pass_record(int key_type, int val_bytes, const void* X, const void* Xv,
+                               int64_t N, int64_t width, void* Y, void* Yv, uint32_t* flags,
+                               size_t flag_words, void* ws, size_t ws_bytes, cr_stream stream) {
+    return pass_common(Pass::kRecord, key_type, val_bytes, X, Xv, N, width, nullptr, Y, Yv,
+                       nullptr, flags, flag_words, ws, ws_bytes, stream);
+}
+
+cr_status cr_merge_pass_backward_recorded(int key_type, int val_bytes, int64_t N, int64_t width,
+                                          const uint32_t* flags, size_t flag_words,
+                                          const void* gY, void* gX, void* ws, size_t ws_bytes,
+                                          cr_stream stream) {
+    return pass_common(Pass::kReplay, key_type, val_bytes, nullptr, nullptr, N, width, gY,
+                       nullptr, nullptr, gX, const_cast<uint32_t*>(flags), flag_words, ws,
+                       ws_bytes, stream);
 }
 
 int64_t cr_sort_run_length(void) { return cr::kSortRun; }

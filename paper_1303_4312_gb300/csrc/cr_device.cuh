@@ -49,6 +49,7 @@ struct MergeArgs {
     void* cv;            // fwd: C payloads / bwd: gradient of A
     void* cv2;           // bwd: gradient of B
     uint32_t* ctag;      // fwd: source tags (nullable)
+    uint32_t* flags;     // fwd, recording kernels: per-tile source flags
     int64_t a_total;     // length of the A array
     int64_t b_total;     // length of the B array
     int64_t c_total;     // length of the C array

@@ -45,7 +45,7 @@ cudaError_t launch_shape(Kern kern, int threads, size_t smem, LaunchShape* cache
     return cudaSuccess;
 }
 
-template <class K, int VB, bool TAG, bool BWD, int S>
+template <class K, int VB, bool TAG, bool BWD, int S, bool REC>
 cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
     constexpr int KS = int(sizeof(K));
     if constexpr (!Stages<KS, VB, TAG, BWD, S>::FITS) {
@@ -56,8 +56,8 @@ cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream
         constexpr int ILP = ShapeAt<S>::ILP;
         constexpr int NS = Stages<KS, VB, TAG, BWD, S>::NS;
         constexpr int MINB = Stages<KS, VB, TAG, BWD, S>::MINB;
-        using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD>;
-        auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, ILP, NS, MINB, BWD>;
+        using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD, REC>;
+        auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, ILP, NS, MINB, BWD, REC>;
         static LaunchShape cache[kMaxDevices];
         static std::once_flag once[kMaxDevices];
         LaunchShape sh;
@@ -72,16 +72,16 @@ cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream
     }
 }
 
-template <class K, int VB, bool TAG, bool BWD>
+template <class K, int VB, bool TAG, bool BWD, bool REC = false>
 cudaError_t launch_merge(int shape, const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
     static_assert(kNumShapes == 6, "dispatch below lists every shape");
     switch (shape) {
-        case 0: return launch_merge_shape<K, VB, TAG, BWD, 0>(a, max_tiles, st);
-        case 1: return launch_merge_shape<K, VB, TAG, BWD, 1>(a, max_tiles, st);
-        case 2: return launch_merge_shape<K, VB, TAG, BWD, 2>(a, max_tiles, st);
-        case 3: return launch_merge_shape<K, VB, TAG, BWD, 3>(a, max_tiles, st);
-        case 4: return launch_merge_shape<K, VB, TAG, BWD, 4>(a, max_tiles, st);
-        case 5: return launch_merge_shape<K, VB, TAG, BWD, 5>(a, max_tiles, st);
+        case 0: return launch_merge_shape<K, VB, TAG, BWD, 0, REC>(a, max_tiles, st);
+        case 1: return launch_merge_shape<K, VB, TAG, BWD, 1, REC>(a, max_tiles, st);
+        case 2: return launch_merge_shape<K, VB, TAG, BWD, 2, REC>(a, max_tiles, st);
+        case 3: return launch_merge_shape<K, VB, TAG, BWD, 3, REC>(a, max_tiles, st);
+        case 4: return launch_merge_shape<K, VB, TAG, BWD, 4, REC>(a, max_tiles, st);
+        case 5: return launch_merge_shape<K, VB, TAG, BWD, 5, REC>(a, max_tiles, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -98,6 +98,14 @@ cudaError_t KeyOps<K>::merge_fwd(int shape, int vb, bool tag, const MergeArgs& a
         case 17: return launch_merge<K, 8, true, false>(shape, a, max_tiles, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_fwd_rec(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                     cudaStream_t st) {
+    if (vb == 4) return launch_merge<K, 4, false, false, true>(shape, a, max_tiles, st);
+    if (vb == 8) return launch_merge<K, 8, false, false, true>(shape, a, max_tiles, st);
+    return cudaErrorInvalidValue;
 }
 
 template <class K>
@@ -219,6 +227,9 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
 #define CR_INSTANTIATE_FORWARD(K)                                                              \
     template cudaError_t cr::KeyOps<K>::merge_fwd(int, int, bool, const cr::MergeArgs&,        \
                                                   int64_t, cudaStream_t);
+#define CR_INSTANTIATE_RECORD(K)                                                               \
+    template cudaError_t cr::KeyOps<K>::merge_fwd_rec(int, int, const cr::MergeArgs&, int64_t, \
+                                                      cudaStream_t);
 #define CR_INSTANTIATE_REST(K)                                                                 \
     template cudaError_t cr::KeyOps<K>::merge_bwd(int, int, const cr::MergeArgs&, int64_t,     \
                                                   cudaStream_t);                               \

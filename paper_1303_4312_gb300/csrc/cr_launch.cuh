@@ -90,6 +90,10 @@ struct KeyOps {
     // shape: index into kShapes (must match the tile size of the table).
     static cudaError_t merge_fwd(int shape, int vb, bool tag, const MergeArgs& a,
                                  int64_t max_tiles, cudaStream_t st);
+    // Forward merge with payloads (vb in {4,8}) that also records every
+    // output's source run as one bit per output (a.flags, per tile).
+    static cudaError_t merge_fwd_rec(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                     cudaStream_t st);
     // Payload backward (vb in {4,8}).
     static cudaError_t merge_bwd(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                  cudaStream_t st);
@@ -117,6 +121,14 @@ struct KeyOps {
     static cudaError_t sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
                                           void* gX, cudaStream_t st);
 };
+
+// Backward of a recorded merge pass (vb in {4,8}) over N elements with run
+// width w (1 <= w <= N): gX from gY, routed by the tile table in ws and the
+// per-tile source flags, without keys.  tile: the table's tile size (the
+// table's header and records are checked against it and the pass geometry).
+cudaError_t route_recorded(int vb, void* ws, const uint32_t* flags, int64_t flag_words,
+                           int64_t N, int64_t w, int64_t tile, const void* gY, void* gX,
+                           cudaStream_t st);
 
 // Tiles of a merge pass over N elements with run width w.
 inline int64_t pass_tiles(int64_t N, int64_t w, int64_t tile, int64_t* tpp_out,

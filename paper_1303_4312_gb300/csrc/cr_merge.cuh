@@ -52,8 +52,9 @@ static_assert(sizeof(StageInfo) == 48, "StageInfo size");
 
 // Shared-memory layout of one kernel instantiation (host and device agree).
 // A stage holds the input windows and, after the consumers have read them,
-// the tile's output (forward: keys, payloads, tags; backward: gA, gB).
-template <class K, int VB, bool TAG, int NT, int IPT, int ILP, int NS, bool BWD>
+// the tile's output (forward: keys, payloads, tags, and with REC the tile's
+// source-flag words; backward: gA, gB).
+template <class K, int VB, bool TAG, int NT, int IPT, int ILP, int NS, bool BWD, bool REC = false>
 struct Layout {
     static constexpr int TILE = NT * IPT * ILP;
     static constexpr int KS = sizeof(K);
@@ -64,11 +65,13 @@ struct Layout {
     static constexpr int SV = (VB && !BWD) ? TILE + 4 * EV : 0;   // A and B payload windows
     static constexpr int ST = (TAG && !BWD) ? TILE + 8 : 0;       // output tags
     static constexpr int SG = BWD ? TILE + 4 * EV : 0;            // gC window, then gA | gB
+    static constexpr int WPT = TILE / 32;                         // source-flag words (REC)
     static constexpr size_t STAGE_K = align_up_sz(size_t(SK) * KS, 128);
     static constexpr size_t STAGE_V = align_up_sz(size_t(SV) * VS, 128);
     static constexpr size_t STAGE_T = align_up_sz(size_t(ST) * 4, 128);
     static constexpr size_t STAGE_G = align_up_sz(size_t(SG) * VS, 128);
-    static constexpr size_t STAGE = STAGE_K + STAGE_V + STAGE_T + STAGE_G;
+    static constexpr size_t STAGE_F = REC ? align_up_sz(size_t(WPT) * 4, 128) : 0;
+    static constexpr size_t STAGE = STAGE_K + STAGE_V + STAGE_T + STAGE_G + STAGE_F;
     static constexpr size_t BAR_OFF = 0;              // full, staged, empty [NS]; flags
     static constexpr size_t INFO_OFF = 256;
     static constexpr size_t STAGE_OFF = align_up_sz(INFO_OFF + NS * sizeof(StageInfo), 128);
@@ -76,6 +79,9 @@ struct Layout {
     static_assert(NS >= 2, "at least one stage can load while another is merged");
     static_assert(3 * NS * 8 + 16 <= INFO_OFF, "barrier area");
     static_assert(TILE % EK == 0 && TILE % EV == 0 && TILE % 4 == 0, "tile alignment");
+    // a tile's flag words form whole 16-byte chunks (bulk store at t * WPT)
+    static_assert(!REC || (!BWD && TILE % 32 == 0 && (WPT * 4) % 16 == 0 && WPT <= NT),
+                  "source flags need TILE % 128 == 0 and at most one word per consumer");
     static_assert(TOTAL <= 232448, "exceeds 227 KB of shared memory per CTA");
 };
 
@@ -187,9 +193,14 @@ template <> struct Log2Ceil<1> { static constexpr int v = 0; };
 // Block: NT consumer threads, then one producer warp, then one storer warp.
 template <int NT> constexpr int merge_block_threads() { return NT + 64; }
 
-template <class K, int VB, bool TAG, int NT, int IPT, int ILP, int NS, int MINB, bool BWD>
+// REC (forward only): also record, per output, whether it came from B, as
+// bit x % 32 of word x / 32 of the tile's WPT flag words, stored at
+// p.flags + t * WPT for tile t (the backward then routes gradients from
+// these bits and the tile table without reading keys).
+template <class K, int VB, bool TAG, int NT, int IPT, int ILP, int NS, int MINB, bool BWD,
+          bool REC>
 __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeArgs p) {
-    using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD>;
+    using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD, REC>;
     using V = typename VBits<VB>::T;
     constexpr int TILE = L::TILE;
     constexpr int EK = L::EK;
@@ -215,6 +226,10 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
     };
     auto stage_g = [&](int s) {
         return reinterpret_cast<V*>(base(s) + L::STAGE_K + L::STAGE_V + L::STAGE_T);
+    };
+    auto stage_f = [&](int s) {
+        return reinterpret_cast<uint32_t*>(base(s) + L::STAGE_K + L::STAGE_V + L::STAGE_T +
+                                           L::STAGE_G);
     };
 
     WsHeader* hdr = reinterpret_cast<WsHeader*>(p.ws);
@@ -263,6 +278,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                     if constexpr (VB != 0)
                         store_bulk(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV);
                     if constexpr (TAG) store_bulk(p.ctag, stage_t(s), in.gc, len, 4);
+                    if constexpr (REC) bulk_s2g(p.flags + t * L::WPT, stage_f(s), L::WPT * 4);
                     bulk_commit();
                 } else if (lane <= 2 * EK) {
                     store_edges(C, stage_k(s), in.gc, len, EK, lane - 1);
@@ -420,8 +436,15 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             K okey[ILP][IPT];
             V oval[ILP][VB ? IPT : 1];
             uint32_t otag[ILP][TAG ? IPT : 1];
+            uint32_t obit[ILP];   // REC: bit q set when output q of chain c came from B
             const V* sv = stage_v(s);
             const int avo = in.av, bvo = in.bv;
+            if constexpr (REC) {
+#pragma unroll
+                for (int c = 0; c < ILP; ++c) obit[c] = 0;
+                // cleared before the barrier below, set after it
+                if (tid < L::WPT) stage_f(s)[tid] = 0;
+            }
             // One merge step of chain c (ties take A).  GUARD: some side may
             // run out within the chain's IPT steps (only near the windows' ends).
             auto step = [&](int c, int q, auto guard) {
@@ -432,6 +455,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                 if constexpr (VB != 0) oval[c][q] = sv[takeA ? avo + j[c] : bvo + k[c]];
                 if constexpr (TAG)
                     otag[c][q] = takeA ? uint32_t(in.ga + j[c]) : uint32_t(p.tag_b + in.gb + k[c]);
+                if constexpr (REC) obit[c] |= (takeA ? 0u : 1u) << q;
                 j[c] += takeA ? 1 : 0;
                 k[c] += takeA ? 0 : 1;
                 const K nx = sk[takeA ? ao + j[c] : bo + k[c]];   // one load from either window
@@ -474,6 +498,18 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
 #pragma unroll
                     for (int q = 0; q < IPT; ++q)
                         if (q < cnt[c]) ot[pht + d[c] + q] = otag[c][q];
+            }
+            if constexpr (REC) {
+                // a chain's IPT (< 32) bits straddle at most two words
+                uint32_t* sf = stage_f(s);
+#pragma unroll
+                for (int c = 0; c < ILP; ++c) {
+                    if (cnt[c] > 0 && obit[c] != 0) {
+                        const int w = d[c] >> 5, o = d[c] & 31;
+                        atomicOr(&sf[w], obit[c] << o);
+                        if (o + cnt[c] > 32) atomicOr(&sf[w + 1], obit[c] >> (32 - o));
+                    }
+                }
             }
         } else {
             V gval[ILP][IPT];

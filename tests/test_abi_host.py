@@ -157,3 +157,53 @@ def test_geometry_classes(lib):
     finally:
         lib.cr_set_tile_shape_for(kt, 0, 0, b0)
         lib.cr_set_tile_shape_for(kt, 0, 1, s0)
+
+
+def test_recorded_pass_sizes_and_validation(lib):
+    """cr_merge_pass_record_size and the argument checks of the recorded pass
+    (all fail before any launch)."""
+    ws, fw = ctypes.c_size_t(), ctypes.c_size_t()
+    for code, vb in ((0, 4), (1, 8), (2, 4), (3, 4), (3, 8)):
+        t = lib.cr_tile_size(code, vb)
+        assert t % 128 == 0
+        for N, w in ((1 << 20, 1024), (1 << 20, 3000), (12345, 100), (7, 1 << 40), (5000, 1)):
+            assert lib.cr_merge_pass_record_size(code, vb, N, w, ctypes.byref(ws),
+                                                 ctypes.byref(fw)) == 0
+            we = min(w, N)
+            npairs = (N + 2 * we - 1) // (2 * we)
+            tpp = (2 * we + t - 1) // t
+            last = N - 2 * we * (npairs - 1)
+            ntiles = (npairs - 1) * tpp + (last + t - 1) // t
+            assert ws.value == 256 + 32 * ntiles
+            assert fw.value == ntiles * (t // 32)
+    # keys-only payload width, bad width, NULL outputs
+    assert lib.cr_merge_pass_record_size(0, 0, 100, 10, ctypes.byref(ws), ctypes.byref(fw)) == 1
+    assert lib.cr_merge_pass_record_size(0, 4, 100, 0, ctypes.byref(ws), ctypes.byref(fw)) == 1
+    assert lib.cr_merge_pass_record_size(0, 4, 100, 10, None, ctypes.byref(fw)) == 1
+
+    N, w = 4096, 256
+    assert lib.cr_merge_pass_record_size(0, 4, N, w, ctypes.byref(ws), ctypes.byref(fw)) == 0
+    X, Xv = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000)
+    Y, Yv = ctypes.c_void_p(0x300000), ctypes.c_void_p(0x400000)
+    F, WS = ctypes.c_void_p(0x500000), ctypes.c_void_p(0x600000)
+    rec = lambda *a: lib.cr_merge_pass_record(*a)
+    # keys only is refused (the record serves a payload backward)
+    assert rec(0, 0, X, None, N, w, Y, None, F, fw.value, WS, ws.value, None) == 1
+    # too few flag words / too small workspace
+    assert rec(0, 4, X, Xv, N, w, Y, Yv, F, fw.value - 1, WS, ws.value, None) == 4
+    assert rec(0, 4, X, Xv, N, w, Y, Yv, F, fw.value, WS, ws.value - 1, None) == 4
+    # flags overlapping the output keys, or misaligned
+    assert rec(0, 4, X, Xv, N, w, Y, Yv, ctypes.c_void_p(0x300100), fw.value, WS, ws.value,
+               None) == 2
+    assert rec(0, 4, X, Xv, N, w, Y, Yv, ctypes.c_void_p(0x500004), fw.value, WS, ws.value,
+               None) == 3
+    # NULL flags with words to write
+    assert rec(0, 4, X, Xv, N, w, Y, Yv, None, fw.value, WS, ws.value, None) == 1
+    bwd = lambda *a: lib.cr_merge_pass_backward_recorded(*a)
+    G, GX = ctypes.c_void_p(0x700000), ctypes.c_void_p(0x800000)
+    assert bwd(0, 4, N, w, F, fw.value - 1, G, GX, WS, ws.value, None) == 4
+    assert bwd(0, 4, N, w, F, fw.value, G, ctypes.c_void_p(0x700100), WS, ws.value, None) == 2
+    assert bwd(0, 0, N, w, F, fw.value, G, GX, WS, ws.value, None) == 1
+    assert bwd(0, 4, N, 0, F, fw.value, G, GX, WS, ws.value, None) == 1
+    # nothing to do is fine
+    assert bwd(0, 4, 0, w, None, 0, None, None, None, 0, None) == 0
