@@ -246,9 +246,10 @@ def t_batched_i32_f32(seed: int = 6, nseg: int = 8192, max_log2: int = 18, devic
     return a_off, b_off, A, Av, B, Bv
 
 
-def t_sort_u64_f32(seed: int = 7, device="cuda", shift: int = 0, run: int = 1024,
+def t_sort_u64_f32(seed: int = 7, device="cuda", shift: int = 0, run: int | None = 1024,
                    distinct: int = 1 << 20):
-    """uint64 keys (int64 container) from `distinct` values, runs stably pre-sorted."""
+    """uint64 keys (int64 container) from `distinct` values, runs stably
+    pre-sorted (run=None: left unsorted)."""
     torch = _torch()
     N = (1 << 27) >> shift
     vals = distinct_values(_rng(seed), distinct, np.uint64).view(np.int64)
@@ -256,6 +257,8 @@ def t_sort_u64_f32(seed: int = 7, device="cuda", shift: int = 0, run: int = 1024
     g = _gen(seed, device)
     X = vals[torch.randint(0, len(vals), (N,), generator=g, device=device)]
     Xv = torch.randn(N, generator=g, device=device, dtype=torch.float32)
+    if run is None:
+        return X, Xv
     flip = torch.tensor(-(1 << 63), dtype=torch.int64, device=device)
     rows = (X ^ flip).view(-1, run)        # signed order of the flipped bits == unsigned order
     srt = torch.sort(rows, dim=1, stable=True)

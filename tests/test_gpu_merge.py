@@ -432,6 +432,19 @@ def test_sharded_merge_single_rank_nccl():
         C, p = shard.sharded_merge(dev(A), dev(B))
         assert (p.k0, p.k1) == (0, len(A) + len(B))
         assert same_bits(host(C, np.int32), oracle.merge(A, B)[0])
+        # block-distributed form: remote-read co-ranks and window fetch over
+        # NCCL (one rank), local merge by the library's kernels
+        C, p = shard.distributed_merge(dev(A), dev(B), "i32")
+        assert (p.i1, p.j1) == (len(A), len(B))
+        assert same_bits(host(C, np.int32), oracle.merge(A, B)[0])
+        Au = sorted_keys(rng, 5000, np.uint64)
+        Bu = sorted_keys(rng, 7000, np.uint64)
+        Av = rng.standard_normal(5000).astype(np.float32)
+        Bv = rng.standard_normal(7000).astype(np.float32)
+        C, Cv, p = shard.distributed_merge(dev(Au), dev(Bu), "u64", Av_blk=dev(Av),
+                                           Bv_blk=dev(Bv))
+        wk, wv, _ = oracle.merge_kv(Au, Av, Bu, Bv)
+        assert same_bits(host(C, np.uint64), wk) and same_bits(host(Cv, np.float32), wv)
     finally:
         dist.destroy_process_group()
 

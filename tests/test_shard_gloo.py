@@ -80,3 +80,101 @@ def test_plan_blocks_are_balanced():
         assert np.array_equal(np.concatenate(blocks), oracle.merge(a, b)[0])
     with pytest.raises(ValueError):
         shard.block_bounds(10, 2, 2)
+
+
+def _dist_worker(rank, world, port, cases, out_q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        for ci, (A, Av, B, Bv, a_cuts, b_cuts, kt) in enumerate(cases):
+            a_blk = torch.from_numpy(A[a_cuts[rank]:a_cuts[rank + 1]].copy())
+            b_blk = torch.from_numpy(B[b_cuts[rank]:b_cuts[rank + 1]].copy())
+            dt = A.dtype
+
+            def merge(x, y):
+                return torch.from_numpy(oracle.merge(x.numpy().view(dt), y.numpy().view(dt))[0]
+                                        .view(x.numpy().dtype))
+
+            def merge_kv(x, xv, y, yv):
+                c, cv, _ = oracle.merge_kv(x.numpy().view(dt), xv.numpy(), y.numpy().view(dt),
+                                           yv.numpy())
+                return torch.from_numpy(c.view(x.numpy().dtype)), torch.from_numpy(cv)
+
+            a_t = torch.from_numpy(a_blk.numpy().view(np.int64 if dt.itemsize == 8 else np.int32))
+            b_t = torch.from_numpy(b_blk.numpy().view(np.int64 if dt.itemsize == 8 else np.int32))
+            if Av is None:
+                C, p = shard.distributed_merge(a_t, b_t, kt, merge=merge)
+                Cv = None
+            else:
+                av = torch.from_numpy(Av[a_cuts[rank]:a_cuts[rank + 1]].copy())
+                bv = torch.from_numpy(Bv[b_cuts[rank]:b_cuts[rank + 1]].copy())
+                C, Cv, p = shard.distributed_merge(a_t, b_t, kt, Av_blk=av, Bv_blk=bv,
+                                                   merge=merge_kv)
+            out_q.put((ci, rank, (p.k0, p.k1, p.i0, p.i1, p.j0, p.j1), C.numpy().tobytes(),
+                       None if Cv is None else Cv.numpy().tobytes()))
+    finally:
+        dist.destroy_process_group()
+
+
+def _cuts(rng, total, world):
+    """Random block boundaries 0 = c0 <= c1 <= ... <= c_world = total (some
+    blocks empty)."""
+    inner = np.sort(rng.integers(0, total + 1, world - 1))
+    if world > 2:
+        inner[0] = inner[1]          # one empty block
+    return [0, *inner.tolist(), total]
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_distributed_merge_block_inputs(world):
+    """Block-distributed A and B: Algorithm 1 with remote point reads finds
+    every rank's block co-ranks, the windows are fetched from their owners,
+    and each rank's merged block equals that slice of the stable merge
+    (keys and payloads), for signed and unsigned orders."""
+    import oracle
+    rng = np.random.default_rng(112 + world)
+    cases = []
+    for m, n, spread, dt, kv in [(1000, 777, 50, np.int32, False), (0, 9, 3, np.int32, False),
+                                 (7, 0, 3, np.int64, True), (1, 1, 2, np.int32, False),
+                                 (5001, 12, 1000, np.uint64, True), (300, 4000, 7, np.uint32, True),
+                                 (2048, 2048, None, np.uint64, False)]:
+        info = np.iinfo(dt)
+        if spread is None:
+            A = np.sort(rng.integers(info.min, info.max, m, dtype=dt, endpoint=True))
+            B = np.sort(rng.integers(info.min, info.max, n, dtype=dt, endpoint=True))
+        else:
+            top = dt(info.max - spread) if info.min == 0 else dt(0)
+            A = np.sort(rng.integers(0, spread, m).astype(dt) + top)
+            B = np.sort(rng.integers(0, spread, n).astype(dt) + top)
+        Av = rng.standard_normal(m).astype(np.float32) if kv else None
+        Bv = rng.standard_normal(n).astype(np.float32) if kv else None
+        kt = {np.int32: "i32", np.uint32: "u32", np.int64: "i64", np.uint64: "u64"}[dt]
+        cases.append((A, Av, B, Bv, _cuts(rng, m, world), _cuts(rng, n, world), kt))
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dist_worker, args=(r, world, port, cases, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=180) for _ in range(world * len(cases))]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for ci, (A, Av, B, Bv, _, _, _) in enumerate(cases):
+        if Av is None:
+            want, _ = oracle.merge(A, B)
+            wantv = None
+        else:
+            want, wantv, _ = oracle.merge_kv(A, Av, B, Bv)
+        got = sorted((r for r in results if r[0] == ci), key=lambda r: r[1])
+        assert len(got) == world
+        for rank, (_, _, (k0, k1, i0, i1, j0, j1), cb, cvb) in enumerate(got):
+            assert (k0, k1) == shard.block_bounds(len(A) + len(B), world, rank)
+            assert (i0, j0) == tuple(oracle.co_rank(k0, A, B)[:2])
+            assert (i1, j1) == tuple(oracle.co_rank(k1, A, B)[:2])
+            assert cb == want[k0:k1].tobytes(), (ci, rank)
+            if wantv is not None:
+                assert cvb == wantv[k0:k1].tobytes(), (ci, rank)
