@@ -727,26 +727,36 @@ def run_row(args):
                 timer.marks.append((None, timer.marks[-1][1]))
         torch.cuda.synchronize()
         un = {lb: round(ms / K, 4) for lb, ms in timer.totals().items()}
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         Yk, Yv = torch.empty_like(Xu), torch.empty_like(Xuv)
         gXr = torch.empty_like(gY)
+        perm = torch.empty(N, dtype=torch.int16, device=dev)
         for rep in range(3):
             ev[0].record(stream)
             api.sort_runs(Xu, Xuv, key_type="u64", out=(Yk, Yv))
             ev[1].record(stream)
             api.sort_runs_backward(Xu, gY, key_type="u64", out=gXr)
             ev[2].record(stream)
+            api.sort_runs_record(Xu, Xuv, key_type="u64", out=(Yk, Yv), perm=perm)
+            ev[3].record(stream)
+            api.sort_runs_backward_recorded(perm, gY, out=gXr)
+            ev[4].record(stream)
         torch.cuda.synchronize()
-        f, b = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        tms = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+
+        def row(ms, bpe):
+            gbs = bpe * N / (ms / 1e3) / 1e9
+            return {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+        # bytes per element: keys + payloads in and out; backward replay reads
+        # keys and gY, writes gX; the recorded forms add / read the 2-byte
+        # permutation instead of the keys
         unsorted = {"run": api.sort_run_length(), "passes": plan.passes,
                     "fwd_graph_ms": un["fwd_graph"], "bwd_graph_ms": un["bwd_graph"],
                     "elements_per_s": N / ((un["fwd_graph"] + un["bwd_graph"]) / 1e3),
-                    "sort_runs": {"ms": round(f, 4), "gbs": round(24 * N / (f / 1e3) / 1e9, 1),
-                                  "frac": round(24 * N / (f / 1e3) / 1e9 / peak, 4)},
-                    "sort_runs_backward": {"ms": round(b, 4),
-                                           "gbs": round(16 * N / (b / 1e3) / 1e9, 1),
-                                           "frac": round(16 * N / (b / 1e3) / 1e9 / peak, 4)}}
-        del plan, Xu, Xuv, Yk, Yv, gXr
+                    "sort_runs": row(tms[0], 24), "sort_runs_backward": row(tms[1], 16),
+                    "sort_runs_record": row(tms[2], 26),
+                    "sort_runs_backward_recorded": row(tms[3], 10)}
+        del plan, Xu, Xuv, Yk, Yv, gXr, perm
         torch.cuda.empty_cache()
         P = len(per_pass["record"])
         rec = rows["record"]

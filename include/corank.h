@@ -306,6 +306,19 @@ cr_status cr_sort_runs(int key_type, int val_bytes, const void* X, const void* X
 cr_status cr_sort_runs_backward(int key_type, int val_bytes, const void* X, int64_t N,
                                 const void* gY, void* gX, cr_stream stream);
 
+/* Recorded run formation: the same forward as cr_sort_runs (val_bytes 4 or
+ * 8) that also writes each run's permutation, perm[base + x] = index inside
+ * the run of the input element that became output x (uint16, N entries,
+ * 16-byte aligned, must not overlap the other arrays).  Its backward
+ * cr_sort_runs_backward_recorded reads no keys: gX[base + perm[base + x]] =
+ * gY[base + x] within every run.  It must get the perm written by the
+ * forward for the same N (entries pointing outside their run are skipped). */
+cr_status cr_sort_runs_record(int key_type, int val_bytes, const void* X, const void* Xv,
+                              int64_t N, void* Y, void* Yv, uint16_t* perm, cr_stream stream);
+
+cr_status cr_sort_runs_backward_recorded(int val_bytes, int64_t N, const uint16_t* perm,
+                                         const void* gY, void* gX, cr_stream stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free stable merge (the paper has no counterpart: this is a
  * deployment convenience of this library).

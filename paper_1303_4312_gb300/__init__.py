@@ -17,7 +17,7 @@ __all__ = [
     "merge_pass_backward", "workspace_status", "tile_size", "CorankError", "merge_sort",
     "MergeSortPlan", "MergeMany", "merge_many", "HostMerger", "sort_runs", "sort_runs_backward",
     "sort_run_length", "PassRecord", "merge_pass_record", "merge_pass_backward_recorded",
-    "merge_pass_record_bytes",
+    "merge_pass_record_bytes", "sort_runs_record", "sort_runs_backward_recorded",
 ]
 
 

@@ -59,6 +59,8 @@ SIGNATURES = {
     "cr_workspace_status": ([P, P], INT),
     "cr_sort_run_length": ([], I64),
     "cr_sort_runs": ([INT, INT, P, P, I64, P, P, P], INT),
+    "cr_sort_runs_record": ([INT, INT, P, P, I64, P, P, P, P], INT),
+    "cr_sort_runs_backward_recorded": ([INT, I64, P, P, P, P], INT),
     "cr_sort_runs_backward": ([INT, INT, P, I64, P, P, P], INT),
     "cr_stable_merge_noalloc": ([INT, P, I64, P, I64, P, P, P], INT),
 }

@@ -583,6 +583,31 @@ def sort_runs_backward(X, gY, key_type: str | None = None, out=None):
     return gX
 
 
+def sort_runs_record(X, Xv, key_type: str | None = None, out=None, perm=None):
+    """sort_runs that also writes each run's permutation (int16 container of
+    uint16 in-run indices) for sort_runs_backward_recorded.  Returns
+    (Y, Yv, perm)."""
+    lib = _lib.load()
+    dev = _dev(X, Xv)
+    kt = _key_code(X, key_type)
+    Y, Yv = out if out is not None else (torch.empty_like(X), torch.empty_like(Xv))
+    if perm is None:
+        perm = torch.empty(X.numel(), dtype=torch.int16, device=dev)
+    _lib.check(lib.cr_sort_runs_record(kt, Xv.element_size(), _ptr(X), _ptr(Xv), X.numel(),
+                                       _ptr(Y), _ptr(Yv), _ptr(perm), _stream(dev)))
+    return Y, Yv, perm
+
+
+def sort_runs_backward_recorded(perm, gY, out=None):
+    """Payload gradient of sort_runs_record from its permutation (no keys)."""
+    lib = _lib.load()
+    dev = _dev(perm, gY)
+    gX = out if out is not None else torch.empty_like(gY)
+    _lib.check(lib.cr_sort_runs_backward_recorded(gY.element_size(), gY.numel(), _ptr(perm),
+                                                  _ptr(gY), _ptr(gX), _stream(dev)))
+    return gX
+
+
 class MergeSortPlan:
     """Buffers and (optionally) CUDA graphs for a stable merge sort of N keys
     with payloads.
@@ -594,9 +619,9 @@ class MergeSortPlan:
 
     The backward needs every pass's merge decisions.  With ``record=True``
     (default) each forward pass records them (cr_merge_pass_record: its tile
-    table plus one bit per element) and the backward routes gradients from
-    those records without reading keys; keys then ping-pong between two
-    buffers.  With ``record=False`` the input keys of every pass are kept
+    table plus one bit per element; run formation: each run's permutation,
+    two bytes per element) and the backward routes gradients from those
+    records without reading keys; keys then ping-pong between two buffers.  With ``record=False`` the input keys of every pass are kept
     ((passes + 1) * N key slots) and the backward re-merges them
     (cr_merge_pass_backward).  Payloads and gradients ping-pong between two
     buffers; with run formation the unsorted input keys are kept too.
@@ -628,6 +653,8 @@ class MergeSortPlan:
                            if self.form_runs else None)
         kt = key_type or _DTYPE_KEY[key_dtype]
         vb = torch.empty(0, dtype=val_dtype).element_size()
+        self.run_perm = (torch.empty(self.N, dtype=torch.int16, device=self.device)
+                         if self.record and self.form_runs else None)
         if self.record:
             self.records = [new_pass_record(kt, vb, self.N, w, self.device) for w in self.widths]
             self.ws = None
@@ -657,7 +684,10 @@ class MergeSortPlan:
             self.vals[0].copy_(Xv)
 
     def _forward_body(self):
-        if self.form_runs:
+        if self.form_runs and self.record:
+            sort_runs_record(self.input_keys, self.vals[1], key_type=self.key_type,
+                             out=(self.keys[0], self.vals[0]), perm=self.run_perm)
+        elif self.form_runs:
             sort_runs(self.input_keys, self.vals[1], key_type=self.key_type,
                       out=(self.keys[0], self.vals[0]))
         for p, w in enumerate(self.widths):
@@ -677,7 +707,9 @@ class MergeSortPlan:
             else:
                 merge_pass_backward(self.keys[p], src, self.widths[p], key_type=self.key_type,
                                     out=self.grads[p & 1], ws=self.ws)
-        if self.form_runs:
+        if self.form_runs and self.record:
+            sort_runs_backward_recorded(self.run_perm, self.grads[0], out=self.grads[1])
+        elif self.form_runs:
             sort_runs_backward(self.input_keys, self.grads[0], key_type=self.key_type,
                                out=self.grads[1])
 

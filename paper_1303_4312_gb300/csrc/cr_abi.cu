@@ -717,22 +717,57 @@ cr_status cr_merge_pass_backward_recorded(int key_type, int val_bytes, int64_t N
 
 int64_t cr_sort_run_length(void) { return cr::kSortRun; }
 
-cr_status cr_sort_runs(int key_type, int val_bytes, const void* X, const void* Xv, int64_t N,
-                       void* Y, void* Yv, cr_stream stream) {
+namespace {
+
+cr_status sort_runs_common(int key_type, int val_bytes, const void* X, const void* Xv, int64_t N,
+                           void* Y, void* Yv, uint16_t* perm, cr_stream stream) {
     CR_TRY(check_key_type(key_type));
-    CR_TRY(check_vb(val_bytes, true));
+    CR_TRY(check_vb(val_bytes, perm == nullptr));
     if (N < 0) return fail(CR_EINVAL, "negative size");
     const int ks = key_bytes(key_type);
     const int vb = val_bytes;
     const Arr ins[2] = {{X, N, ks, "X"}, {vb ? Xv : nullptr, vb ? N : 0, vb, "X payload"}};
-    const Arr outs[2] = {{Y, N, ks, "Y"}, {vb ? Yv : nullptr, vb ? N : 0, vb, "Y payload"}};
+    const Arr outs[3] = {{Y, N, ks, "Y"}, {vb ? Yv : nullptr, vb ? N : 0, vb, "Y payload"},
+                         {perm, perm ? N : 0, 2, "perm"}};
     for (const Arr& a : ins) CR_TRY(check_arr(a));
     for (const Arr& a : outs) CR_TRY(check_arr(a));
-    CR_TRY(check_no_alias(outs, 2, ins, 2));
+    CR_TRY(check_no_alias(outs, 3, ins, 2));
     if (N == 0) return ok();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = by_key(key_type, [&](auto ops) { return ops.sort_runs(vb, X, Xv, N, Y, Yv, st); });
+    cudaError_t e = by_key(key_type, [&](auto ops) {
+        return ops.sort_runs(vb, X, Xv, N, Y, Yv, perm, st);
+    });
     if (e != cudaSuccess) return cuda_fail(e, "run sort launch");
+    return ok();
+}
+
+}  // namespace
+
+cr_status cr_sort_runs(int key_type, int val_bytes, const void* X, const void* Xv, int64_t N,
+                       void* Y, void* Yv, cr_stream stream) {
+    return sort_runs_common(key_type, val_bytes, X, Xv, N, Y, Yv, nullptr, stream);
+}
+
+cr_status cr_sort_runs_record(int key_type, int val_bytes, const void* X, const void* Xv,
+                              int64_t N, void* Y, void* Yv, uint16_t* perm, cr_stream stream) {
+    CR_TRY(check_vb(val_bytes, false));
+    if (perm == nullptr && N > 0) return fail(CR_EINVAL, "perm is NULL");
+    return sort_runs_common(key_type, val_bytes, X, Xv, N, Y, Yv, perm, stream);
+}
+
+cr_status cr_sort_runs_backward_recorded(int val_bytes, int64_t N, const uint16_t* perm,
+                                         const void* gY, void* gX, cr_stream stream) {
+    CR_TRY(check_vb(val_bytes, false));
+    if (N < 0) return fail(CR_EINVAL, "negative size");
+    const Arr ins[2] = {{perm, N, 2, "perm"}, {gY, N, val_bytes, "gY"}};
+    const Arr outs[1] = {{gX, N, val_bytes, "gX"}};
+    for (const Arr& a : ins) CR_TRY(check_arr(a));
+    CR_TRY(check_arr(outs[0]));
+    CR_TRY(check_no_alias(outs, 1, ins, 2));
+    if (N == 0) return ok();
+    const cudaError_t e = cr::sort_route_recorded(val_bytes, N, perm, gY, gX,
+                                                  static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "recorded run sort backward launch");
     return ok();
 }
 

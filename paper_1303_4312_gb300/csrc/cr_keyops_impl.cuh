@@ -168,11 +168,11 @@ cudaError_t KeyOps<K>::partition_batched(const void* A, const void* B, const int
     return cudaGetLastError();
 }
 
-template <class K, int VB, bool BWD>
+template <class K, int VB, int MODE>
 cudaError_t launch_sort_runs(const void* X, const void* Xv, int64_t N, void* Y, void* Yv,
-                             const void* gY, void* gX, cudaStream_t st) {
-    using L = SortLayout<K, VB, BWD, kSortNT, kSortIPT>;
-    auto kern = sort_runs_kernel<K, VB, BWD, kSortNT, kSortIPT>;
+                             uint16_t* perm, const void* gY, void* gX, cudaStream_t st) {
+    using L = SortLayout<K, VB, MODE, kSortNT, kSortIPT>;
+    auto kern = sort_runs_kernel<K, VB, MODE, kSortNT, kSortIPT>;
     static LaunchShape cache[kMaxDevices];
     static std::once_flag once[kMaxDevices];
     LaunchShape sh;
@@ -181,24 +181,29 @@ cudaError_t launch_sort_runs(const void* X, const void* Xv, int64_t N, void* Y, 
     if (N <= 0) return cudaSuccess;
     const unsigned grid = unsigned((N + kSortRun - 1) / kSortRun);
     kern<<<grid, kSortNT, L::TOTAL, st>>>(static_cast<const K*>(X), Xv, N, static_cast<K*>(Y), Yv,
-                                          gY, gX);
+                                          perm, gY, gX);
     return cudaGetLastError();
 }
 
 template <class K>
 cudaError_t KeyOps<K>::sort_runs(int vb, const void* X, const void* Xv, int64_t N, void* Y,
-                                 void* Yv, cudaStream_t st) {
-    if (vb == 0) return launch_sort_runs<K, 0, false>(X, Xv, N, Y, Yv, nullptr, nullptr, st);
-    if (vb == 4) return launch_sort_runs<K, 4, false>(X, Xv, N, Y, Yv, nullptr, nullptr, st);
-    if (vb == 8) return launch_sort_runs<K, 8, false>(X, Xv, N, Y, Yv, nullptr, nullptr, st);
+                                 void* Yv, uint16_t* perm, cudaStream_t st) {
+    if (perm != nullptr) {
+        if (vb == 4) return launch_sort_runs<K, 4, 1>(X, Xv, N, Y, Yv, perm, nullptr, nullptr, st);
+        if (vb == 8) return launch_sort_runs<K, 8, 1>(X, Xv, N, Y, Yv, perm, nullptr, nullptr, st);
+        return cudaErrorInvalidValue;
+    }
+    if (vb == 0) return launch_sort_runs<K, 0, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, st);
+    if (vb == 4) return launch_sort_runs<K, 4, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, st);
+    if (vb == 8) return launch_sort_runs<K, 8, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, st);
     return cudaErrorInvalidValue;
 }
 
 template <class K>
 cudaError_t KeyOps<K>::sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
                                           void* gX, cudaStream_t st) {
-    if (vb == 4) return launch_sort_runs<K, 4, true>(X, nullptr, N, nullptr, nullptr, gY, gX, st);
-    if (vb == 8) return launch_sort_runs<K, 8, true>(X, nullptr, N, nullptr, nullptr, gY, gX, st);
+    if (vb == 4) return launch_sort_runs<K, 4, 2>(X, nullptr, N, nullptr, nullptr, nullptr, gY, gX, st);
+    if (vb == 8) return launch_sort_runs<K, 8, 2>(X, nullptr, N, nullptr, nullptr, nullptr, gY, gX, st);
     return cudaErrorInvalidValue;
 }
 
@@ -250,7 +255,7 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
     template cudaError_t cr::KeyOps<K>::co_rank_one(const void*, int64_t, const void*,         \
                                                     int64_t, int64_t, int64_t*, cudaStream_t); \
     template cudaError_t cr::KeyOps<K>::sort_runs(int, const void*, const void*, int64_t,      \
-                                                  void*, void*, cudaStream_t);                 \
+                                                  void*, void*, uint16_t*, cudaStream_t);      \
     template cudaError_t cr::KeyOps<K>::sort_runs_backward(int, const void*, int64_t,          \
                                                            const void*, void*, cudaStream_t);
 

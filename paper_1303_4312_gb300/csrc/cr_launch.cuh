@@ -115,9 +115,10 @@ struct KeyOps {
     static cudaError_t co_rank_one(const void* A, int64_t m, const void* B, int64_t n, int64_t r,
                                    int64_t* out, cudaStream_t st);
     // Run formation: stably sort runs of kSortRun elements (vb 0, 4, 8);
-    // backward (vb 4, 8): gX from gY through the same in-run permutation.
+    // with perm (vb 4, 8) also write each run's permutation; backward
+    // (vb 4, 8): gX from gY through the same in-run permutation, replayed.
     static cudaError_t sort_runs(int vb, const void* X, const void* Xv, int64_t N, void* Y,
-                                 void* Yv, cudaStream_t st);
+                                 void* Yv, uint16_t* perm, cudaStream_t st);
     static cudaError_t sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
                                           void* gX, cudaStream_t st);
 };
@@ -129,6 +130,11 @@ struct KeyOps {
 cudaError_t route_recorded(int vb, void* ws, const uint32_t* flags, int64_t flag_words,
                            int64_t N, int64_t w, int64_t tile, const void* gY, void* gX,
                            cudaStream_t st);
+
+// Backward of a recorded run formation (vb in {4,8}): within every run of
+// kSortRun elements, gX[base + perm[base + x]] = gY[base + x].
+cudaError_t sort_route_recorded(int vb, int64_t N, const uint16_t* perm, const void* gY, void* gX,
+                                cudaStream_t st);
 
 // Tiles of a merge pass over N elements with run width w.
 inline int64_t pass_tiles(int64_t N, int64_t w, int64_t tile, int64_t* tpp_out,

@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(kRouteThreads) route_recorded_kernel(
         return;
     }
     // output window of tile t from the pass geometry (t < ntiles, so q is a
-    // pair of the pass and gc + len <= N)
-    const int64_t q = t / tpp;
+    // pair of the pass and gc + len <= N); t < 2^31 (one CTA per tile)
+    const int64_t q = int64_t(uint32_t(t) / uint32_t(tpp));
     const int64_t a0 = 2 * q * w;
     const int64_t pair = (N - a0 < 2 * w) ? N - a0 : 2 * w;
     const int64_t r0 = (t - q * tpp) * tile;
@@ -135,17 +135,61 @@ __global__ void __launch_bounds__(kRouteThreads) route_recorded_kernel(
         }
     }
 
-    V* gx = static_cast<V*>(gX);
+    // x = tid + 128 i: a warp's 32 outputs are exactly flag word x / 32
+    // (warp-uniform loads), and output x's bit is the lane's bit
+    V* const pa = static_cast<V*>(gX) + r.ga;
+    V* const pb = static_cast<V*>(gX) + r.gb;
+    const int lane = tid & 31;
+    const uint32_t below = (1u << lane) - 1u;
     for (int x = tid; x < len; x += kRouteThreads) {
         const uint32_t word = s_word[x >> 5];
-        const int bit = x & 31;
-        const int rb = s_pre[x >> 5] + __popc(word & ((1u << bit) - 1u));
-        if ((word >> bit) & 1u) gx[r.gb + rb] = s_val[x];
-        else gx[r.ga + (x - rb)] = s_val[x];
+        const int rb = s_pre[x >> 5] + __popc(word & below);
+        V* const dst = ((word >> lane) & 1u) ? pb + rb : pa + (x - rb);
+        *dst = s_val[x];
     }
 }
 
+// Backward of a recorded run formation: one CTA per run of kSortRun
+// elements scatters the run's gradients through its permutation in shared
+// memory (gX[perm[x]] = gY[x]) and stores them coalesced.  Entries outside
+// the run are skipped (the permutation comes from the forward).
+constexpr int kSortRouteThreads = 256;
+
+template <int VB>
+__global__ void __launch_bounds__(kSortRouteThreads) sort_route_kernel(
+    int64_t N, const uint16_t* __restrict__ perm, const void* __restrict__ gY,
+    void* __restrict__ gX) {
+    using V = typename VBits<VB>::T;
+    extern __shared__ __align__(16) unsigned char route_smem[];
+    V* s = reinterpret_cast<V*>(route_smem);
+    const int64_t base = int64_t(blockIdx.x) * kSortRun;
+    const int len = int(N - base < kSortRun ? N - base : kSortRun);
+    const V* gy = static_cast<const V*>(gY) + base;
+    for (int x = threadIdx.x; x < len; x += kSortRouteThreads) {
+        const int p = perm[base + x];
+        if (p < len) s[p] = gy[x];
+    }
+    __syncthreads();
+    V* gx = static_cast<V*>(gX) + base;
+    for (int x = threadIdx.x; x < len; x += kSortRouteThreads) gx[x] = s[x];
+}
+
 }  // namespace
+
+cudaError_t sort_route_recorded(int vb, int64_t N, const uint16_t* perm, const void* gY, void* gX,
+                                cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const int64_t runs = (N + kSortRun - 1) / kSortRun;
+    if (runs > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const size_t smem = size_t(kSortRun) * size_t(vb);   // 14 KB at most
+    if (vb == 4)
+        sort_route_kernel<4><<<unsigned(runs), kSortRouteThreads, smem, st>>>(N, perm, gY, gX);
+    else if (vb == 8)
+        sort_route_kernel<8><<<unsigned(runs), kSortRouteThreads, smem, st>>>(N, perm, gY, gX);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 cudaError_t route_recorded(int vb, void* ws, const uint32_t* flags, int64_t flag_words, int64_t N,
                            int64_t w, int64_t tile, const void* gY, void* gX, cudaStream_t st) {

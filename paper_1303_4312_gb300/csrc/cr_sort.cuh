@@ -3,19 +3,24 @@
 // their payloads) in shared memory, so that the merge passes can take over
 // from runs of R.
 //
-//  1. coalesced load of the run into shared memory;
-//  2. each thread sorts its IPT consecutive elements in registers by odd-even
-//     transposition (adjacent swaps only when strictly greater: stable);
+//  1. coalesced load of the run's keys (and payloads) into shared memory;
+//     every key is paired with its index inside the run (16 bits);
+//  2. each thread sorts its IPT consecutive (key, index) pairs in registers
+//     by odd-even transposition (adjacent swaps only when strictly greater:
+//     stable);
 //  3. log2(NT) rounds of in-block merges: round r merges neighbouring sorted
 //     runs of IPT*2^r; each thread produces IPT outputs, co-ranking its
 //     diagonal inside its pair of runs (the split of Lemma 1, binary lifting)
-//     and merging serially (ties take the left run, which holds the earlier
-//     elements: stable);
-//  4. coalesced store.
+//     and merging serially with one index-selected load per step (ties take
+//     the left run, which holds the earlier elements: stable);
+//  4. coalesced store of the keys; the payloads are gathered once through
+//     the carried indices (they never move during the rounds).
 //
-// Backward (payload gradient of the run sort): the same sort is replayed on
-// (key, local index) pairs to recover the permutation, then gX[perm[x]] =
-// gY[x] inside the run, scattered through shared memory.
+// MODE 0: forward.  MODE 1: forward that also writes the run's permutation
+// (perm[base + x] = input index inside the run of output x), for a backward
+// that needs no keys.  MODE 2: backward by replay: the same sort on the
+// input keys recovers the permutation, then gX[perm[x]] = gY[x] inside the
+// run, scattered through shared memory.
 #pragma once
 
 #include "cr_device.cuh"
@@ -23,34 +28,37 @@
 
 namespace cr {
 
-template <class K, int VB, bool BWD, int NT, int IPT>
+template <class K, int VB, int MODE, int NT, int IPT>
 struct SortLayout {
     static constexpr int R = NT * IPT;
-    // payload carried through the rounds: the values (forward) or the
-    // element's index inside the run (backward)
-    using P = typename std::conditional<BWD, uint32_t, typename VBits<VB>::T>::type;
-    static constexpr bool CARRY = BWD || VB != 0;
-    static constexpr size_t KEYS = align_up_sz(size_t(R) * sizeof(K), 128);
-    static constexpr size_t PAY = CARRY ? align_up_sz(size_t(R) * sizeof(P), 128) : 0;
-    static constexpr size_t GRAD = BWD ? align_up_sz(size_t(R) * (VB ? VB : 4), 128) * 2 : 0;
-    static constexpr size_t TOTAL = 2 * (KEYS + PAY) + GRAD + 128;
+    static_assert(R <= 65536, "run indices are 16-bit");
+    // one element of slack: a merge step may read one past its pair
+    static constexpr size_t KEYS = align_up_sz(size_t(R + 1) * sizeof(K), 128);
+    static constexpr bool IDX = VB != 0 || MODE != 0;
+    static constexpr size_t INDEX = IDX ? align_up_sz(size_t(R + 1) * 2, 128) : 0;
+    // MODE 0/1: the input payloads; MODE 2: gradient staging
+    static constexpr size_t VALS = VB ? align_up_sz(size_t(R) * VB, 128) : 0;
+    static constexpr size_t TOTAL = 2 * (KEYS + INDEX) + VALS;
     static_assert(TOTAL <= 232448, "run does not fit shared memory");
 };
 
-template <class K, int VB, bool BWD, int NT, int IPT>
+template <class K, int VB, int MODE, int NT, int IPT>
 __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
                                                        const void* __restrict__ Xv, int64_t N,
                                                        K* __restrict__ Y, void* __restrict__ Yv,
+                                                       uint16_t* __restrict__ perm,
                                                        const void* __restrict__ gY,
                                                        void* __restrict__ gX) {
-    using L = SortLayout<K, VB, BWD, NT, IPT>;
-    using P = typename L::P;
+    using L = SortLayout<K, VB, MODE, NT, IPT>;
     using V = typename VBits<VB>::T;
+    constexpr bool IDX = L::IDX;
     constexpr int R = L::R;
     extern __shared__ __align__(128) unsigned char smem[];
-    K* sk[2] = {reinterpret_cast<K*>(smem), reinterpret_cast<K*>(smem + L::KEYS)};
-    P* sp[2] = {reinterpret_cast<P*>(smem + 2 * L::KEYS),
-                reinterpret_cast<P*>(smem + 2 * L::KEYS + L::PAY)};
+    K* const sk0 = reinterpret_cast<K*>(smem);
+    K* const sk1 = reinterpret_cast<K*>(smem + L::KEYS);
+    uint16_t* const si0 = reinterpret_cast<uint16_t*>(smem + 2 * L::KEYS);
+    uint16_t* const si1 = reinterpret_cast<uint16_t*>(smem + 2 * L::KEYS + L::INDEX);
+    V* const sv = reinterpret_cast<V*>(smem + 2 * (L::KEYS + L::INDEX));
 
     const int tid = threadIdx.x;
     const int64_t base = int64_t(blockIdx.x) * R;
@@ -58,11 +66,9 @@ __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
 
     // 1. load
     for (int x = tid; x < len; x += NT) {
-        sk[0][x] = X[base + x];
-        if constexpr (L::CARRY) {
-            if constexpr (BWD) sp[0][x] = uint32_t(x);
-            else sp[0][x] = static_cast<const V*>(Xv)[base + x];
-        }
+        sk0[x] = X[base + x];
+        if constexpr (IDX) si0[x] = uint16_t(x);
+        if constexpr (VB != 0 && MODE != 2) sv[x] = static_cast<const V*>(Xv)[base + x];
     }
     __syncthreads();
 
@@ -71,12 +77,12 @@ __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
     const int cnt = d0 < len ? (len - d0 < IPT ? len - d0 : IPT) : 0;
     {
         K rk[IPT];
-        P rp[L::CARRY ? IPT : 1];
+        uint16_t ri[IDX ? IPT : 1];
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
             if (q < cnt) {
-                rk[q] = sk[0][d0 + q];
-                if constexpr (L::CARRY) rp[q] = sp[0][d0 + q];
+                rk[q] = sk0[d0 + q];
+                if constexpr (IDX) ri[q] = si0[d0 + q];
             }
         }
 #pragma unroll
@@ -87,10 +93,10 @@ __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
                     const K tk = rk[q];
                     rk[q] = rk[q + 1];
                     rk[q + 1] = tk;
-                    if constexpr (L::CARRY) {
-                        const P tp = rp[q];
-                        rp[q] = rp[q + 1];
-                        rp[q + 1] = tp;
+                    if constexpr (IDX) {
+                        const uint16_t tp = ri[q];
+                        ri[q] = ri[q + 1];
+                        ri[q + 1] = tp;
                     }
                 }
             }
@@ -98,8 +104,8 @@ __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
             if (q < cnt) {
-                sk[0][d0 + q] = rk[q];
-                if constexpr (L::CARRY) sp[0][d0 + q] = rp[q];
+                sk0[d0 + q] = rk[q];
+                if constexpr (IDX) si0[d0 + q] = ri[q];
             }
         }
     }
@@ -109,59 +115,57 @@ __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
     //    thread's IPT outputs never straddle two pairs)
     int cur = 0;
     for (int w = IPT; w < len; w *= 2) {
-        const K* ik = sk[cur];
-        const P* ip = sp[cur];
-        K* ok = sk[cur ^ 1];
-        P* op = sp[cur ^ 1];
+        const K* ik = cur ? sk1 : sk0;
+        const uint16_t* ii = cur ? si1 : si0;
+        K* ok = cur ? sk0 : sk1;
+        uint16_t* oi = cur ? si0 : si1;
         if (cnt > 0) {
             const int ps = (d0 / (2 * w)) * (2 * w);      // pair start
             const int alen = min(w, len - ps);
             const int blen = max(0, min(w, len - ps - alen));
-            const K* sA = ik + ps;
-            const K* sB = ik + ps + alen;
+            const int bs = ps + alen;                      // B run start
             const int dd[1] = {d0 - ps};
             int jj[1];
-            split_in_tile<Log2Ceil<R + 1>::v>(sA, alen, sB, blen, dd, jj);
+            split_in_tile<Log2Ceil<R + 1>::v>(ik + ps, alen, ik + bs, blen, dd, jj);
             int j = jj[0], k = dd[0] - j;
-            K a = j < alen ? sA[j] : K(0);
-            K b = k < blen ? sB[k] : K(0);
+            // ik[bs + blen] is at most ik[len] <= ik[R]: inside the slack
+            K a = ik[ps + j];
+            K b = ik[bs + k];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 if (q < cnt) {
                     const bool takeA = (k >= blen) || (j < alen && !(b < a));
+                    const int src = takeA ? ps + j : bs + k;
                     ok[d0 + q] = takeA ? a : b;
-                    if constexpr (L::CARRY) op[d0 + q] = takeA ? ip[ps + j] : ip[ps + alen + k];
+                    if constexpr (IDX) oi[d0 + q] = ii[src];
                     j += takeA ? 1 : 0;
                     k += takeA ? 0 : 1;
-                    if (takeA) {
-                        if (j < alen) a = sA[j];
-                    } else {
-                        if (k < blen) b = sB[k];
-                    }
+                    const K nx = ik[takeA ? ps + j : bs + k];   // never taken when past a run
+                    a = takeA ? nx : a;
+                    b = takeA ? b : nx;
                 }
             }
         }
         __syncthreads();
         cur ^= 1;
     }
+    const K* fk = cur ? sk1 : sk0;
+    const uint16_t* fi = cur ? si1 : si0;
 
     // 4. store
-    if constexpr (!BWD) {
+    if constexpr (MODE != 2) {
         for (int x = tid; x < len; x += NT) {
-            Y[base + x] = sk[cur][x];
-            if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sp[cur][x];
+            Y[base + x] = fk[x];
+            if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[fi[x]];
+            if constexpr (MODE == 1) perm[base + x] = fi[x];
         }
     } else {
         // gradient: gX[perm[x]] = gY[x] within the run
-        V* g0 = reinterpret_cast<V*>(smem + 2 * (L::KEYS + L::PAY));
-        V* g1 = reinterpret_cast<V*>(smem + 2 * (L::KEYS + L::PAY) + L::GRAD / 2);
         const V* gy = static_cast<const V*>(gY);
-        for (int x = tid; x < len; x += NT) g0[x] = gy[base + x];
-        __syncthreads();
-        for (int x = tid; x < len; x += NT) g1[sp[cur][x]] = g0[x];
+        for (int x = tid; x < len; x += NT) sv[fi[x]] = gy[base + x];
         __syncthreads();
         V* gx = static_cast<V*>(gX);
-        for (int x = tid; x < len; x += NT) gx[base + x] = g1[x];
+        for (int x = tid; x < len; x += NT) gx[base + x] = sv[x];
     }
 }
 

@@ -207,3 +207,21 @@ def test_recorded_pass_sizes_and_validation(lib):
     assert bwd(0, 4, N, 0, F, fw.value, G, GX, WS, ws.value, None) == 1
     # nothing to do is fine
     assert bwd(0, 4, 0, w, None, 0, None, None, None, 0, None) == 0
+
+
+def test_recorded_run_sort_validation(lib):
+    X, Xv = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000)
+    Y, Yv = ctypes.c_void_p(0x300000), ctypes.c_void_p(0x400000)
+    P = ctypes.c_void_p(0x500000)
+    N = 5000
+    # keys-only payload width, NULL perm, misaligned or overlapping perm
+    assert lib.cr_sort_runs_record(0, 0, X, None, N, Y, None, P, None) == 1
+    assert lib.cr_sort_runs_record(0, 4, X, Xv, N, Y, Yv, None, None) == 1
+    assert lib.cr_sort_runs_record(0, 4, X, Xv, N, Y, Yv, ctypes.c_void_p(0x500002), None) == 3
+    assert lib.cr_sort_runs_record(0, 4, X, Xv, N, Y, Yv, ctypes.c_void_p(0x300010), None) == 2
+    assert lib.cr_sort_runs_record(9, 4, X, Xv, N, Y, Yv, P, None) == 1
+    G, GX = ctypes.c_void_p(0x600000), ctypes.c_void_p(0x700000)
+    assert lib.cr_sort_runs_backward_recorded(0, N, P, G, GX, None) == 1
+    assert lib.cr_sort_runs_backward_recorded(4, -1, P, G, GX, None) == 1
+    assert lib.cr_sort_runs_backward_recorded(4, N, P, G, ctypes.c_void_p(0x600100), None) == 2
+    assert lib.cr_sort_runs_backward_recorded(4, 0, None, None, None, None) == 0

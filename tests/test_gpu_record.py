@@ -156,3 +156,44 @@ def test_merge_sort_both_backward_forms(record, run):
         g = np.empty_like(gY)
         g[o] = gY
         assert same_bits(host(Xvt.grad, np.float32), g), N
+
+
+@pytest.mark.parametrize("dt", KEY_DTYPES)
+@pytest.mark.parametrize("vb", [4, 8])
+def test_recorded_run_formation(dt, vb):
+    """sort_runs_record: every run of sort_run_length() elements stably
+    sorted with its payloads, the written permutation equal to numpy's stable
+    argsort of the run, and the recorded backward routing gY through it; the
+    plain and replayed forms give the same results."""
+    rng = np.random.default_rng(340 + vb)
+    vdt = VAL_DTYPES[vb]
+    kt = key_type(np.empty(0, dt))
+    R = cr.sort_run_length()
+    info = np.iinfo(dt)
+    for N in (1, R - 1, R, R + 1, 7 * R + 123, 100003):
+        for spread in (None, 4):
+            if spread is None:
+                X = rng.integers(info.min, info.max, N, dtype=dt, endpoint=True)
+            else:
+                X = rng.integers(0, spread, N).astype(dt)
+            Xv = rng.standard_normal(N).astype(vdt)
+            gY = rng.standard_normal(N).astype(vdt)
+            Y, Yv, perm = cr.sort_runs_record(dev(X), dev(Xv), key_type=kt)
+            gX = cr.sort_runs_backward_recorded(perm, dev(gY))
+            Y2, Yv2 = cr.sort_runs(dev(X), dev(Xv), key_type=kt)
+            gX2 = cr.sort_runs_backward(dev(X), dev(gY), key_type=kt)
+            torch.cuda.synchronize()
+            p = host(perm, np.uint16).astype(np.int64)
+            wy, wyv, wg = np.empty_like(X), np.empty_like(Xv), np.empty_like(gY)
+            for b0 in range(0, N, R):
+                o = np.argsort(X[b0:b0 + R], kind="stable")
+                assert np.array_equal(p[b0:b0 + len(o)], o), (N, b0)
+                wy[b0:b0 + len(o)] = X[b0:b0 + R][o]
+                wyv[b0:b0 + len(o)] = Xv[b0:b0 + R][o]
+                g = np.empty(len(o), dtype=vdt)
+                g[o] = gY[b0:b0 + len(o)]
+                wg[b0:b0 + len(o)] = g
+            assert same_bits(host(Y, dt), wy) and same_bits(host(Yv, vdt), wyv), N
+            assert same_bits(host(gX, vdt), wg), N
+            assert same_bits(host(Y2, dt), wy) and same_bits(host(Yv2, vdt), wyv), N
+            assert same_bits(host(gX2, vdt), wg), N
