@@ -69,7 +69,7 @@ def parse_args():
                    help="divide every workload size by 2^shift (for quick runs)")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "single_tag", "kv", "batched", "merge_sort",
-                            "partition_variants"],
+                            "partition_variants", "orders"],
                    help="the default is the headline workload; the others measure the "
                         "remaining rows of the path (one JSON line each)")
     p.add_argument("--tile-shape", type=int, default=None,
@@ -550,6 +550,57 @@ def run_row(args):
                         "size_shift": args.shift},
              "per_merge": out, "steps": K, "warmup": Wm}
         return r
+
+    if args.workload == "orders":
+        # the same keys-only merge in several key orders: the storage type's
+        # own (int32), IEEE-754 totalOrder floats, descending; the orders
+        # other than the native one map the staged keys in shared memory
+        torch_gen = torch.Generator(device=dev).manual_seed(8)
+        rows = {}
+        for kt, dt in (("i32", torch.int32), ("i32:desc", torch.int32), ("f32", torch.float32),
+                       ("f32:desc", torch.float32), ("f64", torch.float64)):
+            m = n = ((1 << 28) >> args.shift) if dt != torch.float64 else ((1 << 27) >> args.shift)
+            vals = torch.randn(m + n, generator=torch_gen, device=dev)
+            if dt == torch.int32:
+                vals = (vals * (1 << 28)).to(torch.int32)
+            else:
+                vals = vals.to(dt)
+            desc = kt.endswith(":desc")
+            A = torch.sort(vals[:m], descending=desc, stable=True).values
+            B = torch.sort(vals[m:], descending=desc, stable=True).values
+            del vals
+            code = _lib.key_code(kt)
+            C = torch.empty(m + n, dtype=dt, device=dev)
+            ws = torch.empty(api.merge_workspace_bytes(kt, 0, m, n), dtype=torch.uint8, device=dev)
+            timer = KernelTimer(stream)
+            for k in range(Wm + K):
+                t = k >= Wm
+                if t:
+                    timer.mark()
+                _lib.check(lib.cr_merge_partition(code, 0, ptr(A), m, ptr(B), n, ptr(ws),
+                                                  ws.numel(), sp))
+                if t:
+                    timer.mark("partition")
+                _lib.check(lib.cr_merge_tiles(code, 0, ptr(A), None, m, ptr(B), None, n, ptr(C),
+                                              None, None, ptr(ws), ws.numel(), sp))
+                if t:
+                    timer.mark("tiles")
+            torch.cuda.synchronize()
+            api.workspace_status(ws)
+            tt = timer.totals()
+            b = 2 * (m + n) * A.element_size()
+            gbs = b / (tt["tiles"] / K / 1e3) / 1e9
+            rows[kt] = {"elements": m + n, "partition_ms": round(tt["partition"] / K, 4),
+                        "tiles_ms": round(tt["tiles"] / K, 4), "tiles_gbs": round(gbs, 1),
+                        "tiles_frac": round(gbs / peak, 4)}
+            del A, B, C, ws
+            torch.cuda.empty_cache()
+        tot = sum(r["partition_ms"] + r["tiles_ms"] for r in rows.values())
+        elems = sum(r["elements"] for r in rows.values())
+        return {"metric": METRIC, "unit": UNIT, "value": elems / (tot / 1e3), "ms_per_step": tot,
+                "config": {"workload": "orders", "size_shift": args.shift,
+                           "orders": list(rows)}, "per_order": rows, "steps": K, "warmup": Wm,
+                "peak_gbs": peak, "peak_source": peak_kind}
 
     if args.workload == "kv":
         Ak, Av, Bk, Bv = W.t_kv_u32_f32(device=dev, shift=args.shift)

@@ -16,12 +16,17 @@
  * and j (into B):  paper (i; j, k)  ==  ABI (k; i, j).  Always i + j == k.
  *
  * ORDER AND STABILITY.  Keys are compared with the natural order of their type
- * (signed for CR_KEY_I32/I64, unsigned for CR_KEY_U32/U64).  The merge is
- * stable: equal keys keep their order inside A and inside B, and an A element
- * precedes every equal B element (second condition of Lemma 1 is strict).
- * A and B must be ascending; this is not checked on the hot path.  Unsorted
- * input gives an unspecified result but never an out-of-bounds access
- * or a hang.
+ * (signed for CR_KEY_I32/I64, unsigned for CR_KEY_U32/U64).  CR_KEY_F32/F64
+ * keys are IEEE-754 binary32/binary64 values ordered by the standard's
+ * totalOrder predicate (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN, NaNs
+ * by payload; every bit pattern is a valid key).  OR-ing CR_KEY_DESC into a key
+ * type reverses the order (A and B descending, largest key first).  The paper
+ * states the method for any total order (Section 2); these are instances of
+ * it.  The merge is stable in every order: equal keys keep their order inside
+ * A and inside B, and an A element precedes every equal B element (second
+ * condition of Lemma 1 is strict).  A and B must be sorted in the chosen
+ * order; this is not checked on the hot path.  Unsorted input gives an
+ * unspecified result but never an out-of-bounds access or a hang.
  *
  * MEMORY.  Every pointer argument marked "device" is a device pointer owned by
  * the caller; the library allocates nothing.  Base pointers of key, payload,
@@ -67,7 +72,10 @@ typedef enum {
     CR_KEY_I32 = 0,
     CR_KEY_U32 = 1,
     CR_KEY_I64 = 2,
-    CR_KEY_U64 = 3
+    CR_KEY_U64 = 3,
+    CR_KEY_F32 = 4,   /* float bits, IEEE-754 totalOrder (see ORDER below) */
+    CR_KEY_F64 = 5,   /* double bits, IEEE-754 totalOrder */
+    CR_KEY_DESC = 256 /* flag, OR-ed into any of the above: descending order */
 } cr_key_type;
 
 /* cudaStream_t, passed as a plain pointer so this header needs no CUDA header. */

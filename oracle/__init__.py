@@ -7,8 +7,11 @@ by the CPU-baseline leg of ``bench.py`` -- nothing else.  It never imports the
 product package and shares no code with it; the product package never imports
 this one.
 
-All arithmetic lives in ``oracle.c`` (compiled with gcc into
-``oracle/_build/liboracle.so``); this module only marshals numpy arrays.
+All merge arithmetic lives in ``oracle.c`` (compiled with gcc into
+``oracle/_build/liboracle.so``); this module marshals numpy arrays and holds
+one numpy bit map, ``order_key``, which turns keys of any supported order
+(floats in IEEE-754 totalOrder, descending orders) into unsigned integers
+merged in their natural order.
 
 Notation is the paper's: output rank ``i``, co-ranks ``j`` (into A) and ``k``
 (into B), ``j + k == i``.  (The product C-ABI names the same triple
@@ -314,3 +317,44 @@ def parallel_merge(A, B, p: int):
     if rc != 0:
         raise RuntimeError("oracle could not start its threads")
     return C, counts
+
+
+# ---------------------------------------------------------------------------
+# Key orders (the paper's merge is stated for any total order, Section 2).
+# ---------------------------------------------------------------------------
+_ORDER_BITS = {"i32": 32, "u32": 32, "f32": 32, "i64": 64, "u64": 64, "f64": 64}
+
+
+def order_key(a: np.ndarray, key_type: str) -> np.ndarray:
+    """Unsigned integers whose natural order is `key_type`'s order on the
+    bit patterns of `a`:
+
+      u32, u64  the value itself;
+      i32, i64  two's complement with the sign bit flipped (offset binary);
+      f32, f64  IEEE 754-2008 totalOrder (Section 5.10): a negative value
+                (sign bit set) has every bit complemented, a non-negative one
+                has its sign bit set, so -NaN < -inf < ... < -0 < +0 < ... <
+                +inf < +NaN with NaN payloads ordered as the standard says;
+      ":desc"   appended to any of these: the complement of the above.
+    """
+    base, _, mod = key_type.partition(":")
+    bits = _ORDER_BITS[base]
+    ut = np.uint32 if bits == 32 else np.uint64
+    u = np.ascontiguousarray(a).view(ut).copy()
+    sign = ut(1) << ut(bits - 1)
+    if base[0] == "i":
+        u ^= sign
+    elif base[0] == "f":
+        neg = (u & sign) != 0
+        u = np.where(neg, ~u, u | sign).astype(ut)
+    if mod == "desc":
+        u = ~u
+    return u
+
+
+def merge_in_order(A: np.ndarray, B: np.ndarray, key_type: str):
+    """Stable merge of A and B sorted in `key_type`'s order: the plain merge
+    of their order keys, applied to the original elements.  Returns (C, src)
+    with C = concat(A, B)[src]."""
+    _, src = merge(order_key(A, key_type), order_key(B, key_type))
+    return np.concatenate([A, B])[src], src

@@ -21,22 +21,25 @@ import torch
 
 from . import _lib
 
-_DTYPE_KEY = {torch.int32: "i32", torch.int64: "i64"}
+_DTYPE_KEY = {torch.int32: "i32", torch.int64: "i64", torch.float32: "f32",
+              torch.float64: "f64"}
 for _name, _kt in (("uint32", "u32"), ("uint64", "u64")):
     if hasattr(torch, _name):
         _DTYPE_KEY[getattr(torch, _name)] = _kt
 
 
 def _key_code(t: torch.Tensor, key_type: str | None) -> int:
+    """Key type code for tensor t: from key_type ("i32", "u32", "i64", "u64",
+    "f32", "f64", optionally ":desc"), else from t's dtype (ascending)."""
     if key_type is None:
         if t.dtype not in _DTYPE_KEY:
-            raise TypeError(f"key dtype {t.dtype} is not int32/int64/uint32/uint64")
+            raise TypeError(f"key dtype {t.dtype} is not int32/int64/uint32/uint64/float32/"
+                            "float64")
         key_type = _DTYPE_KEY[t.dtype]
-    if key_type not in _lib.KEY_TYPES:
-        raise ValueError(f"key_type must be one of {sorted(_lib.KEY_TYPES)}")
-    if t.element_size() != (4 if key_type in ("i32", "u32") else 8):
-        raise TypeError(f"{key_type} keys need {4 if key_type[1:] == '32' else 8}-byte elements")
-    return _lib.KEY_TYPES[key_type]
+    code = _lib.key_code(key_type)
+    if t.element_size() != _lib.key_bytes(code):
+        raise TypeError(f"{key_type} keys need {_lib.key_bytes(code)}-byte elements")
+    return code
 
 
 def _dev(*ts: torch.Tensor) -> torch.device:
@@ -76,7 +79,7 @@ def _size(fn, *args) -> int:
 
 def tile_size(key_type: str, val_bytes: int = 0) -> int:
     """Output elements per tile used for this key type and payload width."""
-    return int(_lib.load().cr_tile_size(_lib.KEY_TYPES[key_type], int(val_bytes)))
+    return int(_lib.load().cr_tile_size(_lib.key_code(key_type), int(val_bytes)))
 
 
 # ---------------------------------------------------------------------------
@@ -116,7 +119,7 @@ def co_rank_many(A: torch.Tensor, B: torch.Tensor, ks: torch.Tensor, key_type: s
 # ---------------------------------------------------------------------------
 def merge_workspace_bytes(key_type: str, val_bytes: int, m: int, n: int) -> int:
     lib = _lib.load()
-    return _size(lib.cr_merge_workspace_size, _lib.KEY_TYPES[key_type], int(val_bytes), int(m),
+    return _size(lib.cr_merge_workspace_size, _lib.key_code(key_type), int(val_bytes), int(m),
                  int(n))
 
 
@@ -438,7 +441,7 @@ def batched_merge_kv_backward(a_off, b_off, Ak, Bk, gC, key_type: str | None = N
 # ---------------------------------------------------------------------------
 def merge_pass_workspace_bytes(key_type: str, val_bytes: int, N: int, width: int) -> int:
     lib = _lib.load()
-    return _size(lib.cr_merge_pass_workspace_size, _lib.KEY_TYPES[key_type], int(val_bytes),
+    return _size(lib.cr_merge_pass_workspace_size, _lib.key_code(key_type), int(val_bytes),
                  int(N), int(width))
 
 
@@ -493,7 +496,7 @@ def merge_pass_record_bytes(key_type: str, val_bytes: int, N: int, width: int):
     """(workspace bytes, flag words) of a recorded pass under the current tile shape."""
     lib = _lib.load()
     wsb, fw = ctypes.c_size_t(), ctypes.c_size_t()
-    _lib.check(lib.cr_merge_pass_record_size(_lib.KEY_TYPES[key_type], int(val_bytes), int(N),
+    _lib.check(lib.cr_merge_pass_record_size(_lib.key_code(key_type), int(val_bytes), int(N),
                                              int(width), ctypes.byref(wsb), ctypes.byref(fw)))
     return wsb.value, fw.value
 
@@ -503,7 +506,7 @@ def new_pass_record(key_type: str, val_bytes: int, N: int, width: int, device) -
     dev = torch.device(device)
     return PassRecord(_ws(wsb, dev),
                       torch.empty(max(fw, 4), dtype=torch.int32, device=dev),
-                      int(N), int(width), _lib.KEY_TYPES[key_type], int(val_bytes))
+                      int(N), int(width), _lib.key_code(key_type), int(val_bytes))
 
 
 def merge_pass_record(X, Xv, width: int, key_type: str | None = None, out=None,
@@ -517,8 +520,7 @@ def merge_pass_record(X, Xv, width: int, key_type: str | None = None, out=None,
     N = X.numel()
     Y, Yv = out if out is not None else (torch.empty_like(X), torch.empty_like(Xv))
     if record is None:
-        name = next(k for k, v in _lib.KEY_TYPES.items() if v == kt)
-        record = new_pass_record(name, vb, N, width, dev)
+        record = new_pass_record(kt, vb, N, width, dev)
     _lib.check(lib.cr_merge_pass_record(kt, vb, _ptr(X), _ptr(Xv), N, int(width), _ptr(Y),
                                         _ptr(Yv), _ptr(record.flags), record.flags.numel(),
                                         _ptr(record.ws), record.ws.numel(), _stream(dev)))

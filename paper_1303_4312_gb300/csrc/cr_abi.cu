@@ -37,15 +37,8 @@ cr_status cuda_fail(cudaError_t e, const char* what) {
     return fail(CR_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
-int key_bytes(int key_type) {
-    switch (key_type) {
-        case CR_KEY_I32:
-        case CR_KEY_U32: return 4;
-        case CR_KEY_I64:
-        case CR_KEY_U64: return 8;
-        default: return 0;
-    }
-}
+int key_bytes(int key_type) { return cr::key_type_bytes(key_type); }
+int key_order(int key_type) { return cr::key_type_order(key_type); }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -111,13 +104,7 @@ cr_status check_ws(const void* ws, size_t have, size_t need) {
 
 template <class F>
 cudaError_t by_key(int key_type, F&& f) {
-    switch (key_type) {
-        case CR_KEY_I32: return f(KeyOps<int32_t>{});
-        case CR_KEY_U32: return f(KeyOps<uint32_t>{});
-        case CR_KEY_I64: return f(KeyOps<int64_t>{});
-        case CR_KEY_U64: return f(KeyOps<uint64_t>{});
-        default: return cudaErrorInvalidValue;
-    }
+    return cr::with_key_ops(key_type, static_cast<F&&>(f));
 }
 
 #define CR_TRY(expr)                       \
@@ -193,7 +180,7 @@ cr_status launch_partition(int shape, int key_type, const void* Ak, int64_t m, c
     const int64_t ntiles = single_tiles(shape, m, n, &tile);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     cudaError_t e = by_key(key_type, [&](auto ops) {
-        return ops.partition_single(Ak, m, Bk, n, tile, ntiles, ws, st);
+        return ops.partition_single(Ak, m, Bk, n, tile, ntiles, ws, key_order(key_type), st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "partition launch");
     return CR_OK;
@@ -205,6 +192,7 @@ cr_status launch_tiles(int shape, int key_type, int vb, const void* Ak, const vo
     const int64_t ntiles = single_tiles(shape, m, n, nullptr);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     cr::MergeArgs a{};
+    a.order = key_order(key_type);
     a.ak = Ak;
     a.bk = Bk;
     a.av = Av;
@@ -230,6 +218,7 @@ cr_status launch_tiles_backward(int shape, int key_type, int vb, const void* Ak,
     const int64_t ntiles = single_tiles(shape, m, n, nullptr);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     cr::MergeArgs a{};
+    a.order = key_order(key_type);
     a.ak = Ak;
     a.bk = Bk;
     a.gc_in = gC;
@@ -357,7 +346,7 @@ cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int6
         return fail(CR_EALIGN, "result pointer is not 8-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = by_key(key_type,
-                           [&](auto ops) { return ops.co_rank_one(A, m, B, n, k, d_ij, st); });
+                           [&](auto ops) { return ops.co_rank_one(A, m, B, n, k, d_ij, key_order(key_type), st); });
     if (e != cudaSuccess) return cuda_fail(e, "co_rank launch");
     return ok();
 }
@@ -377,7 +366,7 @@ cr_status cr_co_rank_many(int key_type, const void* A, int64_t m, const void* B,
     CR_TRY(check_no_alias(outs, 2, ins, 3));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = by_key(key_type, [&](auto ops) {
-        return ops.co_rank_many(A, m, B, n, d_k, cnt, d_i, d_j, st);
+        return ops.co_rank_many(A, m, B, n, d_k, cnt, d_i, d_j, key_order(key_type), st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "co_rank_many launch");
     return ok();
@@ -455,7 +444,7 @@ cr_status cr_merge_partition_alg2(int key_type, int val_bytes, const void* A, in
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = by_key(key_type, [&](auto ops) {
-        return ops.partition_single_free(A, m, B, n, tile, ntiles, ws, st);
+        return ops.partition_single_free(A, m, B, n, tile, ntiles, ws, key_order(key_type), st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "partition launch");
     return ok();
@@ -532,6 +521,7 @@ cr_status batched_common(bool backward, int key_type, int val_bytes, int64_t nse
                                                  size_t(max_tiles) * kRecBytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cr::MergeArgs a{};
+    a.order = key_order(key_type);
     a.ak = Ak;
     a.bk = Bk;
     a.av = Av;
@@ -546,7 +536,7 @@ cr_status batched_common(bool backward, int key_type, int val_bytes, int64_t nse
     a.ws = ws;
     cudaError_t e = by_key(key_type, [&](auto ops) {
         cudaError_t r = ops.partition_batched(Ak, Bk, a_off, b_off, nseg, a_total, b_total, tile,
-                                              max_tiles, ws, prefix, st);
+                                              max_tiles, ws, prefix, key_order(key_type), st);
         if (r != cudaSuccess) return r;
         return backward ? ops.merge_bwd(shape, vb, a, max_tiles, st)
                         : ops.merge_fwd(shape, vb, false, a, max_tiles, st);
@@ -611,6 +601,7 @@ cr_status pass_common(Pass mode, int key_type, int val_bytes, const void* X, con
         return ok();
     }
     cr::MergeArgs a{};
+    a.order = key_order(key_type);
     a.ak = X;
     a.bk = X;
     a.av = Xv;
@@ -626,7 +617,7 @@ cr_status pass_common(Pass mode, int key_type, int val_bytes, const void* X, con
     a.ws = ws;
     cudaError_t e = by_key(key_type, [&](auto ops) {
         int64_t nt = 0;
-        cudaError_t r = ops.partition_pass(X, N, width, tile, ws, &nt, st);
+        cudaError_t r = ops.partition_pass(X, N, width, tile, ws, &nt, key_order(key_type), st);
         if (r != cudaSuccess) return r;
         switch (mode) {
             case Pass::kBackward: return ops.merge_bwd(shape, vb, a, nt, st);
@@ -735,7 +726,7 @@ cr_status sort_runs_common(int key_type, int val_bytes, const void* X, const voi
     if (N == 0) return ok();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = by_key(key_type, [&](auto ops) {
-        return ops.sort_runs(vb, X, Xv, N, Y, Yv, perm, st);
+        return ops.sort_runs(vb, X, Xv, N, Y, Yv, perm, key_order(key_type), st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "run sort launch");
     return ok();
@@ -785,7 +776,7 @@ cr_status cr_sort_runs_backward(int key_type, int val_bytes, const void* X, int6
     if (N == 0) return ok();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = by_key(key_type, [&](auto ops) {
-        return ops.sort_runs_backward(val_bytes, X, N, gY, gX, st);
+        return ops.sort_runs_backward(val_bytes, X, N, gY, gX, key_order(key_type), st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "run sort backward launch");
     return ok();

@@ -55,6 +55,73 @@ struct MergeArgs {
     int64_t c_total;     // length of the C array
     int64_t tag_b;       // tag of B[0]
     void* ws;            // workspace: header + tile records
+    int32_t order;       // key order (order_key): 0 = the key type's own
+};
+
+// ---------------------------------------------------------------------------
+// Key orders.  The merge compares keys with `<` of their storage type; other
+// orders are reached through an order-preserving bijection applied to every
+// key before it is compared (and undone on the keys written out):
+//   bit 1: IEEE-754 totalOrder of a float stored in the signed integer of
+//          its width (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN):
+//          negative values have their magnitude bits flipped, after which
+//          the signed integer order is the float total order;
+//   bit 0: descending: the bitwise complement reverses any integer order.
+// Both steps are involutions; order 0 is the identity.
+// ---------------------------------------------------------------------------
+template <class K>
+__device__ __forceinline__ K order_flip_float(K x) {
+    using S = typename std::make_signed<K>::type;
+    const S s = S(x);
+    constexpr S mag = S(~(typename std::make_unsigned<K>::type(1)
+                          << (8 * sizeof(K) - 1)));     // all bits but the sign
+    return K(s ^ ((s >> (8 * int(sizeof(K)) - 1)) & mag));
+}
+
+template <class K>
+__device__ __forceinline__ K order_key(K x, int order) {
+    if (order & 2) x = order_flip_float(x);
+    if (order & 1) x = K(~x);
+    return x;
+}
+
+template <class K>
+__device__ __forceinline__ K order_key_inverse(K x, int order) {
+    if (order & 1) x = K(~x);
+    if (order & 2) x = order_flip_float(x);
+    return x;
+}
+
+// order_key / order_key_inverse without branches, for hot loops: with
+// F = the magnitude bits when bit 1 of the order is set (else 0) and M = all
+// ones when bit 0 is set (else 0),  map(x) = x ^ ((sign(x) & F) ^ M), where
+// sign(x) is x's sign bit replicated; the inverse undoes M first.
+template <class K>
+struct OrderMap {
+    using S = typename std::make_signed<K>::type;
+    using U = typename std::make_unsigned<K>::type;
+    static constexpr int SH = 8 * int(sizeof(K)) - 1;
+    K flt, neg;
+    __device__ __forceinline__ explicit OrderMap(int order)
+        : flt((order & 2) ? K(U(~U(0)) >> 1) : K(0)), neg((order & 1) ? K(~U(0)) : K(0)) {}
+    __device__ __forceinline__ K operator()(K x) const {
+        return K(x ^ ((K(S(x) >> SH) & flt) ^ neg));
+    }
+    __device__ __forceinline__ K inverse(K u) const {
+        const K v = K(u ^ neg);
+        return K(v ^ (K(S(v) >> SH) & flt));
+    }
+};
+
+// Read-only view of a key array in a given order: v[i] is key i mapped by
+// order_key, so searches written with `<` on v[i] follow that order.
+template <class K>
+struct KeyView {
+    using key_type = K;
+    const K* p;
+    int order;
+    __device__ __forceinline__ K operator[](int64_t i) const { return order_key(p[i], order); }
+    __device__ __forceinline__ KeyView operator+(int64_t off) const { return {p + off, order}; }
 };
 
 __host__ __device__ inline TileRec* ws_recs(void* ws) {

@@ -45,7 +45,7 @@ cudaError_t launch_shape(Kern kern, int threads, size_t smem, LaunchShape* cache
     return cudaSuccess;
 }
 
-template <class K, int VB, bool TAG, bool BWD, int S, bool REC>
+template <class K, int VB, bool TAG, bool BWD, int S, bool REC, bool ORD>
 cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
     constexpr int KS = int(sizeof(K));
     if constexpr (!Stages<KS, VB, TAG, BWD, S>::FITS) {
@@ -57,7 +57,7 @@ cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream
         constexpr int NS = Stages<KS, VB, TAG, BWD, S>::NS;
         constexpr int MINB = Stages<KS, VB, TAG, BWD, S>::MINB;
         using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD, REC>;
-        auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, ILP, NS, MINB, BWD, REC>;
+        auto kern = merge_tiles_kernel<K, VB, TAG, NT, IPT, ILP, NS, MINB, BWD, REC, ORD>;
         static LaunchShape cache[kMaxDevices];
         static std::once_flag once[kMaxDevices];
         LaunchShape sh;
@@ -72,48 +72,89 @@ cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream
     }
 }
 
-template <class K, int VB, bool TAG, bool BWD, bool REC = false>
+template <class K, int VB, bool TAG, bool BWD, bool REC = false, bool ORD = false>
 cudaError_t launch_merge(int shape, const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
     static_assert(kNumShapes == 6, "dispatch below lists every shape");
     switch (shape) {
-        case 0: return launch_merge_shape<K, VB, TAG, BWD, 0, REC>(a, max_tiles, st);
-        case 1: return launch_merge_shape<K, VB, TAG, BWD, 1, REC>(a, max_tiles, st);
-        case 2: return launch_merge_shape<K, VB, TAG, BWD, 2, REC>(a, max_tiles, st);
-        case 3: return launch_merge_shape<K, VB, TAG, BWD, 3, REC>(a, max_tiles, st);
-        case 4: return launch_merge_shape<K, VB, TAG, BWD, 4, REC>(a, max_tiles, st);
-        case 5: return launch_merge_shape<K, VB, TAG, BWD, 5, REC>(a, max_tiles, st);
+        case 0: return launch_merge_shape<K, VB, TAG, BWD, 0, REC, ORD>(a, max_tiles, st);
+        case 1: return launch_merge_shape<K, VB, TAG, BWD, 1, REC, ORD>(a, max_tiles, st);
+        case 2: return launch_merge_shape<K, VB, TAG, BWD, 2, REC, ORD>(a, max_tiles, st);
+        case 3: return launch_merge_shape<K, VB, TAG, BWD, 3, REC, ORD>(a, max_tiles, st);
+        case 4: return launch_merge_shape<K, VB, TAG, BWD, 4, REC, ORD>(a, max_tiles, st);
+        case 5: return launch_merge_shape<K, VB, TAG, BWD, 5, REC, ORD>(a, max_tiles, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// The forward tile merges of one key type, for its own order (ORD false) or
+// another one (ORD true; a.order != 0).
+template <class K, bool ORD>
+cudaError_t merge_fwd_impl(int shape, int vb, bool tag, const MergeArgs& a, int64_t max_tiles,
+                           cudaStream_t st) {
+    switch (vb * 2 + (tag ? 1 : 0)) {
+        case 0: return launch_merge<K, 0, false, false, false, ORD>(shape, a, max_tiles, st);
+        case 1: return launch_merge<K, 0, true, false, false, ORD>(shape, a, max_tiles, st);
+        case 8: return launch_merge<K, 4, false, false, false, ORD>(shape, a, max_tiles, st);
+        case 9: return launch_merge<K, 4, true, false, false, ORD>(shape, a, max_tiles, st);
+        case 16: return launch_merge<K, 8, false, false, false, ORD>(shape, a, max_tiles, st);
+        case 17: return launch_merge<K, 8, true, false, false, ORD>(shape, a, max_tiles, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class K, bool ORD>
+cudaError_t merge_fwd_rec_impl(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                               cudaStream_t st) {
+    if (vb == 4) return launch_merge<K, 4, false, false, true, ORD>(shape, a, max_tiles, st);
+    if (vb == 8) return launch_merge<K, 8, false, false, true, ORD>(shape, a, max_tiles, st);
+    return cudaErrorInvalidValue;
+}
+
+template <class K, bool ORD>
+cudaError_t merge_bwd_impl(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                           cudaStream_t st) {
+    if (vb == 4) return launch_merge<K, 4, false, true, false, ORD>(shape, a, max_tiles, st);
+    if (vb == 8) return launch_merge<K, 8, false, true, false, ORD>(shape, a, max_tiles, st);
+    return cudaErrorInvalidValue;
 }
 
 template <class K>
 cudaError_t KeyOps<K>::merge_fwd(int shape, int vb, bool tag, const MergeArgs& a,
                                  int64_t max_tiles, cudaStream_t st) {
-    switch (vb * 2 + (tag ? 1 : 0)) {
-        case 0: return launch_merge<K, 0, false, false>(shape, a, max_tiles, st);
-        case 1: return launch_merge<K, 0, true, false>(shape, a, max_tiles, st);
-        case 8: return launch_merge<K, 4, false, false>(shape, a, max_tiles, st);
-        case 9: return launch_merge<K, 4, true, false>(shape, a, max_tiles, st);
-        case 16: return launch_merge<K, 8, false, false>(shape, a, max_tiles, st);
-        case 17: return launch_merge<K, 8, true, false>(shape, a, max_tiles, st);
-        default: return cudaErrorInvalidValue;
-    }
+    if (a.order != 0) return merge_fwd_ord(shape, vb, tag, a, max_tiles, st);
+    return merge_fwd_impl<K, false>(shape, vb, tag, a, max_tiles, st);
 }
 
 template <class K>
 cudaError_t KeyOps<K>::merge_fwd_rec(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                      cudaStream_t st) {
-    if (vb == 4) return launch_merge<K, 4, false, false, true>(shape, a, max_tiles, st);
-    if (vb == 8) return launch_merge<K, 8, false, false, true>(shape, a, max_tiles, st);
-    return cudaErrorInvalidValue;
+    if (a.order != 0) return merge_fwd_rec_ord(shape, vb, a, max_tiles, st);
+    return merge_fwd_rec_impl<K, false>(shape, vb, a, max_tiles, st);
 }
 
 template <class K>
 cudaError_t KeyOps<K>::merge_bwd(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                  cudaStream_t st) {
-    if (vb == 4) return launch_merge<K, 4, false, true>(shape, a, max_tiles, st);
-    if (vb == 8) return launch_merge<K, 8, false, true>(shape, a, max_tiles, st);
-    return cudaErrorInvalidValue;
+    if (a.order != 0) return merge_bwd_ord(shape, vb, a, max_tiles, st);
+    return merge_bwd_impl<K, false>(shape, vb, a, max_tiles, st);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_fwd_ord(int shape, int vb, bool tag, const MergeArgs& a,
+                                     int64_t max_tiles, cudaStream_t st) {
+    return merge_fwd_impl<K, true>(shape, vb, tag, a, max_tiles, st);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_fwd_rec_ord(int shape, int vb, const MergeArgs& a,
+                                         int64_t max_tiles, cudaStream_t st) {
+    return merge_fwd_rec_impl<K, true>(shape, vb, a, max_tiles, st);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_bwd_ord(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                     cudaStream_t st) {
+    return merge_bwd_impl<K, true>(shape, vb, a, max_tiles, st);
 }
 
 static inline unsigned blocks_for(int64_t n, int threads) {
@@ -122,35 +163,37 @@ static inline unsigned blocks_for(int64_t n, int threads) {
 
 template <class K>
 cudaError_t KeyOps<K>::partition_single(const void* A, int64_t m, const void* B, int64_t n,
-                                        int64_t tile, int64_t ntiles, void* ws, cudaStream_t st) {
+                                        int64_t tile, int64_t ntiles, void* ws, int order,
+                                        cudaStream_t st) {
     // 256 threads search 256 consecutive boundaries = 255 tiles per block
     const unsigned g = unsigned(((ntiles > 0 ? ntiles : 1) + 254) / 255);
     partition_single_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(A), m,
-                                                   static_cast<const K*>(B), n, tile, ntiles, ws);
+                                                   static_cast<const K*>(B), n, tile, ntiles, ws,
+                                                   order);
     return cudaGetLastError();
 }
 
 template <class K>
 cudaError_t KeyOps<K>::partition_single_free(const void* A, int64_t m, const void* B, int64_t n,
-                                             int64_t tile, int64_t ntiles, void* ws,
+                                             int64_t tile, int64_t ntiles, void* ws, int order,
                                              cudaStream_t st) {
     const unsigned g = blocks_for(ntiles > 0 ? ntiles : 1, 256);
     partition_single_free_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(A), m,
                                                         static_cast<const K*>(B), n, tile, ntiles,
-                                                        ws);
+                                                        ws, order);
     return cudaGetLastError();
 }
 
 template <class K>
 cudaError_t KeyOps<K>::partition_pass(const void* X, int64_t N, int64_t w, int64_t tile,
-                                      void* ws, int64_t* ntiles_out, cudaStream_t st) {
+                                      void* ws, int64_t* ntiles_out, int order, cudaStream_t st) {
     int64_t tpp = 1, npairs = 0;
     const int64_t ntiles = pass_tiles(N, w, tile, &tpp, &npairs);
     if (ntiles_out) *ntiles_out = ntiles;
     // 256 threads co-rank 256 consecutive tile starts = 255 tiles per block
     const unsigned g = unsigned(((ntiles > 0 ? ntiles : 1) + 254) / 255);
     partition_pass_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(X), N, w, tile, tpp,
-                                                 npairs, ntiles, ws);
+                                                 npairs, ntiles, ws, order);
     return cudaGetLastError();
 }
 
@@ -158,19 +201,21 @@ template <class K>
 cudaError_t KeyOps<K>::partition_batched(const void* A, const void* B, const int64_t* a_off,
                                          const int64_t* b_off, int64_t nseg, int64_t a_total,
                                          int64_t b_total, int64_t tile, int64_t max_tiles,
-                                         void* ws, int64_t* prefix, cudaStream_t st) {
+                                         void* ws, int64_t* prefix, int order, cudaStream_t st) {
     segment_scan_kernel<<<1, 1024, 0, st>>>(a_off, b_off, nseg, a_total, b_total, tile, ws,
                                             prefix);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || max_tiles <= 0) return e;
     partition_batched_kernel<K><<<blocks_for(max_tiles, 256), 256, 0, st>>>(
-        static_cast<const K*>(A), static_cast<const K*>(B), a_off, b_off, nseg, tile, prefix, ws);
+        static_cast<const K*>(A), static_cast<const K*>(B), a_off, b_off, nseg, tile, prefix, ws,
+        order);
     return cudaGetLastError();
 }
 
 template <class K, int VB, int MODE>
 cudaError_t launch_sort_runs(const void* X, const void* Xv, int64_t N, void* Y, void* Yv,
-                             uint16_t* perm, const void* gY, void* gX, cudaStream_t st) {
+                             uint16_t* perm, const void* gY, void* gX, int order,
+                             cudaStream_t st) {
     using L = SortLayout<K, VB, MODE, kSortNT, kSortIPT>;
     auto kern = sort_runs_kernel<K, VB, MODE, kSortNT, kSortIPT>;
     static LaunchShape cache[kMaxDevices];
@@ -181,47 +226,56 @@ cudaError_t launch_sort_runs(const void* X, const void* Xv, int64_t N, void* Y, 
     if (N <= 0) return cudaSuccess;
     const unsigned grid = unsigned((N + kSortRun - 1) / kSortRun);
     kern<<<grid, kSortNT, L::TOTAL, st>>>(static_cast<const K*>(X), Xv, N, static_cast<K*>(Y), Yv,
-                                          perm, gY, gX);
+                                          perm, gY, gX, order);
     return cudaGetLastError();
 }
 
 template <class K>
 cudaError_t KeyOps<K>::sort_runs(int vb, const void* X, const void* Xv, int64_t N, void* Y,
-                                 void* Yv, uint16_t* perm, cudaStream_t st) {
+                                 void* Yv, uint16_t* perm, int order, cudaStream_t st) {
     if (perm != nullptr) {
-        if (vb == 4) return launch_sort_runs<K, 4, 1>(X, Xv, N, Y, Yv, perm, nullptr, nullptr, st);
-        if (vb == 8) return launch_sort_runs<K, 8, 1>(X, Xv, N, Y, Yv, perm, nullptr, nullptr, st);
+        if (vb == 4)
+            return launch_sort_runs<K, 4, 1>(X, Xv, N, Y, Yv, perm, nullptr, nullptr, order, st);
+        if (vb == 8)
+            return launch_sort_runs<K, 8, 1>(X, Xv, N, Y, Yv, perm, nullptr, nullptr, order, st);
         return cudaErrorInvalidValue;
     }
-    if (vb == 0) return launch_sort_runs<K, 0, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, st);
-    if (vb == 4) return launch_sort_runs<K, 4, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, st);
-    if (vb == 8) return launch_sort_runs<K, 8, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, st);
+    if (vb == 0)
+        return launch_sort_runs<K, 0, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, order, st);
+    if (vb == 4)
+        return launch_sort_runs<K, 4, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, order, st);
+    if (vb == 8)
+        return launch_sort_runs<K, 8, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, order, st);
     return cudaErrorInvalidValue;
 }
 
 template <class K>
 cudaError_t KeyOps<K>::sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
-                                          void* gX, cudaStream_t st) {
-    if (vb == 4) return launch_sort_runs<K, 4, 2>(X, nullptr, N, nullptr, nullptr, nullptr, gY, gX, st);
-    if (vb == 8) return launch_sort_runs<K, 8, 2>(X, nullptr, N, nullptr, nullptr, nullptr, gY, gX, st);
+                                          void* gX, int order, cudaStream_t st) {
+    if (vb == 4)
+        return launch_sort_runs<K, 4, 2>(X, nullptr, N, nullptr, nullptr, nullptr, gY, gX, order,
+                                         st);
+    if (vb == 8)
+        return launch_sort_runs<K, 8, 2>(X, nullptr, N, nullptr, nullptr, nullptr, gY, gX, order,
+                                         st);
     return cudaErrorInvalidValue;
 }
 
 template <class K>
 cudaError_t KeyOps<K>::co_rank_many(const void* A, int64_t m, const void* B, int64_t n,
                                     const int64_t* ranks, int64_t cnt, int64_t* oi, int64_t* oj,
-                                    cudaStream_t st) {
+                                    int order, cudaStream_t st) {
     if (cnt <= 0) return cudaSuccess;
     co_rank_many_kernel<K><<<blocks_for(cnt, 256), 256, 0, st>>>(
-        static_cast<const K*>(A), m, static_cast<const K*>(B), n, ranks, cnt, oi, oj);
+        static_cast<const K*>(A), m, static_cast<const K*>(B), n, ranks, cnt, oi, oj, order);
     return cudaGetLastError();
 }
 
 template <class K>
 cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int64_t n, int64_t r,
-                                   int64_t* out, cudaStream_t st) {
+                                   int64_t* out, int order, cudaStream_t st) {
     co_rank_one_kernel<K><<<1, 1, 0, st>>>(static_cast<const K*>(A), m,
-                                           static_cast<const K*>(B), n, r, out);
+                                           static_cast<const K*>(B), n, r, out, order);
     return cudaGetLastError();
 }
 
@@ -232,6 +286,13 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
 #define CR_INSTANTIATE_FORWARD(K)                                                              \
     template cudaError_t cr::KeyOps<K>::merge_fwd(int, int, bool, const cr::MergeArgs&,        \
                                                   int64_t, cudaStream_t);
+#define CR_INSTANTIATE_ORDER(K)                                                                \
+    template cudaError_t cr::KeyOps<K>::merge_fwd_ord(int, int, bool, const cr::MergeArgs&,    \
+                                                      int64_t, cudaStream_t);                  \
+    template cudaError_t cr::KeyOps<K>::merge_fwd_rec_ord(int, int, const cr::MergeArgs&,      \
+                                                          int64_t, cudaStream_t);              \
+    template cudaError_t cr::KeyOps<K>::merge_bwd_ord(int, int, const cr::MergeArgs&, int64_t, \
+                                                      cudaStream_t);
 #define CR_INSTANTIATE_RECORD(K)                                                               \
     template cudaError_t cr::KeyOps<K>::merge_fwd_rec(int, int, const cr::MergeArgs&, int64_t, \
                                                       cudaStream_t);
@@ -240,22 +301,23 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
                                                   cudaStream_t);                               \
     template cudaError_t cr::KeyOps<K>::partition_single(const void*, int64_t, const void*,    \
                                                          int64_t, int64_t, int64_t, void*,     \
-                                                         cudaStream_t);                        \
-    template cudaError_t cr::KeyOps<K>::partition_single_free(const void*, int64_t, const void*,\
-                                                              int64_t, int64_t, int64_t, void*, \
-                                                              cudaStream_t);                    \
+                                                         int, cudaStream_t);                   \
+    template cudaError_t cr::KeyOps<K>::partition_single_free(                                 \
+        const void*, int64_t, const void*, int64_t, int64_t, int64_t, void*, int,              \
+        cudaStream_t);                                                                         \
     template cudaError_t cr::KeyOps<K>::partition_pass(const void*, int64_t, int64_t, int64_t, \
-                                                       void*, int64_t*, cudaStream_t);         \
+                                                       void*, int64_t*, int, cudaStream_t);    \
     template cudaError_t cr::KeyOps<K>::partition_batched(                                     \
         const void*, const void*, const int64_t*, const int64_t*, int64_t, int64_t, int64_t,   \
-        int64_t, int64_t, void*, int64_t*, cudaStream_t);                                      \
+        int64_t, int64_t, void*, int64_t*, int, cudaStream_t);                                 \
     template cudaError_t cr::KeyOps<K>::co_rank_many(const void*, int64_t, const void*,        \
                                                      int64_t, const int64_t*, int64_t,         \
-                                                     int64_t*, int64_t*, cudaStream_t);        \
+                                                     int64_t*, int64_t*, int, cudaStream_t);   \
     template cudaError_t cr::KeyOps<K>::co_rank_one(const void*, int64_t, const void*,         \
-                                                    int64_t, int64_t, int64_t*, cudaStream_t); \
+                                                    int64_t, int64_t, int64_t*, int,           \
+                                                    cudaStream_t);                             \
     template cudaError_t cr::KeyOps<K>::sort_runs(int, const void*, const void*, int64_t,      \
-                                                  void*, void*, uint16_t*, cudaStream_t);      \
+                                                  void*, void*, uint16_t*, int, cudaStream_t); \
     template cudaError_t cr::KeyOps<K>::sort_runs_backward(int, const void*, int64_t,          \
-                                                           const void*, void*, cudaStream_t);
-
+                                                           const void*, void*, int,            \
+                                                           cudaStream_t);

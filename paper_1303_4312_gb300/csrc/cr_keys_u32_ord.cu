@@ -1,0 +1,5 @@
+// Tile-merge kernels (forward, recording forward, backward) for uint32_t keys in
+// another order than their own (descending; float total order).
+#include "cr_keyops_impl.cuh"
+
+CR_INSTANTIATE_ORDER(uint32_t)

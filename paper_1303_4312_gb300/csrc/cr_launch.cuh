@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "../../include/corank.h"
 #include "cr_device.cuh"
 
 namespace cr {
@@ -97,30 +98,40 @@ struct KeyOps {
     // Payload backward (vb in {4,8}).
     static cudaError_t merge_bwd(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                  cudaStream_t st);
+    // The same three for keys in another order than their storage type's
+    // (a.order != 0); the calls above forward to these.
+    static cudaError_t merge_fwd_ord(int shape, int vb, bool tag, const MergeArgs& a,
+                                     int64_t max_tiles, cudaStream_t st);
+    static cudaError_t merge_fwd_rec_ord(int shape, int vb, const MergeArgs& a,
+                                         int64_t max_tiles, cudaStream_t st);
+    static cudaError_t merge_bwd_ord(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                     cudaStream_t st);
+    // order: key order of the call (order_key in cr_device.cuh).
     static cudaError_t partition_single(const void* A, int64_t m, const void* B, int64_t n,
-                                        int64_t tile, int64_t ntiles, void* ws, cudaStream_t st);
+                                        int64_t tile, int64_t ntiles, void* ws, int order,
+                                        cudaStream_t st);
     // Same table, every tile co-ranking both of its ends (Algorithm 1).
     static cudaError_t partition_single_free(const void* A, int64_t m, const void* B, int64_t n,
-                                             int64_t tile, int64_t ntiles, void* ws,
+                                             int64_t tile, int64_t ntiles, void* ws, int order,
                                              cudaStream_t st);
     static cudaError_t partition_pass(const void* X, int64_t N, int64_t w, int64_t tile,
-                                      void* ws, int64_t* ntiles_out, cudaStream_t st);
+                                      void* ws, int64_t* ntiles_out, int order, cudaStream_t st);
     static cudaError_t partition_batched(const void* A, const void* B, const int64_t* a_off,
                                          const int64_t* b_off, int64_t nseg, int64_t a_total,
                                          int64_t b_total, int64_t tile, int64_t max_tiles,
-                                         void* ws, int64_t* prefix, cudaStream_t st);
+                                         void* ws, int64_t* prefix, int order, cudaStream_t st);
     static cudaError_t co_rank_many(const void* A, int64_t m, const void* B, int64_t n,
                                     const int64_t* ranks, int64_t cnt, int64_t* oi, int64_t* oj,
-                                    cudaStream_t st);
+                                    int order, cudaStream_t st);
     static cudaError_t co_rank_one(const void* A, int64_t m, const void* B, int64_t n, int64_t r,
-                                   int64_t* out, cudaStream_t st);
+                                   int64_t* out, int order, cudaStream_t st);
     // Run formation: stably sort runs of kSortRun elements (vb 0, 4, 8);
     // with perm (vb 4, 8) also write each run's permutation; backward
     // (vb 4, 8): gX from gY through the same in-run permutation, replayed.
     static cudaError_t sort_runs(int vb, const void* X, const void* Xv, int64_t N, void* Y,
-                                 void* Yv, uint16_t* perm, cudaStream_t st);
+                                 void* Yv, uint16_t* perm, int order, cudaStream_t st);
     static cudaError_t sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
-                                          void* gX, cudaStream_t st);
+                                          void* gX, int order, cudaStream_t st);
 };
 
 // Backward of a recorded merge pass (vb in {4,8}) over N elements with run
@@ -135,6 +146,43 @@ cudaError_t route_recorded(int vb, void* ws, const uint32_t* flags, int64_t flag
 // kSortRun elements, gX[base + perm[base + x]] = gY[base + x].
 cudaError_t sort_route_recorded(int vb, int64_t N, const uint16_t* perm, const void* gY, void* gX,
                                 cudaStream_t st);
+
+// C-ABI key types: storage width, storage type and order (order_key).
+// F32/F64 are stored and compared as the signed integer of their width after
+// the float total-order map; CR_KEY_DESC adds the complement.
+inline int key_base(int key_type) { return key_type & ~int(CR_KEY_DESC); }
+
+inline int key_type_bytes(int key_type) {
+    if (key_type < 0 || (key_type & ~(int(CR_KEY_DESC) | 0xFF)) != 0) return 0;
+    switch (key_base(key_type)) {
+        case CR_KEY_I32:
+        case CR_KEY_U32:
+        case CR_KEY_F32: return 4;
+        case CR_KEY_I64:
+        case CR_KEY_U64:
+        case CR_KEY_F64: return 8;
+        default: return 0;
+    }
+}
+
+inline int key_type_order(int key_type) {
+    const int b = key_base(key_type);
+    return ((b == CR_KEY_F32 || b == CR_KEY_F64) ? 2 : 0) | ((key_type & CR_KEY_DESC) ? 1 : 0);
+}
+
+template <class F>
+cudaError_t with_key_ops(int key_type, F&& f) {
+    if (key_type_bytes(key_type) == 0) return cudaErrorInvalidValue;
+    switch (key_base(key_type)) {
+        case CR_KEY_I32:
+        case CR_KEY_F32: return f(KeyOps<int32_t>{});
+        case CR_KEY_U32: return f(KeyOps<uint32_t>{});
+        case CR_KEY_I64:
+        case CR_KEY_F64: return f(KeyOps<int64_t>{});
+        case CR_KEY_U64: return f(KeyOps<uint64_t>{});
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // Tiles of a merge pass over N elements with run width w.
 inline int64_t pass_tiles(int64_t N, int64_t w, int64_t tile, int64_t* tpp_out,

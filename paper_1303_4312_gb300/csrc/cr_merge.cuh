@@ -164,9 +164,17 @@ __device__ __forceinline__ void store_edges(T* gbase, const T* buf, int64_t g0, 
 // LOG fixed steps of decreasing size, so all threads of a warp run the same
 // instruction stream.  Loads are issued only for in-range probes.  ILP
 // independent diagonals are searched in lock step (their loads overlap).
-template <int LOG, int ILP, class K>
+struct KeyIdentity {
+    template <class K>
+    __device__ __forceinline__ K operator()(K x) const { return x; }
+};
+
+// `key` maps every key read before it is compared (the call's key order;
+// the identity for the storage type's own order).
+template <int LOG, int ILP, class K, class KeyMap = KeyIdentity>
 __device__ __forceinline__ void split_in_tile(const K* sA, int alen, const K* sB, int blen,
-                                              const int (&d)[ILP], int (&pos)[ILP]) {
+                                              const int (&d)[ILP], int (&pos)[ILP],
+                                              KeyMap key = KeyMap()) {
     int hi[ILP];
 #pragma unroll
     for (int c = 0; c < ILP; ++c) {
@@ -178,7 +186,7 @@ __device__ __forceinline__ void split_in_tile(const K* sA, int alen, const K* sB
 #pragma unroll
         for (int c = 0; c < ILP; ++c) {
             const int np = pos[c] + step;
-            if (np <= hi[c] && !(sB[d[c] - np] < sA[np - 1])) pos[c] = np;
+            if (np <= hi[c] && !(key(sB[d[c] - np]) < key(sA[np - 1]))) pos[c] = np;
         }
     }
 }
@@ -197,8 +205,13 @@ template <int NT> constexpr int merge_block_threads() { return NT + 64; }
 // bit x % 32 of word x / 32 of the tile's WPT flag words, stored at
 // p.flags + t * WPT for tile t (the backward then routes gradients from
 // these bits and the tile table without reading keys).
+//
+// ORD: keys in another order than their storage type's (p.order, order_key):
+// every key read from shared memory is mapped before it is compared and the
+// output keys are mapped back.  With ORD false the code is that of the
+// storage type's own order.
 template <class K, int VB, bool TAG, int NT, int IPT, int ILP, int NS, int MINB, bool BWD,
-          bool REC>
+          bool REC, bool ORD>
 __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeArgs p) {
     using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD, REC>;
     using V = typename VBits<VB>::T;
@@ -391,6 +404,8 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
     }
 
     // ---------------------------------------------------------------- consumers
+    const OrderMap<K> om(ORD ? p.order : 0);
+    const auto km = [om](K x) { return ORD ? om(x) : x; };
     // Thread tid merges ILP chains; chain c starts at diagonal (c*NT + tid)*IPT
     // and the chains run interleaved, so each thread has ILP independent
     // dependency chains of shared-memory loads in flight.
@@ -418,15 +433,15 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             d[c] = min((c * NT + tid) * IPT, len);
             cnt[c] = min(IPT, len - d[c]);
         }
-        split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d, j);
+        split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d, j, km);
 #pragma unroll
         for (int c = 0; c < ILP; ++c) {
             k[c] = d[c] - j[c];
             a[c] = K(0);
             b[c] = K(0);
             if (cnt[c] > 0) {
-                a[c] = sA[j[c]];   // may be one past A's window: never taken then
-                b[c] = sB[k[c]];
+                a[c] = km(sA[j[c]]);   // may be one past A's window: never taken then
+                b[c] = km(sB[k[c]]);
             }
             fast = fast && cnt[c] == IPT && j[c] + IPT <= alen && k[c] + IPT <= blen;
         }
@@ -458,7 +473,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                 if constexpr (REC) obit[c] |= (takeA ? 0u : 1u) << q;
                 j[c] += takeA ? 1 : 0;
                 k[c] += takeA ? 0 : 1;
-                const K nx = sk[takeA ? ao + j[c] : bo + k[c]];   // one load from either window
+                const K nx = km(sk[takeA ? ao + j[c] : bo + k[c]]);   // one load from either window
                 a[c] = takeA ? nx : a[c];
                 b[c] = takeA ? b[c] : nx;
             };
@@ -480,7 +495,8 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             for (int c = 0; c < ILP; ++c)
 #pragma unroll
                 for (int q = 0; q < IPT; ++q)
-                    if (q < cnt[c]) sk[ph + d[c] + q] = okey[c][q];
+                    if (q < cnt[c])
+                        sk[ph + d[c] + q] = ORD ? om.inverse(okey[c][q]) : okey[c][q];
             if constexpr (VB != 0) {
                 V* ov = stage_v(s);
                 const int phv = int(in.gc & (EV - 1));
@@ -525,7 +541,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                 dst[c][q] = takeA ? pha + j[c] : boff + k[c];
                 j[c] += takeA ? 1 : 0;
                 k[c] += takeA ? 0 : 1;
-                const K nx = sk[takeA ? ao + j[c] : bo + k[c]];   // one load from either window
+                const K nx = km(sk[takeA ? ao + j[c] : bo + k[c]]);   // one load from either window
                 a[c] = takeA ? nx : a[c];
                 b[c] = takeA ? b[c] : nx;
             };

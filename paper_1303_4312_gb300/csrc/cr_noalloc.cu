@@ -87,9 +87,7 @@ bool ranges_overlap(const void* a, int64_t abytes, const void* b, int64_t bbytes
 extern "C" cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_t m,
                                              const void* B, int64_t n, void* C,
                                              uint32_t* C_tag, cr_stream stream) {
-    int ks = 0;
-    if (key_type == CR_KEY_I32 || key_type == CR_KEY_U32) ks = 4;
-    if (key_type == CR_KEY_I64 || key_type == CR_KEY_U64) ks = 8;
+    const int ks = cr::key_type_bytes(key_type);
     if (ks == 0) return na_fail(CR_EINVAL, "unknown key type %d", key_type);
     if (m < 0 || n < 0) return na_fail(CR_EINVAL, "negative size");
     const int64_t mn = m + n;
@@ -128,6 +126,7 @@ extern "C" cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cr::MergeArgs a{};
+    a.order = cr::key_type_order(key_type);
     a.ak = A;
     a.bk = B;
     a.ck = C;
@@ -138,17 +137,11 @@ extern "C" cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_
     a.tag_b = m;
     a.ws = scratch;
     auto run = [&](auto ops) {
-        cudaError_t e = ops.partition_single(A, m, B, n, tile, ntiles, scratch, st);
+        cudaError_t e = ops.partition_single(A, m, B, n, tile, ntiles, scratch, a.order, st);
         if (e != cudaSuccess) return e;
         return ops.merge_fwd(shape, 0, C_tag != nullptr, a, ntiles, st);
     };
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (key_type) {
-        case CR_KEY_I32: e = run(cr::KeyOps<int32_t>{}); break;
-        case CR_KEY_U32: e = run(cr::KeyOps<uint32_t>{}); break;
-        case CR_KEY_I64: e = run(cr::KeyOps<int64_t>{}); break;
-        case CR_KEY_U64: e = run(cr::KeyOps<uint64_t>{}); break;
-    }
+    const cudaError_t e = cr::with_key_ops(key_type, run);
     if (e != cudaSuccess)
         return na_fail(CR_ECUDA, "merge launch: %s", cudaGetErrorString(e));
     cr::set_last_error("");

@@ -31,9 +31,10 @@ __device__ __forceinline__ CoRankState co_rank_begin(int64_t i, int64_t m, int64
     return s;
 }
 
-template <class K>
-__device__ __forceinline__ void co_rank_step(CoRankState& s, const K* A, int64_t m, const K* B,
-                                             int64_t n) {
+// A and B are key views (KeyView: keys mapped into the call's order).
+template <class V>
+__device__ __forceinline__ void co_rank_step(CoRankState& s, V A, int64_t m, V B, int64_t n) {
+    using K = typename V::key_type;
     if (s.done) return;
     const int64_t j = s.j, k = s.k;
     const bool okA1 = j > 0 && j - 1 < m;
@@ -65,9 +66,9 @@ __device__ __forceinline__ int64_t co_rank_end(const CoRankState& s) {
 }
 
 // Co-ranks of ranks r0 and r1 of one merge problem, searched together.
-template <class K>
-__device__ __forceinline__ void co_rank_pair(int64_t r0, int64_t r1, const K* A, int64_t m,
-                                             const K* B, int64_t n, int64_t& j0, int64_t& j1) {
+template <class V>
+__device__ __forceinline__ void co_rank_pair(int64_t r0, int64_t r1, V A, int64_t m, V B,
+                                             int64_t n, int64_t& j0, int64_t& j1) {
     CoRankState s0 = co_rank_begin(r0, m, n);
     CoRankState s1 = co_rank_begin(r1, m, n);
 #pragma unroll 1
@@ -95,9 +96,9 @@ __device__ __forceinline__ TileRec make_rec(int64_t a_base, int64_t b_base, int6
 // which the first Lemma-1 condition holds (A[j-1] <= B[i-j], with B[n] =
 // +inf); the condition holds exactly for j <= j*, so G probes per round cut
 // the interval (G+1)-fold.
-template <class K, int G>
-__device__ __forceinline__ int64_t co_rank_group(const K* A, int64_t m, const K* B, int64_t n,
-                                                 int64_t i, int l, unsigned gmask, int gshift) {
+template <class V, int G>
+__device__ __forceinline__ int64_t co_rank_group(V A, int64_t m, V B, int64_t n, int64_t i,
+                                                 int l, unsigned gmask, int gshift) {
     int64_t lo = i - n > 0 ? i - n : 0;
     int64_t hi = i < m ? i : m;
 #pragma unroll 1
@@ -130,9 +131,11 @@ __device__ __forceinline__ int64_t co_rank_group(const K* A, int64_t m, const K*
 //     the top levels of their searches probe the same few positions (L1 and
 //     L2 hits) and only the last levels touch distinct DRAM sectors.
 template <class K>
-__global__ void __launch_bounds__(256) partition_single_kernel(const K* A, int64_t m, const K* B,
-                                                               int64_t n, int64_t tile,
-                                                               int64_t ntiles, void* ws) {
+__global__ void __launch_bounds__(256) partition_single_kernel(const K* Ap, int64_t m,
+                                                               const K* Bp, int64_t n,
+                                                               int64_t tile, int64_t ntiles,
+                                                               void* ws, int order) {
+    const KeyView<K> A{Ap, order}, B{Bp, order};
     __shared__ int64_t s_j[256];
     __shared__ int64_t s_jb[2];
     const int64_t mn = m + n;
@@ -148,8 +151,8 @@ __global__ void __launch_bounds__(256) partition_single_kernel(const K* A, int64
         const int grp = threadIdx.x >> 4;
         const int64_t tt = grp == 0 ? tb : (tb + 255 < ntiles ? tb + 255 : ntiles);
         const int64_t i = tt * tile < mn ? tt * tile : mn;
-        const int64_t j = co_rank_group<K, 16>(A, m, B, n, i, threadIdx.x & 15,
-                                               0xFFFFu << (16 * grp), 16 * grp);
+        const int64_t j = co_rank_group<KeyView<K>, 16>(A, m, B, n, i, threadIdx.x & 15,
+                                                        0xFFFFu << (16 * grp), 16 * grp);
         if ((threadIdx.x & 15) == 0) s_jb[grp] = j;
     }
     __syncthreads();
@@ -179,10 +182,11 @@ __global__ void __launch_bounds__(256) partition_single_kernel(const K* A, int64
 // ends itself with Algorithm 1 as printed (the two searches in lock step),
 // sharing nothing with other tiles.  Same records as partition_single_kernel.
 template <class K>
-__global__ void __launch_bounds__(256) partition_single_free_kernel(const K* A, int64_t m,
-                                                                    const K* B, int64_t n,
+__global__ void __launch_bounds__(256) partition_single_free_kernel(const K* Ap, int64_t m,
+                                                                    const K* Bp, int64_t n,
                                                                     int64_t tile, int64_t ntiles,
-                                                                    void* ws) {
+                                                                    void* ws, int order) {
+    const KeyView<K> A{Ap, order}, B{Bp, order};
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t == 0) {
         WsHeader* h = static_cast<WsHeader*>(ws);
@@ -230,10 +234,11 @@ __device__ __forceinline__ PassPos pass_locate(int64_t tt, int64_t N, int64_t w,
 }
 
 template <class K>
-__global__ void __launch_bounds__(256) partition_pass_kernel(const K* X, int64_t N, int64_t w,
+__global__ void __launch_bounds__(256) partition_pass_kernel(const K* Xp, int64_t N, int64_t w,
                                                              int64_t tile, int64_t tpp,
                                                              int64_t npairs, int64_t ntiles,
-                                                             void* ws) {
+                                                             void* ws, int order) {
+    const KeyView<K> X{Xp, order};
     __shared__ int64_t s_j[256];
     __shared__ int64_t s_jb[2];
     __shared__ int64_t s_qb[2];
@@ -248,9 +253,10 @@ __global__ void __launch_bounds__(256) partition_pass_kernel(const K* X, int64_t
         const int grp = threadIdx.x >> 4;
         const int64_t tt = grp == 0 ? tb : (tb + 255 < ntiles ? tb + 255 : ntiles);
         const PassPos p = pass_locate(tt, N, w, tile, tpp, npairs);
-        const K* A = X + 2 * p.q * w;
-        const int64_t j = co_rank_group<K, 16>(A, p.m, A + p.m, p.n, p.r, threadIdx.x & 15,
-                                               0xFFFFu << (16 * grp), 16 * grp);
+        const KeyView<K> A = X + 2 * p.q * w;
+        const int64_t j = co_rank_group<KeyView<K>, 16>(A, p.m, A + p.m, p.n, p.r,
+                                                        threadIdx.x & 15,
+                                                        0xFFFFu << (16 * grp), 16 * grp);
         if ((threadIdx.x & 15) == 0) {
             s_jb[grp] = j;
             s_qb[grp] = p.q;
@@ -260,8 +266,8 @@ __global__ void __launch_bounds__(256) partition_pass_kernel(const K* X, int64_t
     const int64_t tt = tb + threadIdx.x;
     if (tt <= ntiles) {
         const PassPos p = pass_locate(tt, N, w, tile, tpp, npairs);
-        const K* A = X + 2 * p.q * w;
-        const K* B = A + p.m;
+        const KeyView<K> A = X + 2 * p.q * w;
+        const KeyView<K> B = A + p.m;
         int64_t lo = p.r - p.n > 0 ? p.r - p.n : 0;
         int64_t hi = p.r < p.m ? p.r : p.m;
         if (p.q == s_qb[0] && s_jb[0] > lo) lo = s_jb[0];
@@ -363,9 +369,10 @@ static __global__ void __launch_bounds__(1024) segment_scan_kernel(const int64_t
 // Batched merge, step 2: one thread per tile finds its segment in the tile
 // prefix (binary search) and co-ranks both tile ends inside the segment.
 template <class K>
-__global__ void partition_batched_kernel(const K* A, const K* B, const int64_t* a_off,
+__global__ void partition_batched_kernel(const K* Ap, const K* Bp, const int64_t* a_off,
                                          const int64_t* b_off, int64_t nseg, int64_t tile,
-                                         const int64_t* prefix, void* ws) {
+                                         const int64_t* prefix, void* ws, int order) {
+    const KeyView<K> A{Ap, order}, B{Bp, order};
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t ntiles = static_cast<const WsHeader*>(ws)->ntiles;
     if (t >= ntiles) return;
@@ -388,9 +395,10 @@ __global__ void partition_batched_kernel(const K* A, const K* B, const int64_t* 
 
 // co_rank for a list of ranks (C-ABI names: rank k -> (i, j)).
 template <class K>
-__global__ void co_rank_many_kernel(const K* A, int64_t m, const K* B, int64_t n,
+__global__ void co_rank_many_kernel(const K* Ap, int64_t m, const K* Bp, int64_t n,
                                     const int64_t* ranks, int64_t cnt, int64_t* out_i,
-                                    int64_t* out_j) {
+                                    int64_t* out_j, int order) {
+    const KeyView<K> A{Ap, order}, B{Bp, order};
     const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (q >= cnt) return;
     const int64_t r = ranks[q];
@@ -409,8 +417,9 @@ __global__ void co_rank_many_kernel(const K* A, int64_t m, const K* B, int64_t n
 
 // One rank, result as two int64 (i, j) in device memory.
 template <class K>
-__global__ void co_rank_one_kernel(const K* A, int64_t m, const K* B, int64_t n, int64_t r,
-                                   int64_t* out_ij) {
+__global__ void co_rank_one_kernel(const K* Ap, int64_t m, const K* Bp, int64_t n, int64_t r,
+                                   int64_t* out_ij, int order) {
+    const KeyView<K> A{Ap, order}, B{Bp, order};
     CoRankState s = co_rank_begin(r, m, n);
 #pragma unroll 1
     for (int it = 0; it < 128 && !s.done; ++it) co_rank_step(s, A, m, B, n);

@@ -15,6 +15,8 @@
 //     the left run, which holds the earlier elements: stable);
 //  4. coalesced store of the keys; the payloads are gathered once through
 //     the carried indices (they never move during the rounds).
+// Keys are mapped into the call's order on load and back on store
+// (order_key).
 //
 // MODE 0: forward.  MODE 1: forward that also writes the run's permutation
 // (perm[base + x] = input index inside the run of output x), for a backward
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
                                                        K* __restrict__ Y, void* __restrict__ Yv,
                                                        uint16_t* __restrict__ perm,
                                                        const void* __restrict__ gY,
-                                                       void* __restrict__ gX) {
+                                                       void* __restrict__ gX, int order) {
     using L = SortLayout<K, VB, MODE, NT, IPT>;
     using V = typename VBits<VB>::T;
     constexpr bool IDX = L::IDX;
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
 
     // 1. load
     for (int x = tid; x < len; x += NT) {
-        sk0[x] = X[base + x];
+        sk0[x] = order_key(X[base + x], order);
         if constexpr (IDX) si0[x] = uint16_t(x);
         if constexpr (VB != 0 && MODE != 2) sv[x] = static_cast<const V*>(Xv)[base + x];
     }
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(NT) sort_runs_kernel(const K* __restrict__ X,
     // 4. store
     if constexpr (MODE != 2) {
         for (int x = tid; x < len; x += NT) {
-            Y[base + x] = fk[x];
+            Y[base + x] = order_key_inverse(fk[x], order);
             if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[fi[x]];
             if constexpr (MODE == 1) perm[base + x] = fi[x];
         }

@@ -86,14 +86,32 @@ def sharded_merge(A, B, group=None, co_rank=None, merge=None, gather: bool = Tru
 # found by Algorithm 1 with remote point reads, then each rank fetches the
 # two windows they delimit from their owners and merges them locally.
 # ---------------------------------------------------------------------------
-_MASK = {"i32": None, "i64": None, "u32": (1 << 32) - 1, "u64": (1 << 64) - 1}
+_WIDTH = {"i32": 32, "u32": 32, "f32": 32, "i64": 64, "u64": 64, "f64": 64}
 
 
 def _as_key(v: int, key_type: str) -> int:
-    """A key read back from an int64 carrier, as a Python int in the key
-    type's own order (unsigned types are masked to their width)."""
-    mask = _MASK[key_type]
-    return v & mask if mask is not None else v
+    """A key read back from an int64 carrier (the bits of the stored key,
+    sign-extended from its width), as a Python int whose integer order is the
+    key type's order: unsigned types are masked to their width; float bits
+    (IEEE-754 totalOrder) keep positives and flip the magnitude of negatives;
+    ':desc' negates."""
+    base, _, mod = key_type.partition(":")
+    bits = _WIDTH[base]
+    if base[0] == "u":
+        v &= (1 << bits) - 1
+    else:
+        v = ((v + (1 << (bits - 1))) & ((1 << bits) - 1)) - (1 << (bits - 1))   # sign-extend
+        if base[0] == "f" and v < 0:
+            v ^= (1 << (bits - 1)) - 1
+    return -v if mod == "desc" else v
+
+
+def _bits(t):
+    """Integer view of a key block (floats travel as their bit patterns)."""
+    import torch
+    if t.dtype.is_floating_point:
+        return t.view(torch.int32 if t.element_size() == 4 else torch.int64)
+    return t
 
 
 class _Prober:
@@ -105,7 +123,7 @@ class _Prober:
     def __init__(self, A_blk, B_blk, a_off, b_off, rank, world, group):
         import torch
         self.torch = torch
-        self.A, self.B = A_blk, B_blk
+        self.A, self.B = _bits(A_blk), _bits(B_blk)
         self.a0, self.a1 = a_off[rank], a_off[rank + 1]
         self.b0, self.b1 = b_off[rank], b_off[rank + 1]
         self.world, self.group = world, group

@@ -225,3 +225,20 @@ def test_recorded_run_sort_validation(lib):
     assert lib.cr_sort_runs_backward_recorded(4, -1, P, G, GX, None) == 1
     assert lib.cr_sort_runs_backward_recorded(4, N, P, G, ctypes.c_void_p(0x600100), None) == 2
     assert lib.cr_sort_runs_backward_recorded(4, 0, None, None, None, None) == 0
+
+
+def test_key_type_encodings(lib):
+    """Float and descending key types: sizes follow the storage width, and
+    unknown codes or flags are refused."""
+    F32, F64, DESC = 4, 5, 256
+    for code, width in ((F32, 4), (F64, 8), (0 | DESC, 4), (3 | DESC, 8), (F32 | DESC, 4),
+                        (F64 | DESC, 8)):
+        t = lib.cr_tile_size(code, 0)
+        assert t == lib.cr_tile_size(0 if width == 4 else 3, 0) and t > 0, code
+    for bad in (6, 255, 512, 6 | DESC, -1, 0x10000 | 0):
+        assert lib.cr_tile_size(bad, 0) == 0, bad
+        assert lib.cr_stable_merge(bad, None, 0, None, 0, None, None, None, 0, None) == 1
+    from paper_1303_4312_gb300 import _lib as L
+    assert L.key_code("f32:desc") == F32 | DESC and L.key_code("u64") == 3
+    with pytest.raises(ValueError):
+        L.key_code("f16")
