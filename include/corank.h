@@ -20,7 +20,10 @@
  * keys are IEEE-754 binary32/binary64 values ordered by the standard's
  * totalOrder predicate (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN, NaNs
  * by payload; every bit pattern is a valid key).  OR-ing CR_KEY_DESC into a key
- * type reverses the order (A and B descending, largest key first).  The paper
+ * type reverses the order (A and B descending, largest key first).
+ * CR_KEY_PAIR_U32/I32 keys are 64-bit words holding a (major, minor) pair
+ * of 32-bit keys -- the major key in the high 32 bits, i.e. a little-endian
+ * struct { minor; major; } -- ordered lexicographically.  The paper
  * states the method for any total order (Section 2); these are instances of
  * it.  The merge is stable in every order: equal keys keep their order inside
  * A and inside B, and an A element precedes every equal B element (second
@@ -75,6 +78,9 @@ typedef enum {
     CR_KEY_U64 = 3,
     CR_KEY_F32 = 4,   /* float bits, IEEE-754 totalOrder (see ORDER below) */
     CR_KEY_F64 = 5,   /* double bits, IEEE-754 totalOrder */
+    CR_KEY_PAIR_U32 = 6, /* (major, minor) uint32 pair in one 64-bit word, major in
+                            the high 32 bits; lexicographic order */
+    CR_KEY_PAIR_I32 = 7, /* the same with int32 halves */
     CR_KEY_DESC = 256 /* flag, OR-ed into any of the above: descending order */
 } cr_key_type;
 

@@ -322,7 +322,8 @@ def parallel_merge(A, B, p: int):
 # ---------------------------------------------------------------------------
 # Key orders (the paper's merge is stated for any total order, Section 2).
 # ---------------------------------------------------------------------------
-_ORDER_BITS = {"i32": 32, "u32": 32, "f32": 32, "i64": 64, "u64": 64, "f64": 64}
+_ORDER_BITS = {"i32": 32, "u32": 32, "f32": 32, "i64": 64, "u64": 64, "f64": 64,
+               "pair_u32": 64, "pair_i32": 64}
 
 
 def order_key(a: np.ndarray, key_type: str) -> np.ndarray:
@@ -335,6 +336,9 @@ def order_key(a: np.ndarray, key_type: str) -> np.ndarray:
                 (sign bit set) has every bit complemented, a non-negative one
                 has its sign bit set, so -NaN < -inf < ... < -0 < +0 < ... <
                 +inf < +NaN with NaN payloads ordered as the standard says;
+      pair_u32  a 64-bit word holding (major, minor) uint32 keys, major in
+                the high half: lexicographic order is the word's own order;
+      pair_i32  the same with int32 halves: each half offset binary;
       ":desc"   appended to any of these: the complement of the above.
     """
     base, _, mod = key_type.partition(":")
@@ -342,7 +346,11 @@ def order_key(a: np.ndarray, key_type: str) -> np.ndarray:
     ut = np.uint32 if bits == 32 else np.uint64
     u = np.ascontiguousarray(a).view(ut).copy()
     sign = ut(1) << ut(bits - 1)
-    if base[0] == "i":
+    if base == "pair_i32":
+        u ^= ut((1 << 63) | (1 << 31))
+    elif base == "pair_u32":
+        pass
+    elif base[0] == "i":
         u ^= sign
     elif base[0] == "f":
         neg = (u & sign) != 0

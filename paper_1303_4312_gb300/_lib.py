@@ -69,15 +69,16 @@ STATUS = {0: "CR_OK", 1: "CR_EINVAL", 2: "CR_EALIAS", 3: "CR_EALIGN", 4: "CR_ENO
           5: "CR_ECUDA", 6: "CR_ETIMEOUT", 7: "CR_EUNSUPPORTED", 8: "CR_EINTERNAL",
           9: "CR_EBADSEG"}
 
-KEY_TYPES = {"i32": 0, "u32": 1, "i64": 2, "u64": 3, "f32": 4, "f64": 5}
+KEY_TYPES = {"i32": 0, "u32": 1, "i64": 2, "u64": 3, "f32": 4, "f64": 5, "pair_u32": 6,
+             "pair_i32": 7}
 KEY_DESC = 256       # flag: descending order
-KEY_BYTES = {"i32": 4, "u32": 4, "f32": 4, "i64": 8, "u64": 8, "f64": 8}
 
 
 def key_code(key_type) -> int:
     """C-ABI key type of a name: "i32", "u32", "i64", "u64", "f32", "f64"
-    (floats in IEEE-754 totalOrder), with ":desc" for descending order, or an
-    int code passed through."""
+    (floats in IEEE-754 totalOrder), "pair_u32", "pair_i32" (lexicographic
+    (major, minor) pairs in one 64-bit word, major in the high half), with
+    ":desc" for descending order, or an int code passed through."""
     if isinstance(key_type, int):
         return key_type
     base, _, mod = str(key_type).partition(":")

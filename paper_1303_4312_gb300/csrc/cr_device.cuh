@@ -66,8 +66,11 @@ struct MergeArgs {
 //          its width (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN):
 //          negative values have their magnitude bits flipped, after which
 //          the signed integer order is the float total order;
+//   bit 2: a pair of signed 32-bit keys stored in one 64-bit word (major key
+//          in the high half), ordered lexicographically: both halves' sign
+//          bits flipped, after which the unsigned 64-bit order is that order;
 //   bit 0: descending: the bitwise complement reverses any integer order.
-// Both steps are involutions; order 0 is the identity.
+// All steps are involutions; order 0 is the identity.
 // ---------------------------------------------------------------------------
 template <class K>
 __device__ __forceinline__ K order_flip_float(K x) {
@@ -79,8 +82,14 @@ __device__ __forceinline__ K order_flip_float(K x) {
 }
 
 template <class K>
+__host__ __device__ constexpr K pair_sign_bits() {
+    return sizeof(K) == 8 ? K(0x8000000080000000ull) : K(0);
+}
+
+template <class K>
 __device__ __forceinline__ K order_key(K x, int order) {
     if (order & 2) x = order_flip_float(x);
+    if (order & 4) x = K(x ^ pair_sign_bits<K>());
     if (order & 1) x = K(~x);
     return x;
 }
@@ -88,14 +97,16 @@ __device__ __forceinline__ K order_key(K x, int order) {
 template <class K>
 __device__ __forceinline__ K order_key_inverse(K x, int order) {
     if (order & 1) x = K(~x);
+    if (order & 4) x = K(x ^ pair_sign_bits<K>());
     if (order & 2) x = order_flip_float(x);
     return x;
 }
 
 // order_key / order_key_inverse without branches, for hot loops: with
 // F = the magnitude bits when bit 1 of the order is set (else 0) and M = all
-// ones when bit 0 is set (else 0),  map(x) = x ^ ((sign(x) & F) ^ M), where
-// sign(x) is x's sign bit replicated; the inverse undoes M first.
+// ones when bit 0 is set (else 0), xor the pair sign bits when bit 2 is set,
+// map(x) = x ^ ((sign(x) & F) ^ M), where sign(x) is x's sign bit replicated
+// (bits 1 and 2 are never set together); the inverse undoes M first.
 template <class K>
 struct OrderMap {
     using S = typename std::make_signed<K>::type;
@@ -103,7 +114,8 @@ struct OrderMap {
     static constexpr int SH = 8 * int(sizeof(K)) - 1;
     K flt, neg;
     __device__ __forceinline__ explicit OrderMap(int order)
-        : flt((order & 2) ? K(U(~U(0)) >> 1) : K(0)), neg((order & 1) ? K(~U(0)) : K(0)) {}
+        : flt((order & 2) ? K(U(~U(0)) >> 1) : K(0)),
+          neg(K(((order & 1) ? K(~U(0)) : K(0)) ^ ((order & 4) ? pair_sign_bits<K>() : K(0)))) {}
     __device__ __forceinline__ K operator()(K x) const {
         return K(x ^ ((K(S(x) >> SH) & flt) ^ neg));
     }

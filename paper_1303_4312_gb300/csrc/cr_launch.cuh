@@ -149,7 +149,8 @@ cudaError_t sort_route_recorded(int vb, int64_t N, const uint16_t* perm, const v
 
 // C-ABI key types: storage width, storage type and order (order_key).
 // F32/F64 are stored and compared as the signed integer of their width after
-// the float total-order map; CR_KEY_DESC adds the complement.
+// the float total-order map; key pairs as uint64 (signed halves after the
+// pair map); CR_KEY_DESC adds the complement.
 inline int key_base(int key_type) { return key_type & ~int(CR_KEY_DESC); }
 
 inline int key_type_bytes(int key_type) {
@@ -160,14 +161,17 @@ inline int key_type_bytes(int key_type) {
         case CR_KEY_F32: return 4;
         case CR_KEY_I64:
         case CR_KEY_U64:
-        case CR_KEY_F64: return 8;
+        case CR_KEY_F64:
+        case CR_KEY_PAIR_U32:
+        case CR_KEY_PAIR_I32: return 8;
         default: return 0;
     }
 }
 
 inline int key_type_order(int key_type) {
     const int b = key_base(key_type);
-    return ((b == CR_KEY_F32 || b == CR_KEY_F64) ? 2 : 0) | ((key_type & CR_KEY_DESC) ? 1 : 0);
+    return ((b == CR_KEY_F32 || b == CR_KEY_F64) ? 2 : 0) | (b == CR_KEY_PAIR_I32 ? 4 : 0) |
+           ((key_type & CR_KEY_DESC) ? 1 : 0);
 }
 
 template <class F>
@@ -179,7 +183,9 @@ cudaError_t with_key_ops(int key_type, F&& f) {
         case CR_KEY_U32: return f(KeyOps<uint32_t>{});
         case CR_KEY_I64:
         case CR_KEY_F64: return f(KeyOps<int64_t>{});
-        case CR_KEY_U64: return f(KeyOps<uint64_t>{});
+        case CR_KEY_U64:
+        case CR_KEY_PAIR_U32:
+        case CR_KEY_PAIR_I32: return f(KeyOps<uint64_t>{});
         default: return cudaErrorInvalidValue;
     }
 }

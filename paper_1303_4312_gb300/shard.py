@@ -86,7 +86,8 @@ def sharded_merge(A, B, group=None, co_rank=None, merge=None, gather: bool = Tru
 # found by Algorithm 1 with remote point reads, then each rank fetches the
 # two windows they delimit from their owners and merges them locally.
 # ---------------------------------------------------------------------------
-_WIDTH = {"i32": 32, "u32": 32, "f32": 32, "i64": 64, "u64": 64, "f64": 64}
+_WIDTH = {"i32": 32, "u32": 32, "f32": 32, "i64": 64, "u64": 64, "f64": 64, "pair_u32": 64,
+          "pair_i32": 64}
 
 
 def _as_key(v: int, key_type: str) -> int:
@@ -97,6 +98,11 @@ def _as_key(v: int, key_type: str) -> int:
     ':desc' negates."""
     base, _, mod = key_type.partition(":")
     bits = _WIDTH[base]
+    if base.startswith("pair"):
+        v &= (1 << 64) - 1
+        if base == "pair_i32":
+            v ^= (1 << 63) | (1 << 31)      # both halves' sign bits: lexicographic
+        return -v if mod == "desc" else v
     if base[0] == "u":
         v &= (1 << bits) - 1
     else:

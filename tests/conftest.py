@@ -13,6 +13,10 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA path)")
     config.addinivalue_line("markers", "slow: full-size cases (minutes)")
+    config.addinivalue_line(
+        "markers", "host_only: argument checks that pass fake device addresses; they only run "
+                   "where no GPU is present, so a check that failed to refuse a call can never "
+                   "launch a kernel on them")
 
 
 def pytest_collection_modifyitems(config, items):
@@ -22,6 +26,10 @@ def pytest_collection_modifyitems(config, items):
     except Exception:
         have_gpu = False
     if have_gpu:
+        skip = pytest.mark.skip(reason="host-only check (fake device addresses) on a GPU machine")
+        for it in items:
+            if "host_only" in it.keywords:
+                it.add_marker(skip)
         return
     skip = pytest.mark.skip(reason="no CUDA device")
     for it in items:

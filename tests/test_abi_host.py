@@ -9,6 +9,8 @@ import pytest
 
 from paper_1303_4312_gb300 import _lib
 
+pytestmark = pytest.mark.host_only
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -41,11 +43,11 @@ def test_status_strings(lib):
 
 
 def test_tile_sizes(lib):
-    for kt in range(4):
+    for kt in range(8):
         for vb in (0, 4, 8):
             t = lib.cr_tile_size(kt, vb)
             assert t > 0 and t % 4 == 0
-    assert lib.cr_tile_size(7, 0) == 0
+    assert lib.cr_tile_size(8, 0) == 0
     assert lib.cr_tile_size(0, 3) == 0
 
 
@@ -235,7 +237,9 @@ def test_key_type_encodings(lib):
                         (F64 | DESC, 8)):
         t = lib.cr_tile_size(code, 0)
         assert t == lib.cr_tile_size(0 if width == 4 else 3, 0) and t > 0, code
-    for bad in (6, 255, 512, 6 | DESC, -1, 0x10000 | 0):
+    for code in (6, 7, 6 | DESC, 7 | DESC):          # 32-bit key pairs in 64-bit words
+        assert lib.cr_tile_size(code, 0) == lib.cr_tile_size(3, 0)
+    for bad in (8, 255, 512, 8 | DESC, -1, 0x10000 | 0):
         assert lib.cr_tile_size(bad, 0) == 0, bad
         assert lib.cr_stable_merge(bad, None, 0, None, 0, None, None, None, 0, None) == 1
     from paper_1303_4312_gb300 import _lib as L

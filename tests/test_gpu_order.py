@@ -14,9 +14,10 @@ from gpu_util import dev, host, same_bits
 
 pytestmark = pytest.mark.gpu
 
-ORDERS = ["f32", "f64", "f32:desc", "f64:desc", "i32:desc", "u32:desc", "i64:desc", "u64:desc"]
+ORDERS = ["f32", "f64", "f32:desc", "f64:desc", "i32:desc", "u32:desc", "i64:desc", "u64:desc",
+          "pair_u32", "pair_i32", "pair_i32:desc"]
 DT = {"f32": np.float32, "f64": np.float64, "i32": np.int32, "u32": np.uint32,
-      "i64": np.int64, "u64": np.uint64}
+      "i64": np.int64, "u64": np.uint64, "pair_u32": np.uint64, "pair_i32": np.uint64}
 
 
 def draw(rng, size, kt, distinct=None):
@@ -35,6 +36,11 @@ def draw(rng, size, kt, distinct=None):
         specials = np.array([0.0, -0.0, np.inf, -np.inf], dtype=dt)
         sp = rng.random(size) < 0.05
         x[sp] = specials[rng.integers(0, 4, int(sp.sum()))]
+    elif base.startswith("pair"):
+        # few distinct major keys, so the minor key decides often
+        major = rng.integers(0, 2**32, max(1, size // 50 + 1), dtype=np.uint64)
+        x = (major[rng.integers(0, len(major), size)] << np.uint64(32)) | \
+            rng.integers(0, 2**32, size, dtype=np.uint64)
     else:
         info = np.iinfo(dt)
         x = rng.integers(info.min, info.max, size, dtype=dt, endpoint=True)
@@ -138,7 +144,7 @@ def test_recorded_pass_in_order(kt):
     assert same_bits(host(gX, np.float32), g)
 
 
-@pytest.mark.parametrize("kt", ["f32", "f64:desc", "i32:desc", "u64:desc"])
+@pytest.mark.parametrize("kt", ["f32", "f64:desc", "i32:desc", "u64:desc", "pair_i32"])
 @pytest.mark.parametrize("record", [True, False])
 def test_sort_from_unsorted_in_order(kt, record):
     rng = np.random.default_rng(404)

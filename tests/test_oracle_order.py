@@ -131,3 +131,30 @@ def test_merge_in_order_brute_force(kt):
         ref = sorted(range(m + n), key=lambda i: int(ka[i]))
         assert list(src) == ref
         assert C.tobytes() == np.concatenate([A, B])[ref].tobytes()
+
+
+@pytest.mark.parametrize("kt", ["pair_u32", "pair_i32", "pair_i32:desc", "pair_u32:desc"])
+def test_pair_orders_are_lexicographic(kt):
+    """(major, minor) pairs in one 64-bit word, major in the high half:
+    order_key order equals Python's stable sort of the (major, minor) tuples
+    with the halves read as uint32 or int32 (reversed for ':desc')."""
+    rng = np.random.default_rng(4)
+    n = 4000
+    major = rng.integers(0, 2**32, n, dtype=np.uint64)
+    major[: n // 2] = major[n // 2:]                       # repeated majors
+    minor = rng.integers(0, 2**32, n, dtype=np.uint64)
+    minor[:50] = minor[50:100]
+    major[:50] = major[50:100]                             # full ties
+    words = (major << np.uint64(32)) | minor
+    signed = kt.startswith("pair_i32")
+
+    def half(v):
+        v = int(v)
+        return v - (1 << 32) if signed and v >= (1 << 31) else v
+    tup = [(half(a), half(b)) for a, b in zip(major, minor)]
+    if kt.endswith(":desc"):
+        ref = sorted(range(n), key=lambda i: (-tup[i][0], -tup[i][1]))
+    else:
+        ref = sorted(range(n), key=lambda i: tup[i])
+    got = np.argsort(oracle.order_key(words, kt), kind="stable")
+    assert np.array_equal(got, ref)

@@ -178,3 +178,24 @@ def test_distributed_merge_block_inputs(world):
             assert cb == want[k0:k1].tobytes(), (ci, rank)
             if wantv is not None:
                 assert cvb == wantv[k0:k1].tobytes(), (ci, rank)
+
+
+@pytest.mark.parametrize("kt", ["i32", "u32", "i64", "u64", "f32", "f64", "pair_u32", "pair_i32",
+                                "i32:desc", "f64:desc", "pair_i32:desc"])
+def test_remote_key_order_matches_oracle(kt):
+    """The distributed co-rank compares keys read back through int64
+    carriers (_as_key): their order must be the oracle's order for every key
+    type, including floats (totalOrder), pairs and descending orders."""
+    import oracle
+    rng = np.random.default_rng(113)
+    base = kt.split(":")[0]
+    width = 32 if base in ("i32", "u32", "f32") else 64
+    ut = np.uint32 if width == 32 else np.uint64
+    bits = rng.integers(0, np.iinfo(ut).max, 3000, dtype=ut, endpoint=True)
+    bits[:30] = bits[30:60]
+    st = {32: np.int32, 64: np.int64}[width]
+    carriers = bits.view(st).astype(np.int64)        # what the prober all-reduces
+    keys = [shard._as_key(int(v), kt) for v in carriers]
+    ref = np.argsort(oracle.order_key(bits, kt if base[0] != "f" else kt), kind="stable")
+    got = sorted(range(len(keys)), key=lambda i: keys[i])
+    assert np.array_equal(got, ref)

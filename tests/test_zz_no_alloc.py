@@ -25,19 +25,21 @@ def lib():
     return _lib.load()
 
 
+@pytest.mark.host_only
 def test_noalloc_rejects_oversize_without_gpu(lib):
-    """Beyond the array's capacity the call is refused before any launch."""
-    tile = lib.cr_tile_size(0, 0)
-    too_many = MAX_TILES * tile + 1
-    A = ctypes.c_void_p(0x1_0000_0000)
-    st = lib.cr_stable_merge_noalloc(0, A, too_many, ctypes.c_void_p(0x10_0000_0000), 0,
-                                     ctypes.c_void_p(0x20_0000_0000), None, None)
-    assert st == 1
-    assert "scratch" in lib.cr_last_error().decode()
-    tile8 = lib.cr_tile_size(3, 0)
-    st = lib.cr_stable_merge_noalloc(3, A, MAX_TILES * tile8 + 1, A, 0,
-                                     ctypes.c_void_p(0x40_0000_0000), None, None)
-    assert st == 1
+    """Beyond the array's capacity the call is refused before any launch.
+    The sizes exceed the capacity under every tile shape (TILE <= 4096), so
+    the refusal does not depend on which shape the call's geometry selects."""
+    too_many = MAX_TILES * 4096 + 1
+    for code, (m, n) in ((0, (too_many, 0)), (0, (too_many // 2, too_many // 2 + 1)),
+                         (3, (too_many, 0)), (3, (1, too_many))):
+        assert (m + n + lib.cr_tile_size_for(code, 0, m, n) - 1) // \
+            lib.cr_tile_size_for(code, 0, m, n) > MAX_TILES
+        st = lib.cr_stable_merge_noalloc(code, ctypes.c_void_p(0x1_0000_0000), m,
+                                         ctypes.c_void_p(0x10_0000_0000), n,
+                                         ctypes.c_void_p(0x20_0000_0000), None, None)
+        assert st == 1, (code, m, n)
+        assert "scratch" in lib.cr_last_error().decode()
 
 
 def _merge_both(lib, A, B, code, tag):
