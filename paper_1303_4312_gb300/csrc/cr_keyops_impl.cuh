@@ -165,6 +165,13 @@ template <class K>
 cudaError_t KeyOps<K>::partition_single(const void* A, int64_t m, const void* B, int64_t n,
                                         int64_t tile, int64_t ntiles, void* ws, int order,
                                         cudaStream_t st) {
+    if (ntiles <= kSmallMergeTiles) {
+        // 16 lanes per tile start, 15 tiles per block
+        const unsigned g = unsigned(((ntiles > 0 ? ntiles : 1) + 14) / 15);
+        partition_single_small_kernel<K><<<g, 256, 0, st>>>(
+            static_cast<const K*>(A), m, static_cast<const K*>(B), n, tile, ntiles, ws, order);
+        return cudaGetLastError();
+    }
     // 256 threads search 256 consecutive boundaries = 255 tiles per block
     const unsigned g = unsigned(((ntiles > 0 ? ntiles : 1) + 254) / 255);
     partition_single_kernel<K><<<g, 256, 0, st>>>(static_cast<const K*>(A), m,

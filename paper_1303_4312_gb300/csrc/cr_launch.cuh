@@ -77,6 +77,11 @@ inline int geometry_class(int64_t m, int64_t n) {
 // owns the table).
 int current_shape(int key_bytes, int vb, int cls);
 
+// Single merges with at most this many tiles co-rank every tile start with
+// its own 16-lane group (fewer dependent rounds; the probes of all tile
+// starts stay within a few MB).
+constexpr int64_t kSmallMergeTiles = 4096;
+
 // Run formation shape: 256 threads x 7 elements per run.
 constexpr int kSortNT = 256, kSortIPT = 7;
 constexpr int64_t kSortRun = int64_t(kSortNT) * kSortIPT;

@@ -178,6 +178,44 @@ __global__ void __launch_bounds__(256) partition_single_kernel(const K* Ap, int6
     }
 }
 
+// Single merge with few tiles: every tile start is co-ranked by its own
+// group of 16 lanes (co_rank_group over the whole range), so the search takes
+// about log17 of the range in dependent rounds instead of the block-end
+// search followed by a bisection.  A block of 256 threads (16 groups) owns
+// tiles tb .. tb+14 and the 16 starts tb .. tb+15.  Used when the merge has
+// few tiles (the extra probes are then a few MB at most); same records as
+// partition_single_kernel.
+template <class K>
+__global__ void __launch_bounds__(256) partition_single_small_kernel(const K* Ap, int64_t m,
+                                                                     const K* Bp, int64_t n,
+                                                                     int64_t tile, int64_t ntiles,
+                                                                     void* ws, int order) {
+    const KeyView<K> A{Ap, order}, B{Bp, order};
+    __shared__ int64_t s_j[16];
+    const int64_t mn = m + n;
+    const int grp = threadIdx.x >> 4;
+    const int64_t tb = int64_t(blockIdx.x) * 15;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        WsHeader* h = static_cast<WsHeader*>(ws);
+        h->status = kDevOk;
+        h->tile = int32_t(tile);
+        h->ntiles = ntiles;
+    }
+    const int64_t tt = tb + grp < ntiles ? tb + grp : ntiles;   // boundary of this group
+    const int64_t i = tt * tile < mn ? tt * tile : mn;
+    const unsigned gmask = 0xFFFFu << (16 * (grp & 1));
+    const int64_t j = co_rank_group<KeyView<K>, 16>(A, m, B, n, i, threadIdx.x & 15, gmask,
+                                                    16 * (grp & 1));
+    if ((threadIdx.x & 15) == 0) s_j[grp] = j;
+    __syncthreads();
+    const int64_t t = tb + threadIdx.x;
+    if (threadIdx.x < 15 && t < ntiles) {
+        const int64_t r0 = t * tile;
+        const int64_t r1 = r0 + tile < mn ? r0 + tile : mn;
+        ws_recs(ws)[t] = make_rec(0, 0, 0, r0, r1, s_j[threadIdx.x], s_j[threadIdx.x + 1]);
+    }
+}
+
 // Single merge, sync-free form of Algorithm 2: tile t co-ranks both of its
 // ends itself with Algorithm 1 as printed (the two searches in lock step),
 // sharing nothing with other tiles.  Same records as partition_single_kernel.
