@@ -366,6 +366,19 @@ cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_t m, const 
  * ------------------------------------------------------------------------ */
 cr_status cr_workspace_status(const void* ws, cr_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Test hook (the paper has no counterpart).  Every mbarrier wait inside the
+ * merge kernels gives up after a time limit, records CR_ETIMEOUT in the
+ * workspace status word and lets the kernel return.  This call runs that
+ * path on purpose: a one-thread kernel waits, with the same bounded wait and
+ * `limit_ns` (1 .. 10^8 ns), on a barrier nothing arrives at, then writes the
+ * status word of ws (ws_bytes >= 16, 16-byte aligned); cr_workspace_status
+ * must then return CR_ETIMEOUT.  d_elapsed_ns (device, nullable) receives the
+ * time the wait took.  CR_EINVAL for bad arguments.
+ * ------------------------------------------------------------------------ */
+cr_status cr_selftest_bounded_wait(void* ws, size_t ws_bytes, uint64_t limit_ns,
+                                   uint64_t* d_elapsed_ns, cr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

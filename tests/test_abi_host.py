@@ -246,3 +246,12 @@ def test_key_type_encodings(lib):
     assert L.key_code("f32:desc") == F32 | DESC and L.key_code("u64") == 3
     with pytest.raises(ValueError):
         L.key_code("f16")
+
+
+def test_selftest_argument_checks(lib):
+    WS = ctypes.c_void_p(0x100000)
+    assert lib.cr_selftest_bounded_wait(None, 256, 1000, None, None) == 1
+    assert lib.cr_selftest_bounded_wait(WS, 8, 1000, None, None) == 1
+    assert lib.cr_selftest_bounded_wait(ctypes.c_void_p(0x100004), 256, 1000, None, None) == 1
+    assert lib.cr_selftest_bounded_wait(WS, 256, 0, None, None) == 1
+    assert lib.cr_selftest_bounded_wait(WS, 256, 10**9, None, None) == 1
