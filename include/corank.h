@@ -367,6 +367,17 @@ cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_t m, const 
 cr_status cr_workspace_status(const void* ws, cr_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Debug check of the precondition (the hot path does not validate it): is
+ * A[0, m) sorted in key_type's order (including float and descending orders)?
+ * d_first (device, one int64) receives -1 when it is, else the smallest p
+ * with A[p] before A[p-1] in that order.  ws: device scratch of at least 16
+ * bytes (16-byte aligned); A 16-byte aligned.  Asynchronous on `stream`.
+ * CR_EINVAL / CR_EALIGN for bad arguments.
+ * ------------------------------------------------------------------------ */
+cr_status cr_check_sorted(int key_type, const void* A, int64_t m, int64_t* d_first, void* ws,
+                          size_t ws_bytes, cr_stream stream);
+
+/* ------------------------------------------------------------------------
  * Test hook (the paper has no counterpart).  Every mbarrier wait inside the
  * merge kernels gives up after a time limit, records CR_ETIMEOUT in the
  * workspace status word and lets the kernel return.  This call runs that

@@ -58,6 +58,7 @@ SIGNATURES = {
     "cr_merge_pass_backward_recorded": ([INT, INT, I64, I64, P, SZ, P, P, P, SZ, P], INT),
     "cr_workspace_status": ([P, P], INT),
     "cr_selftest_bounded_wait": ([P, SZ, ctypes.c_uint64, P, P], INT),
+    "cr_check_sorted": ([INT, P, I64, P, P, SZ, P], INT),
     "cr_sort_run_length": ([], I64),
     "cr_sort_runs": ([INT, INT, P, P, I64, P, P, P], INT),
     "cr_sort_runs_record": ([INT, INT, P, P, I64, P, P, P, P], INT),

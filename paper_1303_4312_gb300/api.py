@@ -541,6 +541,19 @@ def merge_pass_backward_recorded(record: PassRecord, gY, out=None):
     return gX
 
 
+def check_sorted(A: torch.Tensor, key_type: str | None = None) -> int:
+    """-1 if A is sorted in key_type's order, else the first position p with
+    A[p] before A[p-1] (a debug check of the merge's precondition)."""
+    lib = _lib.load()
+    dev = _dev(A)
+    kt = _key_code(A, key_type)
+    out = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = _ws(16, dev)
+    _lib.check(lib.cr_check_sorted(kt, _ptr(A), A.numel(), _ptr(out), _ptr(ws), ws.numel(),
+                                   _stream(dev)))
+    return int(out.item())
+
+
 def workspace_status(ws: torch.Tensor) -> None:
     """Synchronise the current stream and raise if the last call that used
     `ws` recorded a device-side error."""

@@ -255,3 +255,13 @@ def test_selftest_argument_checks(lib):
     assert lib.cr_selftest_bounded_wait(ctypes.c_void_p(0x100004), 256, 1000, None, None) == 1
     assert lib.cr_selftest_bounded_wait(WS, 256, 0, None, None) == 1
     assert lib.cr_selftest_bounded_wait(WS, 256, 10**9, None, None) == 1
+
+
+def test_check_sorted_argument_checks(lib):
+    A, O, WS = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000), ctypes.c_void_p(0x300000)
+    assert lib.cr_check_sorted(99, A, 10, O, WS, 16, None) == 1
+    assert lib.cr_check_sorted(0, A, -1, O, WS, 16, None) == 1
+    assert lib.cr_check_sorted(0, None, 10, O, WS, 16, None) == 1
+    assert lib.cr_check_sorted(0, A, 10, None, WS, 16, None) == 1
+    assert lib.cr_check_sorted(0, A, 10, O, WS, 8, None) == 1
+    assert lib.cr_check_sorted(0, ctypes.c_void_p(0x100004), 10, O, WS, 16, None) == 3

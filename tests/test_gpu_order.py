@@ -163,3 +163,24 @@ def test_sort_from_unsorted_in_order(kt, record):
         g = np.empty_like(gY)
         g[o] = gY
         assert same_bits(host(Xvt.grad, np.float32), g), N
+
+
+@pytest.mark.parametrize("kt", ["i32", "u32", "i64", "u64"] + ORDERS)
+def test_check_sorted(kt):
+    """cr_check_sorted: -1 on sorted input; else the first position whose key
+    comes before its predecessor in kt's order (numpy on the oracle's order
+    keys)."""
+    rng = np.random.default_rng(405)
+    for N in (0, 1, 2, 1000, 300001):
+        X = in_order(draw(rng, N, kt, 5000), kt)
+        assert cr.check_sorted(dev(X), key_type=kt) == -1, N
+        if N < 2:
+            continue
+        for _ in range(3):
+            Y = X.copy()
+            p, q = sorted(rng.integers(0, N, 2))
+            Y[p], Y[q] = Y[q], Y[p]
+            k = oracle.order_key(Y, kt)
+            bad = np.nonzero(k[1:] < k[:-1])[0]
+            want = int(bad[0]) + 1 if len(bad) else -1
+            assert cr.check_sorted(dev(Y), key_type=kt) == want, (N, p, q)
