@@ -208,3 +208,20 @@ def test_alg2_partition_independence_and_balance():
             assert counts.sum() == tot
             assert counts.max() <= -(-tot // p)
             assert counts.min() >= tot // p
+
+
+def test_co_rank_cross_checked_with_merge_sources():
+    """The oracle's two independent statements agree: Algorithm 1's co-rank j
+    of every rank i equals the number of A elements among the first i
+    outputs of the two-pointer merge (j = #{t < i : src[t] < m})."""
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        m, n = rng.integers(0, 400, 2)
+        spread = int(rng.choice([2, 10, 1000]))
+        A = np.sort(rng.integers(0, spread, m)).astype(np.int64)
+        B = np.sort(rng.integers(0, spread, n)).astype(np.int64)
+        _, src = oracle.merge(A, B)
+        from_a = np.concatenate([[0], np.cumsum(src < m)])
+        ranks = np.arange(m + n + 1)
+        j, k = oracle.co_rank_many(A, B, ranks)
+        assert np.array_equal(j, from_a) and np.array_equal(k, ranks - from_a)
