@@ -22,9 +22,14 @@ __all__ = [
 ]
 
 
+_SUBMODULES = ("api", "shard", "workloads", "autotune", "build", "_lib")
+
+
 def __getattr__(name):
     if name == "CorankError":
         return import_module("._lib", __name__).CorankError
+    if name in _SUBMODULES:
+        return import_module("." + name, __name__)
     if name in __all__:
         return getattr(import_module(".api", __name__), name)
     raise AttributeError(name)
