@@ -30,7 +30,8 @@ for _name, _kt in (("uint32", "u32"), ("uint64", "u64")):
 
 def _key_code(t: torch.Tensor, key_type: str | None) -> int:
     """Key type code for tensor t: from key_type ("i32", "u32", "i64", "u64",
-    "f32", "f64", optionally ":desc"), else from t's dtype (ascending)."""
+    "f32", "f64", "pair_u32", "pair_i32", optionally ":desc"), else from t's
+    dtype (ascending)."""
     if key_type is None:
         if t.dtype not in _DTYPE_KEY:
             raise TypeError(f"key dtype {t.dtype} is not int32/int64/uint32/uint64/float32/"
@@ -126,7 +127,8 @@ def merge_workspace_bytes(key_type: str, val_bytes: int, m: int, n: int) -> int:
 def merge(A: torch.Tensor, B: torch.Tensor, key_type: str | None = None, tag: bool = False,
           out: torch.Tensor | None = None, out_tag: torch.Tensor | None = None,
           ws: torch.Tensor | None = None):
-    """Stable merge of ascending A and B (ties: A first).
+    """Stable merge of A and B, both sorted in key_type's order (ties: A
+    first).
 
     With ``tag=True`` also returns the uint32 source tags (as int32 bits):
     i for A[i], m + j for B[j]."""
