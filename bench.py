@@ -731,12 +731,16 @@ def run_row(args):
         X, Xv = W.t_sort_u64_f32(device=dev, shift=args.shift)
         N = X.numel()
         gY = torch.randn(N, device=dev)
-        # algorithmic bytes per element and pass: forward keys + payloads in
-        # and out (+ one flag bit recorded); backward gY in, gX out (+ the
-        # flag bit, or the pass's input keys re-read)
-        fwd_b = {"record": 24 + 1 / 8, "recompute": 24}
-        bwd_b = {"record": 8 + 1 / 8, "recompute": 16}
-        rows, per_pass = {}, {}
+        # algorithmic bytes per element and stage: forward keys + payloads in
+        # and out (+ one flag bit recorded by a pass, + the 2-byte chunk
+        # permutation recorded by the shared-memory stage); backward gY in,
+        # gX out (+ the flag bit or the permutation, or the pass's input keys
+        # re-read)
+        def stage_bytes(mode, kind):
+            if kind == "block":
+                return 26.0, 10.0
+            return (24 + 1 / 8, 8 + 1 / 8) if mode == "record" else (24.0, 16.0)
+        rows, per_pass, alg = {}, {}, {}
         for mode in ("record", "recompute"):
             plan = api.MergeSortPlan(N, 1024, X.dtype, Xv.dtype, dev, key_type="u64",
                                      graph=True, record=mode == "record")
@@ -759,40 +763,31 @@ def run_row(args):
                     timer.marks.append((None, timer.marks[-1][1]))
             torch.cuda.synchronize()
             rows[mode] = timer.totals()
-            # per-pass breakdown: the same chain pass by pass outside the
-            # graphs (partition + tile kernel, or the routing kernel)
+            alg[mode] = (sum(stage_bytes(mode, kd)[0] for kd, _ in plan.stages) * N,
+                         sum(stage_bytes(mode, kd)[1] for kd, _ in plan.stages) * N)
+            # per-stage breakdown: the same chain stage by stage outside the
+            # graphs (partition + tile kernel, shared-memory stage, or routing)
             P = plan.passes
             plan.keys[0].copy_(X)
             plan.vals[0].copy_(Xv)
             plan.grads[P & 1].copy_(gY)
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * P + 2)]
-            for p_, w in enumerate(plan.widths):
-                ev[p_].record(stream)
-                kin, kout = plan._key_buf(p_), plan._key_buf(p_ + 1)
-                out = (kout, plan.vals[(p_ + 1) & 1])
-                if mode == "record":
-                    api.merge_pass_record(kin, plan.vals[p_ & 1], w, key_type="u64", out=out,
-                                          record=plan.records[p_])
-                else:
-                    api.merge_pass(kin, plan.vals[p_ & 1], w, key_type="u64", out=out,
-                                   ws=plan.ws)
+            for i in range(P):
+                ev[i].record(stream)
+                plan.run_stage(i)
             ev[P].record(stream)
-            for p_ in reversed(range(P)):
-                src, dst = plan.grads[(p_ + 1) & 1], plan.grads[p_ & 1]
-                if mode == "record":
-                    api.merge_pass_backward_recorded(plan.records[p_], src, out=dst)
-                else:
-                    api.merge_pass_backward(plan.keys[p_], src, plan.widths[p_],
-                                            key_type="u64", out=dst, ws=plan.ws)
-                ev[2 * P - p_].record(stream)
+            for i in reversed(range(P)):
+                plan.run_stage_backward(i)
+                ev[2 * P - i].record(stream)
             torch.cuda.synchronize()
             pp = []
-            for p_, w in enumerate(plan.widths):
-                f = ev[p_].elapsed_time(ev[p_ + 1])
-                b = ev[2 * P - p_ - 1].elapsed_time(ev[2 * P - p_])
-                pp.append({"width": w, "fwd_ms": round(f, 4), "bwd_ms": round(b, 4),
-                           "fwd_gbs": round(fwd_b[mode] * N / (f / 1e3) / 1e9, 1),
-                           "bwd_gbs": round(bwd_b[mode] * N / (b / 1e3) / 1e9, 1)})
+            for i, (kind, w) in enumerate(plan.stages):
+                f = ev[i].elapsed_time(ev[i + 1])
+                b = ev[2 * P - i - 1].elapsed_time(ev[2 * P - i])
+                fb, bb = stage_bytes(mode, kind)
+                pp.append({"stage": kind, "width": w, "fwd_ms": round(f, 4), "bwd_ms": round(b, 4),
+                           "fwd_gbs": round(fb * N / (f / 1e3) / 1e9, 1),
+                           "bwd_gbs": round(bb * N / (b / 1e3) / 1e9, 1)})
             per_pass[mode] = pp
             del plan
             torch.cuda.empty_cache()
@@ -850,17 +845,18 @@ def run_row(args):
         torch.cuda.empty_cache()
         P = len(per_pass["record"])
         rec = rows["record"]
-        extra = {"passes": P, "backward": "record",
+        extra = {"stages": P, "backward": "record",
                  "recompute": {}, "unsorted_input": unsorted, "per_pass": per_pass,
-                 "note": "each graph replays its passes' launches; bytes are per pass, times "
-                         "passes; value and the kernels rows are the recorded form"}
+                 "note": "each graph replays its stages' launches (the recorded form merges "
+                         "widths below 4096 in one shared-memory stage); bytes are summed over "
+                         "stages; value and the kernels rows are the recorded form"}
         for label, ms in rows["recompute"].items():
-            b = (fwd_b if label == "fwd_graph" else bwd_b)["recompute"] * N * P
+            b = alg["recompute"][0 if label == "fwd_graph" else 1]
             gbs = b / (ms / K / 1e3) / 1e9
             extra["recompute"][label] = {"ms": round(ms / K, 4), "gbs": round(gbs, 1),
                                          "frac": round(gbs / peak, 4)}
-        return finish(rec, {"fwd_graph": int(fwd_b["record"] * N * P),
-                            "bwd_graph": int(bwd_b["record"] * N * P)}, "sort_u64_f32", N,
+        return finish(rec, {"fwd_graph": int(alg["record"][0]),
+                            "bwd_graph": int(alg["record"][1])}, "sort_u64_f32", N,
                       extra, combos=[("uint64+f32", 3, 4)])
     raise ValueError(args.workload)
 

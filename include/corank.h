@@ -367,6 +367,30 @@ cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_t m, const 
 cr_status cr_workspace_status(const void* ws, cr_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Merge block: the first passes of a merge sort done inside shared memory
+ * (the paper has no counterpart; same result as those cr_merge_pass calls).
+ * X[0, N) holds sorted runs of `width` (a power of two, 8 <= width <=
+ * cr_merge_runs_block_length() / 2); every chunk of
+ * cr_merge_runs_block_length() elements (4096; the last chunk may be
+ * shorter) is merged into one sorted run of Y, i.e. the passes width, 2 width,
+ * ..., up to the chunk length, in one read and one write of the arrays.
+ * val_bytes 0, 4 or 8.  With perm (uint16, N entries, 4 or 8 byte payloads
+ * only) the chunk permutation is written: perm[base + x] = index inside the
+ * chunk of the input element that became output x; its backward
+ * cr_merge_runs_block_backward_recorded routes gY to gX through it without
+ * keys.  Arrays 16-byte aligned (CR_EALIGN); outputs must not overlap
+ * inputs (CR_EALIAS); CR_EINVAL for a bad width, key type or payload width.
+ * ------------------------------------------------------------------------ */
+int64_t cr_merge_runs_block_length(void);
+
+cr_status cr_merge_runs_block(int key_type, int val_bytes, const void* X, const void* Xv,
+                              int64_t N, int64_t width, void* Y, void* Yv, uint16_t* perm,
+                              cr_stream stream);
+
+cr_status cr_merge_runs_block_backward_recorded(int val_bytes, int64_t N, const uint16_t* perm,
+                                                const void* gY, void* gX, cr_stream stream);
+
+/* ------------------------------------------------------------------------
  * Debug check of the precondition (the hot path does not validate it): is
  * A[0, m) sorted in key_type's order (including float and descending orders)?
  * d_first (device, one int64) receives -1 when it is, else the smallest p

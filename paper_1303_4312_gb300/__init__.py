@@ -18,7 +18,8 @@ __all__ = [
     "MergeSortPlan", "MergeMany", "merge_many", "HostMerger", "sort_runs", "sort_runs_backward",
     "sort_run_length", "PassRecord", "merge_pass_record", "merge_pass_backward_recorded",
     "merge_pass_record_bytes", "sort_runs_record", "sort_runs_backward_recorded",
-    "check_sorted",
+    "check_sorted", "merge_runs_block", "merge_runs_block_backward_recorded",
+    "merge_runs_block_length",
 ]
 
 

@@ -59,6 +59,9 @@ SIGNATURES = {
     "cr_workspace_status": ([P, P], INT),
     "cr_selftest_bounded_wait": ([P, SZ, ctypes.c_uint64, P, P], INT),
     "cr_check_sorted": ([INT, P, I64, P, P, SZ, P], INT),
+    "cr_merge_runs_block_length": ([], I64),
+    "cr_merge_runs_block": ([INT, INT, P, P, I64, I64, P, P, P, P], INT),
+    "cr_merge_runs_block_backward_recorded": ([INT, I64, P, P, P, P], INT),
     "cr_sort_run_length": ([], I64),
     "cr_sort_runs": ([INT, INT, P, P, I64, P, P, P], INT),
     "cr_sort_runs_record": ([INT, INT, P, P, I64, P, P, P, P], INT),

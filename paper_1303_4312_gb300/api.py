@@ -625,6 +625,44 @@ def sort_runs_backward_recorded(perm, gY, out=None):
     return gX
 
 
+def merge_runs_block_length() -> int:
+    """Chunk length of merge_runs_block (the width its runs reach)."""
+    return int(_lib.load().cr_merge_runs_block_length())
+
+
+def merge_runs_block(X, Xv, width: int, key_type: str | None = None, out=None, perm=None,
+                     record: bool = False):
+    """The merge passes width, 2 width, ... up to merge_runs_block_length()
+    done inside shared memory, one chunk per CTA (width a power of two).
+    Returns (Y, Yv, perm); perm (the chunk permutation, int16 container of
+    uint16 indices) only with record=True or a perm buffer given."""
+    lib = _lib.load()
+    dev = _dev(X, Xv)
+    kt = _key_code(X, key_type)
+    vb = Xv.element_size() if Xv is not None else 0
+    if out is None:
+        Y = torch.empty_like(X)
+        Yv = torch.empty_like(Xv) if Xv is not None else None
+    else:
+        Y, Yv = out
+    if perm is None and record:
+        perm = torch.empty(X.numel(), dtype=torch.int16, device=dev)
+    _lib.check(lib.cr_merge_runs_block(kt, vb, _ptr(X), _ptr(Xv), X.numel(), int(width),
+                                       _ptr(Y), _ptr(Yv), _ptr(perm), _stream(dev)))
+    return Y, Yv, perm
+
+
+def merge_runs_block_backward_recorded(perm, gY, out=None):
+    """Payload gradient of a recorded merge_runs_block (no keys read)."""
+    lib = _lib.load()
+    dev = _dev(perm, gY)
+    gX = out if out is not None else torch.empty_like(gY)
+    _lib.check(lib.cr_merge_runs_block_backward_recorded(gY.element_size(), gY.numel(),
+                                                         _ptr(perm), _ptr(gY), _ptr(gX),
+                                                         _stream(dev)))
+    return gX
+
+
 class MergeSortPlan:
     """Buffers and (optionally) CUDA graphs for a stable merge sort of N keys
     with payloads.
@@ -632,14 +670,19 @@ class MergeSortPlan:
     With ``run`` given, the input's runs of ``run`` elements must already be
     sorted; with ``run=None`` the plan first sorts runs of
     sort_run_length() itself (run formation), so any input is accepted.
-    Pass p merges runs of width run * 2^p.
+    Then the runs are merged pairwise, width run, 2 run, 4 run, ..., in
+    stages: with ``record=True`` and a power-of-two ``run`` up to half of
+    merge_runs_block_length(), the widths below that length are merged in
+    one shared-memory stage (merge_runs_block), the rest by merge passes over
+    HBM (cr_merge_pass*).
 
-    The backward needs every pass's merge decisions.  With ``record=True``
-    (default) each forward pass records them (cr_merge_pass_record: its tile
-    table plus one bit per element; run formation: each run's permutation,
-    two bytes per element) and the backward routes gradients from those
-    records without reading keys; keys then ping-pong between two buffers.  With ``record=False`` the input keys of every pass are kept
-    ((passes + 1) * N key slots) and the backward re-merges them
+    The backward needs every stage's merge decisions.  With ``record=True``
+    (default) each forward stage records them (a merge pass: its tile table
+    plus one bit per element; run formation and the shared-memory stage:
+    their chunk permutation, two bytes per element) and the backward routes
+    gradients from those records without reading keys; keys then ping-pong
+    between two buffers.  With ``record=False`` the input keys of every pass
+    are kept ((passes + 1) * N key slots) and the backward re-merges them
     (cr_merge_pass_backward).  Payloads and gradients ping-pong between two
     buffers; with run formation the unsorted input keys are kept too.
     Forward and backward are each captured once into a CUDA graph
@@ -655,13 +698,19 @@ class MergeSortPlan:
         self.device = torch.device(device)
         self.key_type = key_type
         self.record = bool(record)
-        self.widths = []
+        R = merge_runs_block_length()
         w = self.run
+        self.stages = []            # ("block", width) or ("pass", width)
+        if (self.record and not self.form_runs and w < self.N and w >= 8 and w <= R // 2
+                and (w & (w - 1)) == 0):
+            self.stages.append(("block", w))
+            w = R
         while w < self.N:
-            self.widths.append(w)
+            self.stages.append(("pass", w))
             w *= 2
-        P = len(self.widths)
-        nkeys = 2 if self.record else P + 1
+        self.widths = [w for kind, w in self.stages if kind == "pass"]
+        S = len(self.stages)
+        nkeys = 2 if self.record else S + 1
         self.keys = [torch.empty(self.N, dtype=key_dtype, device=self.device)
                      for _ in range(nkeys)]
         self.vals = [torch.empty(self.N, dtype=val_dtype, device=self.device) for _ in range(2)]
@@ -672,11 +721,14 @@ class MergeSortPlan:
         vb = torch.empty(0, dtype=val_dtype).element_size()
         self.run_perm = (torch.empty(self.N, dtype=torch.int16, device=self.device)
                          if self.record and self.form_runs else None)
+        self.records = [None] * S       # per stage: PassRecord or block permutation
+        self.ws = None
         if self.record:
-            self.records = [new_pass_record(kt, vb, self.N, w, self.device) for w in self.widths]
-            self.ws = None
+            for i, (kind, w) in enumerate(self.stages):
+                self.records[i] = (new_pass_record(kt, vb, self.N, w, self.device)
+                                   if kind == "pass" else
+                                   torch.empty(self.N, dtype=torch.int16, device=self.device))
         else:
-            self.records = []
             need = max([merge_pass_workspace_bytes(kt, vb, self.N, w) for w in self.widths]
                        + [256])
             self.ws = _ws(need, self.device)
@@ -686,11 +738,12 @@ class MergeSortPlan:
 
     @property
     def passes(self) -> int:
-        return len(self.widths)
+        """Number of merge stages (shared-memory stage and HBM passes)."""
+        return len(self.stages)
 
-    def _key_buf(self, p: int) -> torch.Tensor:
-        """Input keys of pass p (p == passes: the sorted output)."""
-        return self.keys[p & 1] if self.record else self.keys[p]
+    def _key_buf(self, i: int) -> torch.Tensor:
+        """Input keys of stage i (i == passes: the sorted output)."""
+        return self.keys[i & 1] if self.record else self.keys[i]
 
     def _load(self, X, Xv):
         if self.form_runs:
@@ -700,35 +753,54 @@ class MergeSortPlan:
             self.keys[0].copy_(X)
             self.vals[0].copy_(Xv)
 
-    def _forward_body(self):
+    def run_formation(self):
         if self.form_runs and self.record:
             sort_runs_record(self.input_keys, self.vals[1], key_type=self.key_type,
                              out=(self.keys[0], self.vals[0]), perm=self.run_perm)
         elif self.form_runs:
             sort_runs(self.input_keys, self.vals[1], key_type=self.key_type,
                       out=(self.keys[0], self.vals[0]))
-        for p, w in enumerate(self.widths):
-            out = (self._key_buf(p + 1), self.vals[(p + 1) & 1])
-            if self.record:
-                merge_pass_record(self._key_buf(p), self.vals[p & 1], w, key_type=self.key_type,
-                                  out=out, record=self.records[p])
-            else:
-                merge_pass(self._key_buf(p), self.vals[p & 1], w, key_type=self.key_type,
-                           out=out, ws=self.ws)
 
-    def _backward_body(self):
-        for p in reversed(range(self.passes)):
-            src = self.grads[(p + 1) & 1]
-            if self.record:
-                merge_pass_backward_recorded(self.records[p], src, out=self.grads[p & 1])
-            else:
-                merge_pass_backward(self.keys[p], src, self.widths[p], key_type=self.key_type,
-                                    out=self.grads[p & 1], ws=self.ws)
+    def run_stage(self, i: int):
+        """Forward of stage i: keys/payloads of parity i -> parity i + 1."""
+        kind, w = self.stages[i]
+        src = (self._key_buf(i), self.vals[i & 1])
+        out = (self._key_buf(i + 1), self.vals[(i + 1) & 1])
+        if kind == "block":
+            merge_runs_block(*src, w, key_type=self.key_type, out=out, perm=self.records[i])
+        elif self.record:
+            merge_pass_record(*src, w, key_type=self.key_type, out=out, record=self.records[i])
+        else:
+            merge_pass(*src, w, key_type=self.key_type, out=out, ws=self.ws)
+
+    def run_stage_backward(self, i: int):
+        """Backward of stage i: gradients of parity i + 1 -> parity i."""
+        kind, w = self.stages[i]
+        src, dst = self.grads[(i + 1) & 1], self.grads[i & 1]
+        if kind == "block":
+            merge_runs_block_backward_recorded(self.records[i], src, out=dst)
+        elif self.record:
+            merge_pass_backward_recorded(self.records[i], src, out=dst)
+        else:
+            merge_pass_backward(self.keys[i], src, w, key_type=self.key_type, out=dst,
+                                ws=self.ws)
+
+    def run_formation_backward(self):
         if self.form_runs and self.record:
             sort_runs_backward_recorded(self.run_perm, self.grads[0], out=self.grads[1])
         elif self.form_runs:
             sort_runs_backward(self.input_keys, self.grads[0], key_type=self.key_type,
                                out=self.grads[1])
+
+    def _forward_body(self):
+        self.run_formation()
+        for i in range(len(self.stages)):
+            self.run_stage(i)
+
+    def _backward_body(self):
+        for i in reversed(range(len(self.stages))):
+            self.run_stage_backward(i)
+        self.run_formation_backward()
 
     def _grad_out(self):
         return self.grads[1] if self.form_runs else self.grads[0]

@@ -1,0 +1,229 @@
+// cr_block.cu -- the first passes of a bottom-up merge sort whose runs are
+// short, merged inside shared memory: each CTA loads a chunk of R = 4096
+// consecutive elements (R / w runs of a power-of-two width w <= R/2), runs
+// the passes w -> 2w -> ... -> R in shared memory, and stores the chunk once,
+// instead of one pass over HBM per width.  Same result as those passes
+// (stable merges of neighbouring runs; ties take the left run).
+//
+// Work split: thread t of NT owns the outputs [floor(t R / NT),
+// floor((t+1) R / NT)) of every round -- 7 or 8 of them, at a stride of
+// about 7.1 elements, so the shared-memory writes of a warp fall in distinct
+// banks even though R is a power of two.  A thread co-ranks the start of
+// its range inside its pair of runs (the split of Lemma 1, binary lifting)
+// and merges serially; if its range crosses into the next pair it starts
+// over there.  Keys carry their 16-bit index in the chunk; the payloads are
+// gathered once at the end through those indices, and with `perm` the
+// indices are written out, so that the backward routes gradients through
+// them without keys.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/corank.h"
+#include "cr_launch.cuh"
+#include "cr_merge.cuh"
+
+namespace cr {
+namespace {
+
+constexpr int kBlockR = 4096;
+constexpr int kBlockNT = 576;
+constexpr int kBlockMaxOwn = (kBlockR + kBlockNT - 1) / kBlockNT + 1;   // 8
+
+template <class K, int VB>
+struct BlockLayout {
+    static constexpr size_t KEYS = align_up_sz(size_t(kBlockR + 1) * sizeof(K), 128);
+    static constexpr size_t INDEX = align_up_sz(size_t(kBlockR + 1) * 2, 128);
+    static constexpr size_t VALS = VB ? align_up_sz(size_t(kBlockR) * VB, 128) : 0;
+    static constexpr size_t TOTAL = 2 * (KEYS + INDEX) + VALS;
+};
+
+template <class K, int VB, bool REC>
+__global__ void __launch_bounds__(kBlockNT) merge_runs_block_kernel(
+    const K* __restrict__ X, const void* __restrict__ Xv, int64_t N, int w0, K* __restrict__ Y,
+    void* __restrict__ Yv, uint16_t* __restrict__ perm, int order) {
+    using L = BlockLayout<K, VB>;
+    using V = typename VBits<VB>::T;
+    extern __shared__ __align__(128) unsigned char smem[];
+    K* const sk0 = reinterpret_cast<K*>(smem);
+    K* const sk1 = reinterpret_cast<K*>(smem + L::KEYS);
+    uint16_t* const si0 = reinterpret_cast<uint16_t*>(smem + 2 * L::KEYS);
+    uint16_t* const si1 = reinterpret_cast<uint16_t*>(smem + 2 * L::KEYS + L::INDEX);
+    V* const sv = reinterpret_cast<V*>(smem + 2 * (L::KEYS + L::INDEX));
+
+    const int tid = threadIdx.x;
+    const int64_t base = int64_t(blockIdx.x) * kBlockR;
+    const int len = int(N - base < kBlockR ? N - base : kBlockR);
+
+    for (int x = tid; x < len; x += kBlockNT) {
+        sk0[x] = order_key(X[base + x], order);
+        si0[x] = uint16_t(x);
+        if constexpr (VB != 0) sv[x] = static_cast<const V*>(Xv)[base + x];
+    }
+    __syncthreads();
+
+    const int own0 = int((int64_t(tid) * kBlockR) / kBlockNT);
+    const int own1 = int((int64_t(tid + 1) * kBlockR) / kBlockNT);
+    const int o0 = own0 < len ? own0 : len;
+    const int o1 = own1 < len ? own1 : len;
+
+    int cur = 0;
+    for (int w = w0; w < len; w *= 2) {
+        const K* ik = cur ? sk1 : sk0;
+        const uint16_t* ii = cur ? si1 : si0;
+        K* ok = cur ? sk0 : sk1;
+        uint16_t* oi = cur ? si0 : si1;
+        int x = o0;
+#pragma unroll 1
+        for (int seg = 0; seg < kBlockMaxOwn && x < o1; ++seg) {   // at most two pairs
+            const int ps = (x / (2 * w)) * (2 * w);             // pair start
+            const int alen = min(w, len - ps);
+            const int blen = max(0, min(w, len - ps - alen));
+            const int pe = ps + alen + blen;
+            const int bs = ps + alen;
+            const int dd[1] = {x - ps};
+            int jj[1];
+            split_in_tile<Log2Ceil<kBlockR + 1>::v>(ik + ps, alen, ik + bs, blen, dd, jj);
+            int j = jj[0], k = dd[0] - j;
+            K a = ik[ps + j];      // at most ik[len] <= ik[R]: inside the slack
+            K b = ik[bs + k];
+            const int stop = o1 < pe ? o1 : pe;
+#pragma unroll 1
+            for (; x < stop; ++x) {
+                const bool takeA = (k >= blen) || (j < alen && !(b < a));
+                const int src = takeA ? ps + j : bs + k;
+                ok[x] = takeA ? a : b;
+                oi[x] = ii[src];
+                j += takeA ? 1 : 0;
+                k += takeA ? 0 : 1;
+                const K nx = ik[takeA ? ps + j : bs + k];   // never taken when past a run
+                a = takeA ? nx : a;
+                b = takeA ? b : nx;
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    const K* fk = cur ? sk1 : sk0;
+    const uint16_t* fi = cur ? si1 : si0;
+    for (int x = tid; x < len; x += kBlockNT) {
+        Y[base + x] = order_key_inverse(fk[x], order);
+        if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[fi[x]];
+        if constexpr (REC) perm[base + x] = fi[x];
+    }
+}
+
+template <class K, int VB, bool REC>
+cudaError_t launch_block(const void* X, const void* Xv, int64_t N, int w0, void* Y, void* Yv,
+                         uint16_t* perm, int order, cudaStream_t st) {
+    using L = BlockLayout<K, VB>;
+    auto kern = merge_runs_block_kernel<K, VB, REC>;
+    static std::once_flag once[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [&] {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(L::TOTAL));
+    });
+    if (e != cudaSuccess) return e;
+    const int64_t chunks = (N + kBlockR - 1) / kBlockR;
+    kern<<<unsigned(chunks), kBlockNT, L::TOTAL, st>>>(static_cast<const K*>(X), Xv, N, w0,
+                                                        static_cast<K*>(Y), Yv, perm, order);
+    return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t block_dispatch(int vb, const void* X, const void* Xv, int64_t N, int w0, void* Y,
+                           void* Yv, uint16_t* perm, int order, cudaStream_t st) {
+    const bool rec = perm != nullptr;
+    switch (vb * 2 + (rec ? 1 : 0)) {
+        case 0: return launch_block<K, 0, false>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 8: return launch_block<K, 4, false>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 9: return launch_block<K, 4, true>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 16: return launch_block<K, 8, false>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 17: return launch_block<K, 8, true>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool overlaps(const void* p, int64_t pb, const void* q, int64_t qb) {
+    if (pb <= 0 || qb <= 0) return false;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p), b = reinterpret_cast<uintptr_t>(q);
+    return a < b + uintptr_t(qb) && b < a + uintptr_t(pb);
+}
+
+}  // namespace
+
+// Backward of a recorded block: the chunk permutation routes gY to gX
+// (cr_route.cu, shared with run formation's recorded backward).
+cudaError_t chunk_route_recorded(int vb, int64_t N, int64_t chunk, const uint16_t* perm,
+                                 const void* gY, void* gX, cudaStream_t st);
+
+}  // namespace cr
+
+extern "C" int64_t cr_merge_runs_block_length(void) { return cr::kBlockR; }
+
+extern "C" cr_status cr_merge_runs_block(int key_type, int val_bytes, const void* X,
+                                         const void* Xv, int64_t N, int64_t width, void* Y,
+                                         void* Yv, uint16_t* perm, cr_stream stream) {
+    const int ks = cr::key_type_bytes(key_type);
+    if (ks == 0 || N < 0) return CR_EINVAL;
+    if (!(val_bytes == 0 || val_bytes == 4 || val_bytes == 8)) return CR_EINVAL;
+    if (perm != nullptr && val_bytes == 0) return CR_EINVAL;
+    if (width < 8 || width > cr::kBlockR / 2 || (width & (width - 1)) != 0) return CR_EINVAL;
+    if (N == 0) return CR_OK;
+    const void* arrs[5] = {X, Y, val_bytes ? Xv : nullptr, val_bytes ? Yv : nullptr, perm};
+    const bool need[5] = {true, true, val_bytes != 0, val_bytes != 0, perm != nullptr};
+    for (int i = 0; i < 5; ++i) {
+        if (!need[i]) continue;
+        if (arrs[i] == nullptr) return CR_EINVAL;
+        if (reinterpret_cast<uintptr_t>(arrs[i]) & 15u) return CR_EALIGN;
+    }
+    const int64_t kb = N * ks, vbb = N * val_bytes, pb = perm ? N * 2 : 0;
+    if (cr::overlaps(Y, kb, X, kb) || (val_bytes && cr::overlaps(Y, kb, Xv, vbb)) ||
+        (val_bytes && cr::overlaps(Yv, vbb, X, kb)) ||
+        (val_bytes && cr::overlaps(Yv, vbb, Xv, vbb)) || (val_bytes && cr::overlaps(Yv, vbb, Y, kb)) ||
+        (perm && (cr::overlaps(perm, pb, X, kb) || cr::overlaps(perm, pb, Y, kb) ||
+                  (val_bytes && (cr::overlaps(perm, pb, Xv, vbb) ||
+                                 cr::overlaps(perm, pb, Yv, vbb))))))
+        return CR_EALIAS;
+    const int order = cr::key_type_order(key_type);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int w0 = int(width);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (cr::key_base(key_type)) {
+        case CR_KEY_I32:
+        case CR_KEY_F32:
+            e = cr::block_dispatch<int32_t>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
+            break;
+        case CR_KEY_U32:
+            e = cr::block_dispatch<uint32_t>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
+            break;
+        case CR_KEY_I64:
+        case CR_KEY_F64:
+            e = cr::block_dispatch<int64_t>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
+            break;
+        default:
+            e = cr::block_dispatch<uint64_t>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
+            break;
+    }
+    return e == cudaSuccess ? CR_OK : CR_ECUDA;
+}
+
+extern "C" cr_status cr_merge_runs_block_backward_recorded(int val_bytes, int64_t N,
+                                                           const uint16_t* perm, const void* gY,
+                                                           void* gX, cr_stream stream) {
+    if (!(val_bytes == 4 || val_bytes == 8) || N < 0) return CR_EINVAL;
+    if (N == 0) return CR_OK;
+    if (!perm || !gY || !gX) return CR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(perm) | reinterpret_cast<uintptr_t>(gY) |
+         reinterpret_cast<uintptr_t>(gX)) & 15u)
+        return CR_EALIGN;
+    const int64_t b = N * val_bytes;
+    if (cr::overlaps(gX, b, gY, b) || cr::overlaps(gX, b, perm, N * 2)) return CR_EALIAS;
+    const cudaError_t e = cr::chunk_route_recorded(val_bytes, N, cr::kBlockR, perm, gY, gX,
+                                                   static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CR_OK : CR_ECUDA;
+}

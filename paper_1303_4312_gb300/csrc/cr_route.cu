@@ -149,21 +149,22 @@ __global__ void __launch_bounds__(kRouteThreads) route_recorded_kernel(
     }
 }
 
-// Backward of a recorded run formation: one CTA per run of kSortRun
-// elements scatters the run's gradients through its permutation in shared
-// memory (gX[perm[x]] = gY[x]) and stores them coalesced.  Entries outside
-// the run are skipped (the permutation comes from the forward).
+// Backward of a recorded run formation or merge block: one CTA per chunk of
+// `chunk` elements scatters the chunk's gradients through its permutation
+// in shared memory (gX[perm[x]] = gY[x]) and stores them coalesced.  Entries
+// outside the chunk are skipped (the permutation comes from the forward).
 constexpr int kSortRouteThreads = 256;
+constexpr int64_t kRouteMaxChunk = 4096;
 
 template <int VB>
 __global__ void __launch_bounds__(kSortRouteThreads) sort_route_kernel(
-    int64_t N, const uint16_t* __restrict__ perm, const void* __restrict__ gY,
+    int64_t N, int64_t chunk, const uint16_t* __restrict__ perm, const void* __restrict__ gY,
     void* __restrict__ gX) {
     using V = typename VBits<VB>::T;
     extern __shared__ __align__(16) unsigned char route_smem[];
     V* s = reinterpret_cast<V*>(route_smem);
-    const int64_t base = int64_t(blockIdx.x) * kSortRun;
-    const int len = int(N - base < kSortRun ? N - base : kSortRun);
+    const int64_t base = int64_t(blockIdx.x) * chunk;
+    const int len = int(N - base < chunk ? N - base : chunk);
     const V* gy = static_cast<const V*>(gY) + base;
     for (int x = threadIdx.x; x < len; x += kSortRouteThreads) {
         const int p = perm[base + x];
@@ -176,19 +177,27 @@ __global__ void __launch_bounds__(kSortRouteThreads) sort_route_kernel(
 
 }  // namespace
 
-cudaError_t sort_route_recorded(int vb, int64_t N, const uint16_t* perm, const void* gY, void* gX,
-                                cudaStream_t st) {
+cudaError_t chunk_route_recorded(int vb, int64_t N, int64_t chunk, const uint16_t* perm,
+                                 const void* gY, void* gX, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
-    const int64_t runs = (N + kSortRun - 1) / kSortRun;
+    if (chunk <= 0 || chunk > kRouteMaxChunk) return cudaErrorInvalidValue;
+    const int64_t runs = (N + chunk - 1) / chunk;
     if (runs > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const size_t smem = size_t(kSortRun) * size_t(vb);   // 14 KB at most
+    const size_t smem = size_t(chunk) * size_t(vb);   // 32 KB at most
     if (vb == 4)
-        sort_route_kernel<4><<<unsigned(runs), kSortRouteThreads, smem, st>>>(N, perm, gY, gX);
+        sort_route_kernel<4><<<unsigned(runs), kSortRouteThreads, smem, st>>>(N, chunk, perm, gY,
+                                                                             gX);
     else if (vb == 8)
-        sort_route_kernel<8><<<unsigned(runs), kSortRouteThreads, smem, st>>>(N, perm, gY, gX);
+        sort_route_kernel<8><<<unsigned(runs), kSortRouteThreads, smem, st>>>(N, chunk, perm, gY,
+                                                                             gX);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
+}
+
+cudaError_t sort_route_recorded(int vb, int64_t N, const uint16_t* perm, const void* gY, void* gX,
+                                cudaStream_t st) {
+    return chunk_route_recorded(vb, N, kSortRun, perm, gY, gX, st);
 }
 
 cudaError_t route_recorded(int vb, void* ws, const uint32_t* flags, int64_t flag_words, int64_t N,

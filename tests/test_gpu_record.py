@@ -197,3 +197,42 @@ def test_recorded_run_formation(dt, vb):
             assert same_bits(host(gX, vdt), wg), N
             assert same_bits(host(Y2, dt), wy) and same_bits(host(Yv2, vdt), wyv), N
             assert same_bits(host(gX2, vdt), wg), N
+
+
+@pytest.mark.parametrize("dt", KEY_DTYPES)
+@pytest.mark.parametrize("vb", [0, 4, 8])
+def test_merge_runs_block(dt, vb):
+    """The shared-memory stage equals the chain of merge passes it replaces
+    (oracle merge_pass, width by width up to the chunk length), keys and
+    payloads bit for bit; its recorded permutation routes gradients like the
+    passes' composed permutation."""
+    rng = np.random.default_rng(350 + vb)
+    R = cr.merge_runs_block_length()
+    kt = key_type(np.empty(0, dt))
+    for N, w in [(R, 1024), (5 * R + 333, 8), (100003, 1024), (1, 64), (3 * R, 2048),
+                 (R - 1, 512)]:
+        X = run_sorted_keys(rng, N, w, dt, 7 if vb else None)
+        Xv = rng.standard_normal(N).astype(VAL_DTYPES.get(vb, np.float32))
+        want, wv, src = X.copy(), Xv.copy(), np.arange(N)
+        ww = w
+        while ww < R and ww < N:
+            # chunks of R are independent: merge pass by pass inside each
+            want, wv, s = oracle.merge_pass(want, wv, ww)
+            src = src[s]
+            ww *= 2
+        # merge_pass runs over the whole array; restricted to widths < R its
+        # pairs never cross a chunk boundary, so it equals the chunked stage
+        Y, Yv, perm = cr.merge_runs_block(dev(X), dev(Xv) if vb else None, w, key_type=kt,
+                                          record=vb != 0)
+        torch.cuda.synchronize()
+        assert same_bits(host(Y, dt), want), (N, w)
+        if vb:
+            assert same_bits(host(Yv, Xv.dtype), wv), (N, w)
+            base = (np.arange(N) // R) * R
+            assert np.array_equal(host(perm, np.uint16).astype(np.int64) + base, src), (N, w)
+            gY = rng.standard_normal(N).astype(Xv.dtype)
+            gX = cr.merge_runs_block_backward_recorded(perm, dev(gY))
+            torch.cuda.synchronize()
+            g = np.empty_like(gY)
+            g[src] = gY
+            assert same_bits(host(gX, Xv.dtype), g), (N, w)
