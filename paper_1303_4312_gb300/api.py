@@ -236,9 +236,15 @@ class HostMerger:
     the three per pair, so the output copy of one pair overlaps the input
     copy of the next (the two copy directions run concurrently) and both
     overlap the merges.  Device buffers and workspaces are allocated once and
-    reused by every ``run``.  The work joins the caller's current stream at
-    both ends, so events recorded on it around ``run`` time the whole
-    pipeline.
+    reused by every ``run``; events order each buffer's reuse across calls,
+    so the input copies of one call overlap the output copies of the
+    previous one.  The caller's current stream waits at the end of ``run``
+    for every output copy, so events recorded on it around a series of
+    ``run`` calls time the whole pipeline and a synchronisation of it makes
+    the outputs readable.  The input copies do not wait for the caller's
+    earlier work: host inputs are read asynchronously, so the caller must not
+    overwrite them before its stream has passed the end of the ``run`` that
+    reads them.
     """
 
     def __init__(self, shapes, device="cuda"):
@@ -264,10 +270,6 @@ class HostMerger:
         """host_pairs[i] = (A, B) pinned CPU tensors; host_outs[i] receives C."""
         lib = _lib.load()
         caller = torch.cuda.current_stream(self.dev)
-        start = torch.cuda.Event()
-        start.record(caller)
-        for st in (self.s_in, self.s_comp, self.s_out):
-            st.wait_event(start)
         done = []
         for it, (hA, hB), hC in zip(self.items, host_pairs, host_outs):
             if hA.numel() != it["m"] or hB.numel() != it["n"] or hC.numel() != it["m"] + it["n"]:
