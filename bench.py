@@ -72,6 +72,9 @@ def parse_args():
                             "partition_variants", "orders"],
                    help="the default is the headline workload; the others measure the "
                         "remaining rows of the path (one JSON line each)")
+    p.add_argument("--batched-pairs", type=int, default=8192,
+                   help="segment pairs of the batched workload (8192 as specified; 24576 "
+                        "reaches about 2^30 elements)")
     p.add_argument("--tile-shape", type=int, default=None,
                    help="force tile shape S (cr_tile_shape_info) for every key type and "
                         "payload width it fits, instead of the tuned table")
@@ -685,7 +688,7 @@ def run_row(args):
                       combos=[("uint32+f32", 1, 4)])
 
     if args.workload == "batched":
-        a_off, b_off, A, Av, B, Bv = W.t_batched_i32_f32(device=dev)
+        a_off, b_off, A, Av, B, Bv = W.t_batched_i32_f32(device=dev, nseg=args.batched_pairs)
         ao = torch.from_numpy(a_off).to(dev)
         bo = torch.from_numpy(b_off).to(dev)
         at, bt = A.numel(), B.numel()
@@ -718,7 +721,8 @@ def run_row(args):
         api.workspace_status(ws)
         tot = timer.totals()
         N = at + bt
-        return finish(tot, {"fwd": 16 * N, "bwd": 12 * N}, "batched_i32_f32", N,
+        name = "batched_i32_f32" if nseg == 8192 else f"batched_i32_f32_{nseg}_pairs"
+        return finish(tot, {"fwd": 16 * N, "bwd": 12 * N}, name, N,
                       {"segments": nseg, "note": "fwd/bwd include the segment scan and "
                        "partition launches (3 kernels each)"},
                       combos=[("int32+f32", 0, 4)])

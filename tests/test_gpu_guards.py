@@ -221,3 +221,25 @@ def test_kv_autograd_finite_differences():
         lp = (cr.merge_kv(Ak, Av.detach(), Bk, bp, key_type="i32")[1] * w).sum()
         lm = (cr.merge_kv(Ak, Av.detach(), Bk, bm, key_type="i32")[1] * w).sum()
         assert abs(float((lp - lm) / (2 * h)) - float(Bv.grad[i])) <= 1e-9
+
+
+def test_batched_many_segments_scan_carry():
+    """More segments than one pass of the segment scan covers (8192 per
+    pass): the carried prefix across passes, empty segments included."""
+    rng = np.random.default_rng(605)
+    nseg = 20011
+    ms = rng.integers(0, 40, nseg)
+    ns = rng.integers(0, 40, nseg)
+    ms[::7] = 0
+    ns[::11] = 0
+    a_off = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+    b_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    A = np.concatenate([np.sort(rng.integers(0, 5, x)) for x in ms]).astype(np.int32)
+    B = np.concatenate([np.sort(rng.integers(0, 5, x)) for x in ns]).astype(np.int32)
+    Av = rng.standard_normal(len(A)).astype(np.float32)
+    Bv = rng.standard_normal(len(B)).astype(np.float32)
+    Ck, Cv = cr.batched_merge_kv(torch.from_numpy(a_off).cuda(), torch.from_numpy(b_off).cuda(),
+                                 dev(A), dev(Av), dev(B), dev(Bv))
+    torch.cuda.synchronize()
+    wk, wv = oracle.batched_merge_kv(a_off, b_off, A, Av, B, Bv)
+    assert same_bits(host(Ck, np.int32), wk) and same_bits(host(Cv, np.float32), wv)
