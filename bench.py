@@ -795,7 +795,8 @@ def run_row(args):
             per_pass[mode] = pp
             del plan
             torch.cuda.empty_cache()
-        # unsorted input: run formation (sort_runs) then the recorded chain
+        # unsorted input: the recorded chain from runs of one element (its
+        # shared-memory stage sorts every chunk of 4096, then HBM passes)
         Xu, Xuv = W.t_sort_u64_f32(device=dev, shift=args.shift, run=None)
         plan = api.MergeSortPlan(N, None, Xu.dtype, Xuv.dtype, dev, key_type="u64", graph=True)
         plan.forward(Xu, Xuv)
@@ -816,7 +817,8 @@ def run_row(args):
                 timer.marks.append((None, timer.marks[-1][1]))
         torch.cuda.synchronize()
         un = {lb: round(ms / K, 4) for lb, ms in timer.totals().items()}
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        stages_un = [f"{kd}:{w}" for kd, w in plan.stages]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         Yk, Yv = torch.empty_like(Xu), torch.empty_like(Xuv)
         gXr = torch.empty_like(gY)
         perm = torch.empty(N, dtype=torch.int16, device=dev)
@@ -830,8 +832,12 @@ def run_row(args):
             ev[3].record(stream)
             api.sort_runs_backward_recorded(perm, gY, out=gXr)
             ev[4].record(stream)
+            api.merge_runs_block(Xu, Xuv, 1, key_type="u64", out=(Yk, Yv), perm=perm)
+            ev[5].record(stream)
+            api.merge_runs_block_backward_recorded(perm, gY, out=gXr)
+            ev[6].record(stream)
         torch.cuda.synchronize()
-        tms = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+        tms = [ev[i].elapsed_time(ev[i + 1]) for i in range(6)]
 
         def row(ms, bpe):
             gbs = bpe * N / (ms / 1e3) / 1e9
@@ -839,9 +845,11 @@ def run_row(args):
         # bytes per element: keys + payloads in and out; backward replay reads
         # keys and gY, writes gX; the recorded forms add / read the 2-byte
         # permutation instead of the keys
-        unsorted = {"run": api.sort_run_length(), "passes": plan.passes,
+        unsorted = {"stages": stages_un, "passes": plan.passes,
                     "fwd_graph_ms": un["fwd_graph"], "bwd_graph_ms": un["bwd_graph"],
                     "elements_per_s": N / ((un["fwd_graph"] + un["bwd_graph"]) / 1e3),
+                    "block_form": row(tms[4], 26), "block_form_backward": row(tms[5], 10),
+                    "sort_runs_run": api.sort_run_length(),
                     "sort_runs": row(tms[0], 24), "sort_runs_backward": row(tms[1], 16),
                     "sort_runs_record": row(tms[2], 26),
                     "sort_runs_backward_recorded": row(tms[3], 10)}

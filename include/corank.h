@@ -369,11 +369,14 @@ cr_status cr_workspace_status(const void* ws, cr_stream stream);
 /* ------------------------------------------------------------------------
  * Merge block: the first passes of a merge sort done inside shared memory
  * (the paper has no counterpart; same result as those cr_merge_pass calls).
- * X[0, N) holds sorted runs of `width` (a power of two, 8 <= width <=
+ * X[0, N) holds sorted runs of `width` (a power of two, 1 <= width <=
  * cr_merge_runs_block_length() / 2); every chunk of
  * cr_merge_runs_block_length() elements (4096; the last chunk may be
  * shorter) is merged into one sorted run of Y, i.e. the passes width, 2 width,
  * ..., up to the chunk length, in one read and one write of the arrays.
+ * With width 1 (runs of one element: any input) this is run formation: the
+ * chunk is sorted stably (ties keep input order); widths below 8 start from
+ * groups of 8 sorted in registers.
  * val_bytes 0, 4 or 8.  With perm (uint16, N entries, 4 or 8 byte payloads
  * only) the chunk permutation is written: perm[base + x] = index inside the
  * chunk of the input element that became output x; its backward

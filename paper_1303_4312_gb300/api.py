@@ -635,9 +635,10 @@ def merge_runs_block_length() -> int:
 def merge_runs_block(X, Xv, width: int, key_type: str | None = None, out=None, perm=None,
                      record: bool = False):
     """The merge passes width, 2 width, ... up to merge_runs_block_length()
-    done inside shared memory, one chunk per CTA (width a power of two).
-    Returns (Y, Yv, perm); perm (the chunk permutation, int16 container of
-    uint16 indices) only with record=True or a perm buffer given."""
+    done inside shared memory, one chunk per CTA (width a power of two; width
+    1 sorts every chunk of any input stably).  Returns (Y, Yv, perm); perm
+    (the chunk permutation, int16 container of uint16 indices) only with
+    record=True or a perm buffer given."""
     lib = _lib.load()
     dev = _dev(X, Xv)
     kt = _key_code(X, key_type)
@@ -670,18 +671,20 @@ class MergeSortPlan:
     with payloads.
 
     With ``run`` given, the input's runs of ``run`` elements must already be
-    sorted; with ``run=None`` the plan first sorts runs of
-    sort_run_length() itself (run formation), so any input is accepted.
-    Then the runs are merged pairwise, width run, 2 run, 4 run, ..., in
-    stages: with ``record=True`` and a power-of-two ``run`` up to half of
+    sorted; with ``run=None`` any input is accepted (runs of one element).
+    The runs are merged pairwise, width run, 2 run, 4 run, ..., in stages:
+    with ``record=True`` and a power-of-two ``run`` up to half of
     merge_runs_block_length(), the widths below that length are merged in
-    one shared-memory stage (merge_runs_block), the rest by merge passes over
-    HBM (cr_merge_pass*).
+    one shared-memory stage (merge_runs_block; from unsorted input it sorts
+    every chunk of that length), the rest by merge passes over HBM
+    (cr_merge_pass*).  With ``record=False`` unsorted input is first sorted
+    into runs of sort_run_length() (run formation, cr_sort_runs), whose
+    backward replays that sort.
 
     The backward needs every stage's merge decisions.  With ``record=True``
     (default) each forward stage records them (a merge pass: its tile table
-    plus one bit per element; run formation and the shared-memory stage:
-    their chunk permutation, two bytes per element) and the backward routes
+    plus one bit per element; the shared-memory stage: its chunk
+    permutation, two bytes per element) and the backward routes
     gradients from those records without reading keys; keys then ping-pong
     between two buffers.  With ``record=False`` the input keys of every pass
     are kept ((passes + 1) * N key slots) and the backward re-merges them
@@ -695,15 +698,19 @@ class MergeSortPlan:
     def __init__(self, N: int, run: int | None, key_dtype, val_dtype, device="cuda",
                  key_type: str | None = None, graph: bool = True, record: bool = True):
         self.N = int(N)
-        self.form_runs = run is None
-        self.run = sort_run_length() if run is None else int(run)
+        self.record = bool(record)
+        # run formation by cr_sort_runs (recompute form only): its own step
+        self.form_runs = run is None and not self.record
+        if run is None:
+            self.run = sort_run_length() if self.form_runs else 1
+        else:
+            self.run = int(run)
         self.device = torch.device(device)
         self.key_type = key_type
-        self.record = bool(record)
         R = merge_runs_block_length()
         w = self.run
         self.stages = []            # ("block", width) or ("pass", width)
-        if (self.record and not self.form_runs and w < self.N and w >= 8 and w <= R // 2
+        if (self.record and w < self.N and w >= 1 and w <= R // 2
                 and (w & (w - 1)) == 0):
             self.stages.append(("block", w))
             w = R
@@ -721,8 +728,6 @@ class MergeSortPlan:
                            if self.form_runs else None)
         kt = key_type or _DTYPE_KEY[key_dtype]
         vb = torch.empty(0, dtype=val_dtype).element_size()
-        self.run_perm = (torch.empty(self.N, dtype=torch.int16, device=self.device)
-                         if self.record and self.form_runs else None)
         self.records = [None] * S       # per stage: PassRecord or block permutation
         self.ws = None
         if self.record:
@@ -756,10 +761,9 @@ class MergeSortPlan:
             self.vals[0].copy_(Xv)
 
     def run_formation(self):
-        if self.form_runs and self.record:
-            sort_runs_record(self.input_keys, self.vals[1], key_type=self.key_type,
-                             out=(self.keys[0], self.vals[0]), perm=self.run_perm)
-        elif self.form_runs:
+        """Recompute form with unsorted input: sort runs of sort_run_length()
+        (the recorded form forms runs in its shared-memory stage)."""
+        if self.form_runs:
             sort_runs(self.input_keys, self.vals[1], key_type=self.key_type,
                       out=(self.keys[0], self.vals[0]))
 
@@ -788,9 +792,7 @@ class MergeSortPlan:
                                 ws=self.ws)
 
     def run_formation_backward(self):
-        if self.form_runs and self.record:
-            sort_runs_backward_recorded(self.run_perm, self.grads[0], out=self.grads[1])
-        elif self.form_runs:
+        if self.form_runs:
             sort_runs_backward(self.input_keys, self.grads[0], key_type=self.key_type,
                                out=self.grads[1])
 

@@ -5,16 +5,25 @@
 // instead of one pass over HBM per width.  Same result as those passes
 // (stable merges of neighbouring runs; ties take the left run).
 //
-// Work split: thread t of NT owns the outputs [floor(t R / NT),
-// floor((t+1) R / NT)) of every round -- 7 or 8 of them, at a stride of
-// about 7.1 elements, so the shared-memory writes of a warp fall in distinct
-// banks even though R is a power of two.  A thread co-ranks the start of
-// its range inside its pair of runs (the split of Lemma 1, binary lifting)
-// and merges serially; if its range crosses into the next pair it starts
-// over there.  Keys carry their 16-bit index in the chunk; the payloads are
-// gathered once at the end through those indices, and with `perm` the
-// indices are written out, so that the backward routes gradients through
-// them without keys.
+// Work split: thread t of NT = R / IPT owns the outputs [t IPT, (t+1) IPT)
+// of every round (IPT = 8); since 2w is a multiple of IPT they lie in one
+// pair of runs.  A thread co-ranks the start of its range inside its pair
+// (the split of Lemma 1, binary lifting) and merges IPT steps serially.  Keys
+// carry their 16-bit index in the chunk; the payloads are gathered once at
+// the end through those indices, and with `perm` the indices are written
+// out, so that the backward routes gradients through them without keys.
+//
+// Shared-memory layout: element i of a key array sits at slot
+// i + i / 16 (8-byte keys) or i + i / 32 (4-byte keys), element i of an index
+// array at i + 2 (i / 64).  With those gaps the IPT-strided writes of a warp
+// (and its linear loads and stores) fall in distinct banks, although the
+// stride IPT and the chunk length are powers of two.
+//
+// Run formation (w < IPT, FORM): every thread first sorts its own group of
+// IPT consecutive elements stably in registers (odd-even transposition,
+// swaps only on strictly smaller), which equals the merges of widths
+// w .. IPT/2 (a stable merge's result is unique), and the rounds start at
+// IPT; with w = 1 this sorts any input into sorted runs of R.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -27,23 +36,54 @@ namespace cr {
 namespace {
 
 constexpr int kBlockR = 4096;
-constexpr int kBlockNT = 576;
-constexpr int kBlockMaxOwn = (kBlockR + kBlockNT - 1) / kBlockNT + 1;   // 8
+constexpr int kBlockIPT = 8;
+constexpr int kBlockNT = kBlockR / kBlockIPT;   // 512
+constexpr int kBlockMinWidth = kBlockIPT;       // narrowest merge round: 2w multiple of IPT
+
+template <class K>
+struct BlockSlots {
+    static constexpr int SHIFT = sizeof(K) == 8 ? 4 : 5;
+    static __device__ __forceinline__ int key(int i) { return i + (i >> SHIFT); }
+    static __device__ __forceinline__ int idx(int i) { return i + ((i >> 6) << 1); }
+    // slot of element R included: a merge step may read one past its pair
+    static constexpr int KEYS = kBlockR + (kBlockR >> SHIFT) + 1;
+    static constexpr int IDX = kBlockR + ((kBlockR >> 6) << 1) + 1;
+};
 
 template <class K, int VB>
 struct BlockLayout {
-    static constexpr size_t KEYS = align_up_sz(size_t(kBlockR + 1) * sizeof(K), 128);
-    static constexpr size_t INDEX = align_up_sz(size_t(kBlockR + 1) * 2, 128);
+    using S = BlockSlots<K>;
+    static constexpr size_t KEYS = align_up_sz(size_t(S::KEYS) * sizeof(K), 128);
+    static constexpr size_t INDEX = align_up_sz(size_t(S::IDX) * 2, 128);
     static constexpr size_t VALS = VB ? align_up_sz(size_t(kBlockR) * VB, 128) : 0;
     static constexpr size_t TOTAL = 2 * (KEYS + INDEX) + VALS;
+    static_assert(TOTAL <= 232448, "chunk does not fit shared memory");
 };
 
-template <class K, int VB, bool REC>
-__global__ void __launch_bounds__(kBlockNT) merge_runs_block_kernel(
+// Largest j in [max(0, d - blen), min(d, alen)] with A[j-1] <= B[d-j]
+// (Lemma 1's first condition; A = s[pa ..], B = s[pb ..] in logical
+// indices), by binary lifting over LOG steps.
+template <class K, int LOG>
+__device__ __forceinline__ int split_pair(const K* s, int pa, int alen, int pb, int blen, int d) {
+    using S = BlockSlots<K>;
+    int pos = d - blen > 0 ? d - blen : 0;
+    const int hi = d < alen ? d : alen;
+#pragma unroll
+    for (int step = 1 << (LOG - 1); step > 0; step >>= 1) {
+        const int np = pos + step;
+        if (np <= hi && !(s[S::key(pb + d - np)] < s[S::key(pa + np - 1)])) pos = np;
+    }
+    return pos;
+}
+
+template <class K, int VB, bool REC, bool FORM>
+__global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
     const K* __restrict__ X, const void* __restrict__ Xv, int64_t N, int w0, K* __restrict__ Y,
     void* __restrict__ Yv, uint16_t* __restrict__ perm, int order) {
     using L = BlockLayout<K, VB>;
+    using S = BlockSlots<K>;
     using V = typename VBits<VB>::T;
+    constexpr int IPT = kBlockIPT;
     extern __shared__ __align__(128) unsigned char smem[];
     K* const sk0 = reinterpret_cast<K*>(smem);
     K* const sk1 = reinterpret_cast<K*>(smem + L::KEYS);
@@ -56,49 +96,77 @@ __global__ void __launch_bounds__(kBlockNT) merge_runs_block_kernel(
     const int len = int(N - base < kBlockR ? N - base : kBlockR);
 
     for (int x = tid; x < len; x += kBlockNT) {
-        sk0[x] = order_key(X[base + x], order);
-        si0[x] = uint16_t(x);
+        sk0[S::key(x)] = order_key(X[base + x], order);
+        si0[S::idx(x)] = uint16_t(x);
         if constexpr (VB != 0) sv[x] = static_cast<const V*>(Xv)[base + x];
     }
     __syncthreads();
 
-    const int own0 = int((int64_t(tid) * kBlockR) / kBlockNT);
-    const int own1 = int((int64_t(tid + 1) * kBlockR) / kBlockNT);
-    const int o0 = own0 < len ? own0 : len;
-    const int o1 = own1 < len ? own1 : len;
+    const int d0 = tid * IPT;
+    const int cnt = d0 < len ? (len - d0 < IPT ? len - d0 : IPT) : 0;
+    if constexpr (FORM) {
+        K rk[IPT];
+        uint16_t ri[IPT];
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            if (q < cnt) {
+                rk[q] = sk0[S::key(d0 + q)];
+                ri[q] = uint16_t(d0 + q);
+            }
+        }
+#pragma unroll
+        for (int round = 0; round < IPT; ++round) {
+#pragma unroll
+            for (int q = round & 1; q + 1 < IPT; q += 2) {
+                if (q + 1 < cnt && rk[q + 1] < rk[q]) {
+                    const K tk = rk[q];
+                    rk[q] = rk[q + 1];
+                    rk[q + 1] = tk;
+                    const uint16_t ti = ri[q];
+                    ri[q] = ri[q + 1];
+                    ri[q + 1] = ti;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            if (q < cnt) {
+                sk0[S::key(d0 + q)] = rk[q];
+                si0[S::idx(d0 + q)] = ri[q];
+            }
+        }
+        __syncthreads();
+    }
 
     int cur = 0;
-    for (int w = w0; w < len; w *= 2) {
+    for (int w = FORM ? IPT : w0; w < len; w *= 2) {
         const K* ik = cur ? sk1 : sk0;
         const uint16_t* ii = cur ? si1 : si0;
         K* ok = cur ? sk0 : sk1;
         uint16_t* oi = cur ? si0 : si1;
-        int x = o0;
-#pragma unroll 1
-        for (int seg = 0; seg < kBlockMaxOwn && x < o1; ++seg) {   // at most two pairs
-            const int ps = (x / (2 * w)) * (2 * w);             // pair start
+        if (cnt > 0) {
+            const int ps = (d0 / (2 * w)) * (2 * w);     // pair start
             const int alen = min(w, len - ps);
             const int blen = max(0, min(w, len - ps - alen));
-            const int pe = ps + alen + blen;
             const int bs = ps + alen;
-            const int dd[1] = {x - ps};
-            int jj[1];
-            split_in_tile<Log2Ceil<kBlockR + 1>::v>(ik + ps, alen, ik + bs, blen, dd, jj);
-            int j = jj[0], k = dd[0] - j;
-            K a = ik[ps + j];      // at most ik[len] <= ik[R]: inside the slack
-            K b = ik[bs + k];
-            const int stop = o1 < pe ? o1 : pe;
-#pragma unroll 1
-            for (; x < stop; ++x) {
-                const bool takeA = (k >= blen) || (j < alen && !(b < a));
-                const int src = takeA ? ps + j : bs + k;
-                ok[x] = takeA ? a : b;
-                oi[x] = ii[src];
-                j += takeA ? 1 : 0;
-                k += takeA ? 0 : 1;
-                const K nx = ik[takeA ? ps + j : bs + k];   // never taken when past a run
-                a = takeA ? nx : a;
-                b = takeA ? b : nx;
+            const int d = d0 - ps;
+            int j = split_pair<K, Log2Ceil<kBlockR / 2 + 1>::v>(ik, ps, alen, bs, blen, d);
+            int k = d - j;
+            K a = ik[S::key(ps + j)];     // at most element len <= R: the slack slot
+            K b = ik[S::key(bs + k)];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                if (q < cnt) {
+                    const bool takeA = (k >= blen) || (j < alen && !(b < a));
+                    const int src = takeA ? ps + j : bs + k;
+                    ok[S::key(d0 + q)] = takeA ? a : b;
+                    oi[S::idx(d0 + q)] = ii[S::idx(src)];
+                    j += takeA ? 1 : 0;
+                    k += takeA ? 0 : 1;
+                    const K nx = ik[S::key(takeA ? ps + j : bs + k)];   // unused past a run
+                    a = takeA ? nx : a;
+                    b = takeA ? b : nx;
+                }
             }
         }
         __syncthreads();
@@ -107,17 +175,18 @@ __global__ void __launch_bounds__(kBlockNT) merge_runs_block_kernel(
     const K* fk = cur ? sk1 : sk0;
     const uint16_t* fi = cur ? si1 : si0;
     for (int x = tid; x < len; x += kBlockNT) {
-        Y[base + x] = order_key_inverse(fk[x], order);
-        if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[fi[x]];
-        if constexpr (REC) perm[base + x] = fi[x];
+        Y[base + x] = order_key_inverse(fk[S::key(x)], order);
+        const uint16_t src = fi[S::idx(x)];
+        if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[src];
+        if constexpr (REC) perm[base + x] = src;
     }
 }
 
-template <class K, int VB, bool REC>
+template <class K, int VB, bool REC, bool FORM>
 cudaError_t launch_block(const void* X, const void* Xv, int64_t N, int w0, void* Y, void* Yv,
                          uint16_t* perm, int order, cudaStream_t st) {
     using L = BlockLayout<K, VB>;
-    auto kern = merge_runs_block_kernel<K, VB, REC>;
+    auto kern = merge_runs_block_kernel<K, VB, REC, FORM>;
     static std::once_flag once[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -134,18 +203,26 @@ cudaError_t launch_block(const void* X, const void* Xv, int64_t N, int w0, void*
     return cudaGetLastError();
 }
 
+template <class K, bool FORM>
+cudaError_t block_dispatch_form(int vb, const void* X, const void* Xv, int64_t N, int w0,
+                                void* Y, void* Yv, uint16_t* perm, int order, cudaStream_t st) {
+    const bool rec = perm != nullptr;
+    switch (vb * 2 + (rec ? 1 : 0)) {
+        case 0: return launch_block<K, 0, false, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 8: return launch_block<K, 4, false, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 9: return launch_block<K, 4, true, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 16: return launch_block<K, 8, false, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 17: return launch_block<K, 8, true, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <class K>
 cudaError_t block_dispatch(int vb, const void* X, const void* Xv, int64_t N, int w0, void* Y,
                            void* Yv, uint16_t* perm, int order, cudaStream_t st) {
-    const bool rec = perm != nullptr;
-    switch (vb * 2 + (rec ? 1 : 0)) {
-        case 0: return launch_block<K, 0, false>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        case 8: return launch_block<K, 4, false>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        case 9: return launch_block<K, 4, true>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        case 16: return launch_block<K, 8, false>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        case 17: return launch_block<K, 8, true>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return w0 < kBlockIPT
+               ? block_dispatch_form<K, true>(vb, X, Xv, N, w0, Y, Yv, perm, order, st)
+               : block_dispatch_form<K, false>(vb, X, Xv, N, w0, Y, Yv, perm, order, st);
 }
 
 bool overlaps(const void* p, int64_t pb, const void* q, int64_t qb) {
@@ -172,7 +249,7 @@ extern "C" cr_status cr_merge_runs_block(int key_type, int val_bytes, const void
     if (ks == 0 || N < 0) return CR_EINVAL;
     if (!(val_bytes == 0 || val_bytes == 4 || val_bytes == 8)) return CR_EINVAL;
     if (perm != nullptr && val_bytes == 0) return CR_EINVAL;
-    if (width < 8 || width > cr::kBlockR / 2 || (width & (width - 1)) != 0) return CR_EINVAL;
+    if (width < 1 || width > cr::kBlockR / 2 || (width & (width - 1)) != 0) return CR_EINVAL;
     if (N == 0) return CR_OK;
     const void* arrs[5] = {X, Y, val_bytes ? Xv : nullptr, val_bytes ? Yv : nullptr, perm};
     const bool need[5] = {true, true, val_bytes != 0, val_bytes != 0, perm != nullptr};

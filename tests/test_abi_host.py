@@ -229,6 +229,38 @@ def test_recorded_run_sort_validation(lib):
     assert lib.cr_sort_runs_backward_recorded(4, 0, None, None, None, None) == 0
 
 
+def test_merge_runs_block_validation(lib):
+    """Widths: powers of two from 1 (run formation) to half the chunk; bad
+    payload widths, a permutation without payloads, misaligned or overlapping
+    arrays are refused before any launch."""
+    X, Xv = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000)
+    Y, Yv = ctypes.c_void_p(0x300000), ctypes.c_void_p(0x400000)
+    P = ctypes.c_void_p(0x500000)
+    N = 5000
+    R = lib.cr_merge_runs_block_length()
+    assert R == 4096
+    for bad in (0, -1, 3, 6, 12, R, 2 * R):
+        assert lib.cr_merge_runs_block(0, 4, X, Xv, N, bad, Y, Yv, P, None) == 1, bad
+    assert lib.cr_merge_runs_block(0, 2, X, Xv, N, 1, Y, Yv, P, None) == 1
+    assert lib.cr_merge_runs_block(0, 0, X, None, N, 1, Y, None, P, None) == 1
+    assert lib.cr_merge_runs_block(99, 4, X, Xv, N, 1, Y, Yv, P, None) == 1
+    assert lib.cr_merge_runs_block(0, 4, X, Xv, -1, 1, Y, Yv, P, None) == 1
+    assert lib.cr_merge_runs_block(0, 4, X, Xv, N, 1, ctypes.c_void_p(0x300004), Yv, P,
+                                   None) == 3
+    assert lib.cr_merge_runs_block(0, 4, X, Xv, N, 1, ctypes.c_void_p(0x100010), Yv, P,
+                                   None) == 2
+    assert lib.cr_merge_runs_block(0, 4, X, Xv, N, 1, Y, Yv, ctypes.c_void_p(0x300100),
+                                   None) == 2
+    assert lib.cr_merge_runs_block(0, 4, X, Xv, 0, 1, Y, Yv, P, None) == 0
+    G, GX = ctypes.c_void_p(0x600000), ctypes.c_void_p(0x700000)
+    assert lib.cr_merge_runs_block_backward_recorded(0, N, P, G, GX, None) == 1
+    assert lib.cr_merge_runs_block_backward_recorded(4, N, P, G, ctypes.c_void_p(0x600100),
+                                                     None) == 2
+    assert lib.cr_merge_runs_block_backward_recorded(4, N, ctypes.c_void_p(0x500002), G, GX,
+                                                     None) == 3
+    assert lib.cr_merge_runs_block_backward_recorded(4, 0, None, None, None, None) == 0
+
+
 def test_key_type_encodings(lib):
     """Float and descending key types: sizes follow the storage width, and
     unknown codes or flags are refused."""

@@ -205,12 +205,14 @@ def test_merge_runs_block(dt, vb):
     """The shared-memory stage equals the chain of merge passes it replaces
     (oracle merge_pass, width by width up to the chunk length), keys and
     payloads bit for bit; its recorded permutation routes gradients like the
-    passes' composed permutation."""
+    passes' composed permutation.  Widths 1, 2 and 4 (run formation: groups
+    of 8 sorted in registers first) equal the passes from that width."""
     rng = np.random.default_rng(350 + vb)
     R = cr.merge_runs_block_length()
     kt = key_type(np.empty(0, dt))
     for N, w in [(R, 1024), (5 * R + 333, 8), (100003, 1024), (1, 64), (3 * R, 2048),
-                 (R - 1, 512)]:
+                 (R - 1, 512), (5 * R + 333, 1), (R, 2), (3 * R + 5, 4), (1, 1), (13, 1),
+                 (100003, 1)]:
         X = run_sorted_keys(rng, N, w, dt, 7 if vb else None)
         Xv = rng.standard_normal(N).astype(VAL_DTYPES.get(vb, np.float32))
         want, wv, src = X.copy(), Xv.copy(), np.arange(N)
