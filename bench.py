@@ -818,7 +818,7 @@ def run_row(args):
         torch.cuda.synchronize()
         un = {lb: round(ms / K, 4) for lb, ms in timer.totals().items()}
         stages_un = [f"{kd}:{w}" for kd, w in plan.stages]
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         Yk, Yv = torch.empty_like(Xu), torch.empty_like(Xuv)
         gXr = torch.empty_like(gY)
         perm = torch.empty(N, dtype=torch.int16, device=dev)
@@ -832,23 +832,19 @@ def run_row(args):
             ev[3].record(stream)
             api.sort_runs_backward_recorded(perm, gY, out=gXr)
             ev[4].record(stream)
-            api.merge_runs_block(Xu, Xuv, 1, key_type="u64", out=(Yk, Yv), perm=perm)
-            ev[5].record(stream)
-            api.merge_runs_block_backward_recorded(perm, gY, out=gXr)
-            ev[6].record(stream)
         torch.cuda.synchronize()
-        tms = [ev[i].elapsed_time(ev[i + 1]) for i in range(6)]
+        tms = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
 
         def row(ms, bpe):
             gbs = bpe * N / (ms / 1e3) / 1e9
             return {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
-        # bytes per element: keys + payloads in and out; backward replay reads
-        # keys and gY, writes gX; the recorded forms add / read the 2-byte
-        # permutation instead of the keys
+        # run formation alone (the recorded chain's first stage is
+        # sort_runs_record's launch).  Bytes per element: keys + payloads in
+        # and out; backward replay reads keys and gY, writes gX; the recorded
+        # forms add / read the 2-byte permutation instead of the keys
         unsorted = {"stages": stages_un, "passes": plan.passes,
                     "fwd_graph_ms": un["fwd_graph"], "bwd_graph_ms": un["bwd_graph"],
                     "elements_per_s": N / ((un["fwd_graph"] + un["bwd_graph"]) / 1e3),
-                    "block_form": row(tms[4], 26), "block_form_backward": row(tms[5], 10),
                     "sort_runs_run": api.sort_run_length(),
                     "sort_runs": row(tms[0], 24), "sort_runs_backward": row(tms[1], 16),
                     "sort_runs_record": row(tms[2], 26),

@@ -304,13 +304,14 @@ cr_status cr_merge_pass_backward_recorded(int key_type, int val_bytes, int64_t N
 
 /* ------------------------------------------------------------------------
  * Run formation for a stable merge sort from unsorted input: every run of
- * cr_sort_run_length() consecutive elements of X[0, N) (the last one may be
- * shorter) is stably sorted into Y (payloads follow their keys, equal keys
- * keep their input order), so that cr_merge_pass can take over with width
- * cr_sort_run_length().  The paper has no counterpart; it assumes sorted
- * inputs.  The backward routes gY to gX through the same in-run
- * permutation, recomputed from the input keys X.  Y must not overlap X;
- * val_bytes 0, 4 or 8 (4 or 8 for the backward).
+ * cr_sort_run_length() (4096) consecutive elements of X[0, N) (the last one
+ * may be shorter) is stably sorted into Y (payloads follow their keys, equal
+ * keys keep their input order), so that cr_merge_pass can take over with
+ * width cr_sort_run_length().  Same result as cr_merge_runs_block with width
+ * 1.  The paper has no counterpart; it assumes sorted inputs.  The backward
+ * routes gY to gX through the same in-run permutation, recomputed by sorting
+ * the input keys X again.  Y must not overlap X; val_bytes 0, 4 or 8 (4 or 8
+ * for the backward).
  * ------------------------------------------------------------------------ */
 int64_t cr_sort_run_length(void);
 

@@ -724,10 +724,8 @@ cr_status sort_runs_common(int key_type, int val_bytes, const void* X, const voi
     for (const Arr& a : outs) CR_TRY(check_arr(a));
     CR_TRY(check_no_alias(outs, 3, ins, 2));
     if (N == 0) return ok();
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = by_key(key_type, [&](auto ops) {
-        return ops.sort_runs(vb, X, Xv, N, Y, Yv, perm, key_order(key_type), st);
-    });
+    const cudaError_t e = cr::block_sort_runs(key_type, vb, perm ? 1 : 0, X, Xv, N, Y, Yv, perm,
+                                              nullptr, nullptr, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "run sort launch");
     return ok();
 }
@@ -774,10 +772,9 @@ cr_status cr_sort_runs_backward(int key_type, int val_bytes, const void* X, int6
     CR_TRY(check_arr(outs[0]));
     CR_TRY(check_no_alias(outs, 1, ins, 2));
     if (N == 0) return ok();
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = by_key(key_type, [&](auto ops) {
-        return ops.sort_runs_backward(val_bytes, X, N, gY, gX, key_order(key_type), st);
-    });
+    const cudaError_t e = cr::block_sort_runs(key_type, val_bytes, 2, X, nullptr, N, nullptr,
+                                              nullptr, nullptr, gY, gX,
+                                              static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "run sort backward launch");
     return ok();
 }

@@ -24,6 +24,11 @@
 // swaps only on strictly smaller), which equals the merges of widths
 // w .. IPT/2 (a stable merge's result is unique), and the rounds start at
 // IPT; with w = 1 this sorts any input into sorted runs of R.
+//
+// MODE 0: forward.  MODE 1: forward that also writes the chunk permutation.
+// MODE 2 (run formation only): backward by replay -- the same sort of the
+// input keys recovers the permutation, and gX[base + perm[x]] = gY[base + x]
+// is scattered through shared memory.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,6 +44,7 @@ constexpr int kBlockR = 4096;
 constexpr int kBlockIPT = 8;
 constexpr int kBlockNT = kBlockR / kBlockIPT;   // 512
 constexpr int kBlockMinWidth = kBlockIPT;       // narrowest merge round: 2w multiple of IPT
+static_assert(kBlockR == kSortRun, "run formation sorts chunks of the merge stage");
 
 template <class K>
 struct BlockSlots {
@@ -76,10 +82,12 @@ __device__ __forceinline__ int split_pair(const K* s, int pa, int alen, int pb, 
     return pos;
 }
 
-template <class K, int VB, bool REC, bool FORM>
+template <class K, int VB, int MODE, bool FORM>
 __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
     const K* __restrict__ X, const void* __restrict__ Xv, int64_t N, int w0, K* __restrict__ Y,
-    void* __restrict__ Yv, uint16_t* __restrict__ perm, int order) {
+    void* __restrict__ Yv, uint16_t* __restrict__ perm, const void* __restrict__ gY,
+    void* __restrict__ gX, int order) {
+    static_assert(MODE != 2 || (FORM && VB != 0), "replay backward: run formation, payloads");
     using L = BlockLayout<K, VB>;
     using S = BlockSlots<K>;
     using V = typename VBits<VB>::T;
@@ -98,7 +106,7 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
     for (int x = tid; x < len; x += kBlockNT) {
         sk0[S::key(x)] = order_key(X[base + x], order);
         si0[S::idx(x)] = uint16_t(x);
-        if constexpr (VB != 0) sv[x] = static_cast<const V*>(Xv)[base + x];
+        if constexpr (VB != 0 && MODE != 2) sv[x] = static_cast<const V*>(Xv)[base + x];
     }
     __syncthreads();
 
@@ -174,19 +182,27 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
     }
     const K* fk = cur ? sk1 : sk0;
     const uint16_t* fi = cur ? si1 : si0;
-    for (int x = tid; x < len; x += kBlockNT) {
-        Y[base + x] = order_key_inverse(fk[S::key(x)], order);
-        const uint16_t src = fi[S::idx(x)];
-        if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[src];
-        if constexpr (REC) perm[base + x] = src;
+    if constexpr (MODE != 2) {
+        for (int x = tid; x < len; x += kBlockNT) {
+            Y[base + x] = order_key_inverse(fk[S::key(x)], order);
+            const uint16_t src = fi[S::idx(x)];
+            if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[src];
+            if constexpr (MODE == 1) perm[base + x] = src;
+        }
+    } else {
+        const V* gy = static_cast<const V*>(gY);
+        for (int x = tid; x < len; x += kBlockNT) sv[fi[S::idx(x)]] = gy[base + x];
+        __syncthreads();
+        V* gx = static_cast<V*>(gX);
+        for (int x = tid; x < len; x += kBlockNT) gx[base + x] = sv[x];
     }
 }
 
-template <class K, int VB, bool REC, bool FORM>
+template <class K, int VB, int MODE, bool FORM>
 cudaError_t launch_block(const void* X, const void* Xv, int64_t N, int w0, void* Y, void* Yv,
-                         uint16_t* perm, int order, cudaStream_t st) {
+                         uint16_t* perm, const void* gY, void* gX, int order, cudaStream_t st) {
     using L = BlockLayout<K, VB>;
-    auto kern = merge_runs_block_kernel<K, VB, REC, FORM>;
+    auto kern = merge_runs_block_kernel<K, VB, MODE, FORM>;
     static std::once_flag once[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -199,7 +215,8 @@ cudaError_t launch_block(const void* X, const void* Xv, int64_t N, int w0, void*
     if (e != cudaSuccess) return e;
     const int64_t chunks = (N + kBlockR - 1) / kBlockR;
     kern<<<unsigned(chunks), kBlockNT, L::TOTAL, st>>>(static_cast<const K*>(X), Xv, N, w0,
-                                                        static_cast<K*>(Y), Yv, perm, order);
+                                                        static_cast<K*>(Y), Yv, perm, gY, gX,
+                                                        order);
     return cudaGetLastError();
 }
 
@@ -208,11 +225,16 @@ cudaError_t block_dispatch_form(int vb, const void* X, const void* Xv, int64_t N
                                 void* Y, void* Yv, uint16_t* perm, int order, cudaStream_t st) {
     const bool rec = perm != nullptr;
     switch (vb * 2 + (rec ? 1 : 0)) {
-        case 0: return launch_block<K, 0, false, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        case 8: return launch_block<K, 4, false, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        case 9: return launch_block<K, 4, true, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        case 16: return launch_block<K, 8, false, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
-        case 17: return launch_block<K, 8, true, FORM>(X, Xv, N, w0, Y, Yv, perm, order, st);
+        case 0: return launch_block<K, 0, 0, FORM>(X, Xv, N, w0, Y, Yv, perm, nullptr, nullptr,
+                                                   order, st);
+        case 8: return launch_block<K, 4, 0, FORM>(X, Xv, N, w0, Y, Yv, perm, nullptr, nullptr,
+                                                   order, st);
+        case 9: return launch_block<K, 4, 1, FORM>(X, Xv, N, w0, Y, Yv, perm, nullptr, nullptr,
+                                                   order, st);
+        case 16: return launch_block<K, 8, 0, FORM>(X, Xv, N, w0, Y, Yv, perm, nullptr, nullptr,
+                                                    order, st);
+        case 17: return launch_block<K, 8, 1, FORM>(X, Xv, N, w0, Y, Yv, perm, nullptr, nullptr,
+                                                    order, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -225,6 +247,32 @@ cudaError_t block_dispatch(int vb, const void* X, const void* Xv, int64_t N, int
                : block_dispatch_form<K, false>(vb, X, Xv, N, w0, Y, Yv, perm, order, st);
 }
 
+template <class K>
+cudaError_t block_replay(int vb, const void* X, int64_t N, const void* gY, void* gX, int order,
+                         cudaStream_t st) {
+    if (vb == 4)
+        return launch_block<K, 4, 2, true>(X, nullptr, N, 1, nullptr, nullptr, nullptr, gY, gX,
+                                           order, st);
+    if (vb == 8)
+        return launch_block<K, 8, 2, true>(X, nullptr, N, 1, nullptr, nullptr, nullptr, gY, gX,
+                                           order, st);
+    return cudaErrorInvalidValue;
+}
+
+// Storage type of a key type (float keys are ordered as the signed integer
+// of their width after order_key).
+template <class F>
+cudaError_t by_storage(int key_type, F&& f) {
+    switch (key_base(key_type)) {
+        case CR_KEY_I32:
+        case CR_KEY_F32: return f(int32_t(0));
+        case CR_KEY_U32: return f(uint32_t(0));
+        case CR_KEY_I64:
+        case CR_KEY_F64: return f(int64_t(0));
+        default: return f(uint64_t(0));
+    }
+}
+
 bool overlaps(const void* p, int64_t pb, const void* q, int64_t qb) {
     if (pb <= 0 || qb <= 0) return false;
     const uintptr_t a = reinterpret_cast<uintptr_t>(p), b = reinterpret_cast<uintptr_t>(q);
@@ -232,6 +280,19 @@ bool overlaps(const void* p, int64_t pb, const void* q, int64_t qb) {
 }
 
 }  // namespace
+
+cudaError_t block_sort_runs(int key_type, int vb, int mode, const void* X, const void* Xv,
+                            int64_t N, void* Y, void* Yv, uint16_t* perm, const void* gY,
+                            void* gX, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const int order = key_type_order(key_type);
+    return by_storage(key_type, [&](auto k) {
+        using K = decltype(k);
+        if (mode == 2) return block_replay<K>(vb, X, N, gY, gX, order, st);
+        if ((mode == 1) != (perm != nullptr)) return cudaErrorInvalidValue;
+        return block_dispatch_form<K, true>(vb, X, Xv, N, 1, Y, Yv, perm, order, st);
+    });
+}
 
 // Backward of a recorded block: the chunk permutation routes gY to gX
 // (cr_route.cu, shared with run formation's recorded backward).
@@ -269,23 +330,10 @@ extern "C" cr_status cr_merge_runs_block(int key_type, int val_bytes, const void
     const int order = cr::key_type_order(key_type);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int w0 = int(width);
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (cr::key_base(key_type)) {
-        case CR_KEY_I32:
-        case CR_KEY_F32:
-            e = cr::block_dispatch<int32_t>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
-            break;
-        case CR_KEY_U32:
-            e = cr::block_dispatch<uint32_t>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
-            break;
-        case CR_KEY_I64:
-        case CR_KEY_F64:
-            e = cr::block_dispatch<int64_t>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
-            break;
-        default:
-            e = cr::block_dispatch<uint64_t>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
-            break;
-    }
+    const cudaError_t e = cr::by_storage(key_type, [&](auto k) {
+        using K = decltype(k);
+        return cr::block_dispatch<K>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
+    });
     return e == cudaSuccess ? CR_OK : CR_ECUDA;
 }
 

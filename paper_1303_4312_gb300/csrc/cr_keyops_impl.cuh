@@ -7,7 +7,6 @@
 #include "cr_launch.cuh"
 #include "cr_merge.cuh"
 #include "cr_partition.cuh"
-#include "cr_sort.cuh"
 
 namespace cr {
 
@@ -219,55 +218,6 @@ cudaError_t KeyOps<K>::partition_batched(const void* A, const void* B, const int
     return cudaGetLastError();
 }
 
-template <class K, int VB, int MODE>
-cudaError_t launch_sort_runs(const void* X, const void* Xv, int64_t N, void* Y, void* Yv,
-                             uint16_t* perm, const void* gY, void* gX, int order,
-                             cudaStream_t st) {
-    using L = SortLayout<K, VB, MODE, kSortNT, kSortIPT>;
-    auto kern = sort_runs_kernel<K, VB, MODE, kSortNT, kSortIPT>;
-    static LaunchShape cache[kMaxDevices];
-    static std::once_flag once[kMaxDevices];
-    LaunchShape sh;
-    cudaError_t e = launch_shape(kern, kSortNT, L::TOTAL, cache, once, sh);
-    if (e != cudaSuccess) return e;
-    if (N <= 0) return cudaSuccess;
-    const unsigned grid = unsigned((N + kSortRun - 1) / kSortRun);
-    kern<<<grid, kSortNT, L::TOTAL, st>>>(static_cast<const K*>(X), Xv, N, static_cast<K*>(Y), Yv,
-                                          perm, gY, gX, order);
-    return cudaGetLastError();
-}
-
-template <class K>
-cudaError_t KeyOps<K>::sort_runs(int vb, const void* X, const void* Xv, int64_t N, void* Y,
-                                 void* Yv, uint16_t* perm, int order, cudaStream_t st) {
-    if (perm != nullptr) {
-        if (vb == 4)
-            return launch_sort_runs<K, 4, 1>(X, Xv, N, Y, Yv, perm, nullptr, nullptr, order, st);
-        if (vb == 8)
-            return launch_sort_runs<K, 8, 1>(X, Xv, N, Y, Yv, perm, nullptr, nullptr, order, st);
-        return cudaErrorInvalidValue;
-    }
-    if (vb == 0)
-        return launch_sort_runs<K, 0, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, order, st);
-    if (vb == 4)
-        return launch_sort_runs<K, 4, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, order, st);
-    if (vb == 8)
-        return launch_sort_runs<K, 8, 0>(X, Xv, N, Y, Yv, nullptr, nullptr, nullptr, order, st);
-    return cudaErrorInvalidValue;
-}
-
-template <class K>
-cudaError_t KeyOps<K>::sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
-                                          void* gX, int order, cudaStream_t st) {
-    if (vb == 4)
-        return launch_sort_runs<K, 4, 2>(X, nullptr, N, nullptr, nullptr, nullptr, gY, gX, order,
-                                         st);
-    if (vb == 8)
-        return launch_sort_runs<K, 8, 2>(X, nullptr, N, nullptr, nullptr, nullptr, gY, gX, order,
-                                         st);
-    return cudaErrorInvalidValue;
-}
-
 template <class K>
 cudaError_t KeyOps<K>::co_rank_many(const void* A, int64_t m, const void* B, int64_t n,
                                     const int64_t* ranks, int64_t cnt, int64_t* oi, int64_t* oj,
@@ -322,9 +272,4 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
                                                      int64_t*, int64_t*, int, cudaStream_t);   \
     template cudaError_t cr::KeyOps<K>::co_rank_one(const void*, int64_t, const void*,         \
                                                     int64_t, int64_t, int64_t*, int,           \
-                                                    cudaStream_t);                             \
-    template cudaError_t cr::KeyOps<K>::sort_runs(int, const void*, const void*, int64_t,      \
-                                                  void*, void*, uint16_t*, int, cudaStream_t); \
-    template cudaError_t cr::KeyOps<K>::sort_runs_backward(int, const void*, int64_t,          \
-                                                           const void*, void*, int,            \
-                                                           cudaStream_t);
+                                                    cudaStream_t);

@@ -82,9 +82,8 @@ int current_shape(int key_bytes, int vb, int cls);
 // starts stay within a few MB).
 constexpr int64_t kSmallMergeTiles = 4096;
 
-// Run formation shape: 256 threads x 7 elements per run.
-constexpr int kSortNT = 256, kSortIPT = 7;
-constexpr int64_t kSortRun = int64_t(kSortNT) * kSortIPT;
+// Run formation: the chunk of the shared-memory merge stage (cr_block.cu).
+constexpr int64_t kSortRun = 4096;
 
 inline int64_t tile_of_shape(int s) {
     return int64_t(kShapes[s].nt) * kShapes[s].ipt * kShapes[s].ilp;
@@ -130,13 +129,6 @@ struct KeyOps {
                                     int order, cudaStream_t st);
     static cudaError_t co_rank_one(const void* A, int64_t m, const void* B, int64_t n, int64_t r,
                                    int64_t* out, int order, cudaStream_t st);
-    // Run formation: stably sort runs of kSortRun elements (vb 0, 4, 8);
-    // with perm (vb 4, 8) also write each run's permutation; backward
-    // (vb 4, 8): gX from gY through the same in-run permutation, replayed.
-    static cudaError_t sort_runs(int vb, const void* X, const void* Xv, int64_t N, void* Y,
-                                 void* Yv, uint16_t* perm, int order, cudaStream_t st);
-    static cudaError_t sort_runs_backward(int vb, const void* X, int64_t N, const void* gY,
-                                          void* gX, int order, cudaStream_t st);
 };
 
 // Backward of a recorded merge pass (vb in {4,8}) over N elements with run
@@ -146,6 +138,15 @@ struct KeyOps {
 cudaError_t route_recorded(int vb, void* ws, const uint32_t* flags, int64_t flag_words,
                            int64_t N, int64_t w, int64_t tile, const void* gY, void* gX,
                            cudaStream_t st);
+
+// Run formation (cr_block.cu): the shared-memory merge stage from width 1
+// stably sorts every run of kSortRun elements.  mode 0: forward (vb 0, 4,
+// 8); 1: forward that also writes each run's permutation (vb 4, 8); 2:
+// backward that replays the sort on X and routes gY to gX through the
+// recovered permutation (vb 4, 8; Xv, Y, Yv, perm unused).
+cudaError_t block_sort_runs(int key_type, int vb, int mode, const void* X, const void* Xv,
+                            int64_t N, void* Y, void* Yv, uint16_t* perm, const void* gY,
+                            void* gX, cudaStream_t st);
 
 // Backward of a recorded run formation (vb in {4,8}): within every run of
 // kSortRun elements, gX[base + perm[base + x]] = gY[base + x].
