@@ -208,6 +208,11 @@ def algorithmic_bytes(mg) -> int:
     return 2 * (mg["m"] + mg["n"]) * mg["kb"]
 
 
+# nominal HBM3e bandwidth of one GB300 (the measured copy peak is the
+# roofline denominator; the nominal figure is reported beside it)
+NOMINAL_HBM_GBS = 7900.0
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -362,6 +367,7 @@ def run_ours(args, rank, world, local, dist):
         "roofline": {"kernel": "merge_tiles_kernel", "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
+                     "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "traffic": recorded_traffic(args.shift),
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
@@ -475,6 +481,7 @@ def run_row(args):
             if b:
                 gbs = b / (ms / K / 1e3) / 1e9
                 kern[label].update({"gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                                    "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4),
                                     "alg_bytes": b})
         res["kernels"] = kern
         if extra:
