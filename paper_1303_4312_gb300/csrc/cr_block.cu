@@ -68,14 +68,17 @@ struct BlockLayout {
 
 // Largest j in [max(0, d - blen), min(d, alen)] with A[j-1] <= B[d-j]
 // (Lemma 1's first condition; A = s[pa ..], B = s[pb ..] in logical
-// indices), by binary lifting over LOG steps.
-template <class K, int LOG>
-__device__ __forceinline__ int split_pair(const K* s, int pa, int alen, int pb, int blen, int d) {
+// indices), by binary lifting with steps w, w/2, ..., 1: the interval is at
+// most w long (alen, blen <= w, a power of two), so a round of width w
+// takes log2(w) + 1 steps, the same for every thread of the round.
+template <class K>
+__device__ __forceinline__ int split_pair(const K* s, int pa, int alen, int pb, int blen, int d,
+                                          int w) {
     using S = BlockSlots<K>;
     int pos = d - blen > 0 ? d - blen : 0;
     const int hi = d < alen ? d : alen;
-#pragma unroll
-    for (int step = 1 << (LOG - 1); step > 0; step >>= 1) {
+#pragma unroll 4
+    for (int step = w; step > 0; step >>= 1) {
         const int np = pos + step;
         if (np <= hi && !(s[S::key(pb + d - np)] < s[S::key(pa + np - 1)])) pos = np;
     }
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
             const int blen = max(0, min(w, len - ps - alen));
             const int bs = ps + alen;
             const int d = d0 - ps;
-            int j = split_pair<K, Log2Ceil<kBlockR / 2 + 1>::v>(ik, ps, alen, bs, blen, d);
+            int j = split_pair<K>(ik, ps, alen, bs, blen, d, w);
             int k = d - j;
             K a = ik[S::key(ps + j)];     // at most element len <= R: the slack slot
             K b = ik[S::key(bs + k)];
