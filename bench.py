@@ -91,17 +91,18 @@ def force_tile_shape(lib, shape):
 
 
 def tile_shapes(lib, combos):
-    """NTxIPTxILP of the balanced and skewed shape for each (label, key code, vb)."""
+    """NTxIPTxILP of the balanced, skewed and small-merge shape for each
+    (label, key code, vb)."""
     import ctypes
     out = {}
     for label, code, vb in combos:
         row = []
-        for cls in (0, 1):
+        for cls in (0, 1, 2):
             s = lib.cr_get_tile_shape_for(code, vb, cls)
             nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
             lib.cr_tile_shape_info(s, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
             row.append(f"{nt.value}x{ipt.value}x{ilp.value}")
-        out[label] = row if row[0] != row[1] else row[0]
+        out[label] = row if len(set(row)) > 1 else row[0]
     return out
 
 

@@ -124,13 +124,14 @@ cr_status cr_set_tile_shape(int key_type, int val_bytes, int shape);
 /* Current shape for this key type and payload width (-1 if invalid). */
 int cr_get_tile_shape(int key_type, int val_bytes);
 
-/* Single merges choose between two shapes per key type and payload width by
- * geometry: "skewed" when one input is more than 16 times longer than the
- * other (16 * min(m, n) < max(m, n)), else "balanced".  Batched and merge-pass
- * calls use the balanced shape.  cr_set_tile_shape sets both classes; these
- * set and read one (skewed = 0 or 1). */
-cr_status cr_set_tile_shape_for(int key_type, int val_bytes, int skewed, int shape);
-int cr_get_tile_shape_for(int key_type, int val_bytes, int skewed);
+/* Single merges choose among three shapes per key type and payload width by
+ * geometry class: 2 "small" when m + n <= 2^23 (few tiles per CTA slot),
+ * else 1 "skewed" when one input is more than 16 times longer than the other
+ * (16 * min(m, n) < max(m, n)), else 0 "balanced".  Batched and merge-pass
+ * calls use the balanced shape.  cr_set_tile_shape sets every class; these
+ * set and read one (cls = 0, 1 or 2; CR_EINVAL / -1 for another value). */
+cr_status cr_set_tile_shape_for(int key_type, int val_bytes, int cls, int shape);
+int cr_get_tile_shape_for(int key_type, int val_bytes, int cls);
 /* TILE a single merge of m and n elements uses (0 for invalid arguments). */
 int64_t cr_tile_size_for(int key_type, int val_bytes, int64_t m, int64_t n);
 

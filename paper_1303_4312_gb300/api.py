@@ -78,9 +78,16 @@ def _size(fn, *args) -> int:
     return out.value
 
 
-def tile_size(key_type: str, val_bytes: int = 0) -> int:
-    """Output elements per tile used for this key type and payload width."""
-    return int(_lib.load().cr_tile_size(_lib.key_code(key_type), int(val_bytes)))
+def tile_size(key_type: str, val_bytes: int = 0, m: int | None = None,
+              n: int | None = None) -> int:
+    """Output elements per tile used for this key type and payload width: by
+    a single merge of m and n elements when given (its geometry class), else
+    by batched calls, merge passes and large balanced merges."""
+    lib = _lib.load()
+    code = _lib.key_code(key_type)
+    if m is None and n is None:
+        return int(lib.cr_tile_size(code, int(val_bytes)))
+    return int(lib.cr_tile_size_for(code, int(val_bytes), int(m or 0), int(n or 0)))
 
 
 # ---------------------------------------------------------------------------

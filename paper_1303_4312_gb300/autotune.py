@@ -1,7 +1,8 @@
 """Autotuner for the tile shape of the merge kernels.
 
-For every (key size, payload width) combination and both geometry classes
-(balanced: m = n; skewed: one input 512 times longer than the other) it times
+For every (key size, payload width) combination and each geometry class
+(balanced: m = n; skewed: one input 512 times longer than the other; small:
+m = n with 2^21 elements in all, below the library's small-merge limit) it times
 the forward merge (and, with payloads, the backward) of a seeded random
 problem under each tile shape the library offers for that combination, keeps
 the fastest, and writes a JSON table keyed by GPU name and compute
@@ -27,7 +28,7 @@ TABLE_DIR = os.path.join(HERE, "tuning")
 # (key type name, payload bytes) combinations; uint keys share the kernels'
 # shapes with the int keys of the same width.
 COMBOS = [("i32", 0), ("i32", 4), ("i32", 8), ("i64", 0), ("i64", 4), ("i64", 8)]
-CLASSES = (("balanced", 0), ("skewed", 1))
+CLASSES = (("balanced", 0), ("skewed", 1), ("small", 2))
 
 
 def _slug(name: str) -> str:
@@ -59,20 +60,20 @@ def apply(lib=None, gpu_name: str | None = None, cc: str | None = None) -> dict 
         return None
     for key, entry in table.get("shapes", {}).items():
         kt, vb = key.split(":")
-        for cls, skewed in CLASSES:
+        for cls, index in CLASSES:
             if cls in entry:
-                _lib.check(lib.cr_set_tile_shape_for(_lib.KEY_TYPES[kt], int(vb), skewed,
+                _lib.check(lib.cr_set_tile_shape_for(_lib.KEY_TYPES[kt], int(vb), index,
                                                      int(entry[cls]["shape"])))
     return table
 
 
-def _time_combo(lib, kt: str, vb: int, log2_size: int, reps: int, skewed: int):
+def _time_combo(lib, kt: str, vb: int, log2_size: int, reps: int, cls: int):
     import torch
     code = _lib.KEY_TYPES[kt]
     dev = torch.device("cuda")
     g = torch.Generator(device=dev).manual_seed(1234)
-    total = 1 << log2_size
-    m = total // 513 if skewed else total // 2
+    total = 1 << (min(log2_size, 21) if cls == 2 else log2_size)
+    m = total // 513 if cls == 1 else total // 2
     n = total - m
     kdt = torch.int32 if kt == "i32" else torch.int64
     lo, hi = (-(1 << 31), 1 << 31) if kt == "i32" else (-(1 << 62), 1 << 62)
@@ -92,7 +93,7 @@ def _time_combo(lib, kt: str, vb: int, log2_size: int, reps: int, skewed: int):
     s = torch.cuda.current_stream().cuda_stream
     results = {}
     for shape in range(lib.cr_tile_shape_count()):
-        if lib.cr_set_tile_shape_for(code, vb, skewed, shape) != 0:
+        if lib.cr_set_tile_shape_for(code, vb, cls, shape) != 0:
             continue
         need = ctypes.c_size_t()
         _lib.check(lib.cr_merge_workspace_size(code, vb, m, n, ctypes.byref(need)))
@@ -133,9 +134,9 @@ def tune(log2_size: int = 26, reps: int = 10, write: bool = True,
     for kt, vb in COMBOS:
         code = _lib.KEY_TYPES[kt]
         entry = {}
-        for cls, skewed in CLASSES:
-            before = lib.cr_get_tile_shape_for(code, vb, skewed)
-            res = _time_combo(lib, kt, vb, log2_size, reps, skewed)
+        for cls, index in CLASSES:
+            before = lib.cr_get_tile_shape_for(code, vb, index)
+            res = _time_combo(lib, kt, vb, log2_size, reps, index)
             best = min(res, key=lambda s: sum(res[s].values()))
             nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
             _lib.check(lib.cr_tile_shape_info(best, ctypes.byref(nt), ctypes.byref(ipt),
@@ -143,7 +144,7 @@ def tune(log2_size: int = 26, reps: int = 10, write: bool = True,
             entry[cls] = {
                 "shape": best, "nt": nt.value, "ipt": ipt.value, "ilp": ilp.value,
                 "ms": {str(s): {k: round(v, 4) for k, v in r.items()} for s, r in res.items()}}
-            _lib.check(lib.cr_set_tile_shape_for(code, vb, skewed, before))
+            _lib.check(lib.cr_set_tile_shape_for(code, vb, index, before))
         table["shapes"][f"{kt}:{vb}"] = entry
     if write:
         path = out or table_path(name)

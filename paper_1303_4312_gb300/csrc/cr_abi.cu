@@ -161,11 +161,14 @@ cr_status check_backward(int key_type, int vb, const void* Ak, int64_t m, const 
     return check_no_alias(outs, 2, ins, 3);
 }
 
-// Shape for a merge of these sizes (batched and pass calls use the
-// balanced class: their segments are not known on the host).
-int shape_of(int key_type, int vb, int64_t m = 1, int64_t n = 1) {
+// Shape of a single merge of m and n elements (its geometry class).
+int shape_of(int key_type, int vb, int64_t m, int64_t n) {
     return cr::current_shape(key_bytes(key_type), vb, cr::geometry_class(m, n));
 }
+
+// Shape of batched and merge-pass calls: the balanced class (their segments
+// are not known on the host).
+int shape_of(int key_type, int vb) { return cr::current_shape(key_bytes(key_type), vb, 0); }
 
 int64_t single_tiles(int shape, int64_t m, int64_t n, int64_t* tile_out) {
     const int64_t tile = cr::tile_of_shape(shape);
@@ -241,13 +244,14 @@ namespace cr {
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
 // Selected tile shape per (key size 4|8, payload width 0|4|8, geometry
-// class balanced|skewed).  Defaults: 256 x 15 for keys without payload
+// class balanced|skewed|small).  Defaults: 256 x 15 for keys without payload
 // (128 x 31 for skewed 8-byte merges), 256 x 7 otherwise.
-static std::atomic<int> g_shape[2][3][2] = {{{{0}, {0}}, {{2}, {2}}, {{2}, {2}}},
-                                            {{{0}, {1}}, {{2}, {2}}, {{2}, {2}}}};
+static std::atomic<int> g_shape[2][3][kNumClasses] = {
+    {{{0}, {0}, {0}}, {{2}, {2}, {2}}, {{2}, {2}, {2}}},
+    {{{0}, {1}, {0}}, {{2}, {2}, {2}}, {{2}, {2}, {2}}}};
 
 int current_shape(int key_bytes, int vb, int cls) {
-    return g_shape[key_bytes == 8 ? 1 : 0][vb / 4][cls ? 1 : 0].load(std::memory_order_relaxed);
+    return g_shape[key_bytes == 8 ? 1 : 0][vb / 4][cls].load(std::memory_order_relaxed);
 }
 }  // namespace cr
 
@@ -271,7 +275,7 @@ const char* cr_status_string(int status) {
 
 const char* cr_last_error(void) { return g_last_error.c_str(); }
 
-int cr_abi_version(void) { return 100; }
+int cr_abi_version(void) { return 101; }
 
 int64_t cr_tile_size(int key_type, int val_bytes) {
     const int ks = key_bytes(key_type);
@@ -297,7 +301,7 @@ cr_status cr_set_tile_shape(int key_type, int val_bytes, int shape) {
     if (!cr::shape_available(ks, val_bytes, shape))
         return fail(CR_EUNSUPPORTED, "tile shape %d does not fit %d-byte keys with %d-byte payloads",
                     shape, ks, val_bytes);
-    for (int cls = 0; cls < 2; ++cls)
+    for (int cls = 0; cls < cr::kNumClasses; ++cls)
         cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4][cls].store(shape, std::memory_order_relaxed);
     return ok();
 }
@@ -306,22 +310,23 @@ int cr_get_tile_shape(int key_type, int val_bytes) {
     return cr_get_tile_shape_for(key_type, val_bytes, 0);
 }
 
-cr_status cr_set_tile_shape_for(int key_type, int val_bytes, int skewed, int shape) {
+cr_status cr_set_tile_shape_for(int key_type, int val_bytes, int cls, int shape) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, true));
+    if (cls < 0 || cls >= cr::kNumClasses) return fail(CR_EINVAL, "no geometry class %d", cls);
     const int ks = key_bytes(key_type);
     if (!cr::shape_available(ks, val_bytes, shape))
         return fail(CR_EUNSUPPORTED, "tile shape %d does not fit %d-byte keys with %d-byte payloads",
                     shape, ks, val_bytes);
-    cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4][skewed ? 1 : 0].store(shape,
-                                                                    std::memory_order_relaxed);
+    cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4][cls].store(shape, std::memory_order_relaxed);
     return ok();
 }
 
-int cr_get_tile_shape_for(int key_type, int val_bytes, int skewed) {
+int cr_get_tile_shape_for(int key_type, int val_bytes, int cls) {
     const int ks = key_bytes(key_type);
     if (ks == 0 || (val_bytes != 0 && val_bytes != 4 && val_bytes != 8)) return -1;
-    return cr::current_shape(ks, val_bytes, skewed ? 1 : 0);
+    if (cls < 0 || cls >= cr::kNumClasses) return -1;
+    return cr::current_shape(ks, val_bytes, cls);
 }
 
 int64_t cr_tile_size_for(int key_type, int val_bytes, int64_t m, int64_t n) {

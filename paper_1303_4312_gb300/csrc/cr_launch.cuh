@@ -24,7 +24,7 @@ struct ShapeDesc {
 };
 constexpr int kNumShapes = 6;
 constexpr ShapeDesc kShapes[kNumShapes] = {{256, 15, 1}, {128, 31, 1}, {256, 7, 1},
-                                           {128, 15, 1}, {128, 15, 2}, {128, 7, 2}};
+                                           {128, 15, 1}, {128, 15, 2}, {256, 31, 1}};
 
 template <int S> struct ShapeAt {
     static constexpr int NT = kShapes[S].nt;
@@ -65,10 +65,15 @@ inline bool shape_available(int key_bytes, int vb, int s) {
     return false;
 }
 
-// Geometry class of a merge: skewed (1) when one input is more than 16 times
-// longer than the other, else balanced (0).  Skewed merges take nearly whole
-// tiles from one input, so their best tile shape differs.
+// Geometry class of a merge: small (2) when m + n <= kSmallClassElems --
+// few tiles per CTA slot, where smaller tiles balance the grid better and
+// the partition is cheap; else skewed (1) when one input is more than 16
+// times longer than the other (nearly whole tiles come from one input);
+// else balanced (0).  Each class has its own tile shape.
+constexpr int64_t kSmallClassElems = int64_t(1) << 23;
+constexpr int kNumClasses = 3;
 inline int geometry_class(int64_t m, int64_t n) {
+    if (m + n <= kSmallClassElems) return 2;
     const int64_t lo = m < n ? m : n, hi = m < n ? n : m;
     return 16 * lo < hi ? 1 : 0;
 }

@@ -39,7 +39,7 @@ def test_status_strings(lib):
     for code, name in _lib.STATUS.items():
         assert lib.cr_status_string(code).decode() == name
     assert lib.cr_status_string(99).decode() == "CR_UNKNOWN"
-    assert lib.cr_abi_version() == 100
+    assert lib.cr_abi_version() == 101
 
 
 def test_tile_sizes(lib):
@@ -136,10 +136,11 @@ def test_tile_shapes(lib):
 
 
 def test_geometry_classes(lib):
-    """Balanced and skewed merges can use different shapes; cr_tile_size_for
-    and the workspace size follow the class of (m, n)."""
+    """Balanced, skewed and small merges can use different shapes;
+    cr_tile_size_for and the workspace size follow the class of (m, n)."""
     kt = 3  # uint64
     b0, s0 = lib.cr_get_tile_shape_for(kt, 0, 0), lib.cr_get_tile_shape_for(kt, 0, 1)
+    m0 = lib.cr_get_tile_shape_for(kt, 0, 2)
     try:
         assert lib.cr_set_tile_shape_for(kt, 0, 0, 2) == 0
         assert lib.cr_set_tile_shape_for(kt, 0, 1, 3) == 0
@@ -148,17 +149,33 @@ def test_geometry_classes(lib):
         t2 = nt.value * ipt.value * ilp.value
         lib.cr_tile_shape_info(3, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
         t3 = nt.value * ipt.value * ilp.value
-        assert lib.cr_tile_size_for(kt, 0, 1000, 1000) == t2
-        assert lib.cr_tile_size_for(kt, 0, 1000, 16000) == t2      # 16*min == max: balanced
-        assert lib.cr_tile_size_for(kt, 0, 1000, 16001) == t3      # skewed
-        assert lib.cr_tile_size_for(kt, 0, 16001, 1000) == t3
+        big = 1 << 23                                             # small-class limit
+        assert lib.cr_tile_size_for(kt, 0, big, big) == t2
+        assert lib.cr_tile_size_for(kt, 0, big, 16 * big) == t2  # 16*min == max: balanced
+        assert lib.cr_tile_size_for(kt, 0, big, 16 * big + 1) == t3   # skewed
+        assert lib.cr_tile_size_for(kt, 0, 16 * big + 1, big) == t3
         assert lib.cr_tile_size(kt, 0) == t2
         out = ctypes.c_size_t()
+        assert lib.cr_merge_workspace_size(kt, 0, 10, 100 * big, ctypes.byref(out)) == 0
+        assert out.value == 256 + 32 * ((100 * big + 10 + t3 - 1) // t3)
+        # small merges (m + n <= 2^23) use the third class, whatever their ratio
+        assert lib.cr_set_tile_shape_for(kt, 0, 2, 0) == 0
+        lib.cr_tile_shape_info(0, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
+        t0 = nt.value * ipt.value * ilp.value
+        assert lib.cr_get_tile_shape_for(kt, 0, 2) == 0
+        for m, n in ((1000, 1000), (10, 100000), (big // 2, big // 2), (0, big)):
+            assert lib.cr_tile_size_for(kt, 0, m, n) == t0, (m, n)
+        assert lib.cr_tile_size_for(kt, 0, big // 2, big // 2 + 1) == t2
         assert lib.cr_merge_workspace_size(kt, 0, 10, 100000, ctypes.byref(out)) == 0
-        assert out.value == 256 + 32 * ((100010 + t3 - 1) // t3)
+        assert out.value == 256 + 32 * ((100010 + t0 - 1) // t0)
+        # classes other than 0, 1, 2 are refused
+        assert lib.cr_set_tile_shape_for(kt, 0, 3, 0) == 1
+        assert lib.cr_set_tile_shape_for(kt, 0, -1, 0) == 1
+        assert lib.cr_get_tile_shape_for(kt, 0, 3) == -1
     finally:
         lib.cr_set_tile_shape_for(kt, 0, 0, b0)
         lib.cr_set_tile_shape_for(kt, 0, 1, s0)
+        lib.cr_set_tile_shape_for(kt, 0, 2, m0)
 
 
 def test_recorded_pass_sizes_and_validation(lib):

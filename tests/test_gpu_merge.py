@@ -15,7 +15,8 @@ KEY_DTYPES = [np.int32, np.uint32, np.int64, np.uint64]
 
 
 def sizes_for(dt, vb=0):
-    t = cr.tile_size(key_type(np.empty(0, dt)), vb)
+    # the tile of the small single merges built here (geometry class "small")
+    t = cr.tile_size(key_type(np.empty(0, dt)), vb, 1, 1)
     return [(0, 0), (1, 0), (0, 1), (1, 1), (3, 5), (17, 0), (0, 29), (t - 1, 1), (t, t),
             (2 * t + 3, t - 5), (5 * t + 11, 7), (7, 4 * t + 9), (1000, 3 * t + 777)]
 
@@ -37,7 +38,7 @@ def test_merge_keys_and_tags(dt):
 @pytest.mark.parametrize("dt", KEY_DTYPES)
 def test_special_orders(dt):
     """All keys equal; A entirely below B; B entirely below A."""
-    t = cr.tile_size(key_type(np.empty(0, dt)))
+    t = cr.tile_size(key_type(np.empty(0, dt)), 0, 1, 1)
     m, n = 3 * t + 5, 2 * t + 9
     info = np.iinfo(dt)
     cases = [
@@ -231,7 +232,7 @@ def test_shared_corank_table_path(dt, vdt):
     vb = np.dtype(vdt).itemsize if vdt else 0
     kt = key_type(np.empty(0, dt))
     code = _lib.KEY_TYPES[kt]
-    t = cr.tile_size(kt, vb)
+    t = cr.tile_size(kt, vb, 1, 1)      # tile of these small merges
     for m, n in [(1, 0), (5 * t + 3, 2 * t - 1), (t, 7 * t), (123457, 98765)]:
         A = sorted_keys(rng, m, dt, 300)
         B = sorted_keys(rng, n, dt, 300)
@@ -280,8 +281,9 @@ def test_streaming_merge_block_edges(dt):
     tiles per CTA, one tile per CTA, more CTAs than tiles, and inputs whose
     ends fall inside a 16-byte unit."""
     rng = np.random.default_rng(106)
-    t = cr.tile_size(key_type(np.empty(0, dt)))
+    t = cr.tile_size(key_type(np.empty(0, dt)), 0, 1, 1)    # these merges are small
     for total in (t * 152 - 1, t * 304 + 5, t * 700 + 13, 3 * t + 1):
+        assert cr.tile_size(key_type(np.empty(0, dt)), 0, total // 2, total - total // 2) == t
         for frac in (0.0, 0.01, 0.5, 0.97, 1.0):
             m = int(total * frac)
             n = total - m

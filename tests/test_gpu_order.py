@@ -56,7 +56,7 @@ def in_order(x, kt):
 @pytest.mark.parametrize("kt", ORDERS)
 def test_merge_with_tags_and_co_ranks(kt):
     rng = np.random.default_rng(400)
-    t = cr.tile_size(kt, 0)
+    t = cr.tile_size(kt, 0, 1, 1)       # tile of these small merges
     for m, n in [(0, 5), (7, 0), (3 * t + 5, 2 * t - 1), (100, 9 * t), (20000, 20000)]:
         for distinct in (None, 9):
             A = in_order(draw(rng, m, kt, distinct), kt)

@@ -28,9 +28,15 @@ def lib():
 @pytest.mark.host_only
 def test_noalloc_rejects_oversize_without_gpu(lib):
     """Beyond the array's capacity the call is refused before any launch.
-    The sizes exceed the capacity under every tile shape (TILE <= 4096), so
-    the refusal does not depend on which shape the call's geometry selects."""
-    too_many = MAX_TILES * 4096 + 1
+    The sizes exceed the capacity under every tile shape the library offers
+    (MAX_TILES times the largest TILE), so the refusal does not depend on
+    which shape the call's geometry selects."""
+    nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    largest = 0
+    for s in range(lib.cr_tile_shape_count()):
+        assert lib.cr_tile_shape_info(s, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp)) == 0
+        largest = max(largest, nt.value * ipt.value * ilp.value)
+    too_many = MAX_TILES * largest + 1
     for code, (m, n) in ((0, (too_many, 0)), (0, (too_many // 2, too_many // 2 + 1)),
                          (3, (too_many, 0)), (3, (1, too_many))):
         assert (m + n + lib.cr_tile_size_for(code, 0, m, n) - 1) // \
