@@ -348,10 +348,11 @@ cr_status cr_sort_runs_backward_recorded(int val_bytes, int64_t N, const uint16_
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
  *     before any stream capture begins.
- *   - Size limit: m + n at most 131064 tiles of cr_tile_size(key_type, 0)
- *     elements each (with the default shapes: 503,285,760 elements for 4-byte
- *     keys, 234,866,688 for 8-byte keys).  Larger requests return CR_EINVAL
- *     and launch nothing.
+ *   - Size limit: m + n at most 131064 tiles of cr_tile_size_for(key_type,
+ *     0, m, n) elements each (with the compiled-in shapes: 503,285,760
+ *     elements for 4-byte keys, 234,866,688 for 8-byte keys; more with
+ *     larger tiles selected).  Larger requests return CR_EINVAL and launch
+ *     nothing.
  *   - Every call shares the array; calls whose kernels overlap on the GPU
  *     (other streams, other host threads) race and may give wrong output, so
  *     serialise them on one stream.  Device-side status is not reported for
