@@ -275,6 +275,30 @@ def test_shared_corank_table_path(dt, vdt):
         cr.workspace_status(ws)
 
 
+@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+def test_geometry_class_boundary(dt):
+    """Merges just inside and just outside the small-merge class (m + n =
+    2^23 and 2^23 + 1), where the tile shape may switch: each uses the tile
+    cr_tile_size_for reports (its workspace is sized for it) and equals the
+    oracle's merge, keys and tags."""
+    rng = np.random.default_rng(108)
+    kt = key_type(np.empty(0, dt))
+    limit = 1 << 23
+    for m, n in ((limit // 2, limit // 2), (limit // 2, limit // 2 + 1), (7, limit - 7),
+                 (7, limit), (limit // 16, limit - limit // 16 + 1)):
+        A = sorted_keys(rng, m, dt, 5000)
+        B = sorted_keys(rng, n, dt, 5000)
+        t = cr.tile_size(kt, 0, m, n)
+        assert t > 0
+        need = cr.merge_workspace_bytes(kt, 0, m, n)
+        assert need == 256 + 32 * ((m + n + t - 1) // t)
+        C, T = cr.merge(dev(A), dev(B), key_type=kt, tag=True)
+        torch.cuda.synchronize()
+        want, src = oracle.merge(A, B)
+        assert same_bits(host(C, dt), want), (m, n)
+        assert np.array_equal(host(T, np.uint32).astype(np.int64), src), (m, n)
+
+
 @pytest.mark.parametrize("dt", [np.int32, np.int64])
 def test_streaming_merge_block_edges(dt):
     """Sizes around the streaming kernel's block and chunk boundaries: a few
