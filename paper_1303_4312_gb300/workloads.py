@@ -142,13 +142,17 @@ def batched_i32_f32(seed: int = 6, nseg: int = 8192, max_log2: int = 18):
     return a_off, b_off, A, Av, B, Bv
 
 
-def sort_u64_f32(seed: int = 7, shift: int = 0, run: int = 1024, distinct: int = 1 << 20):
-    """uint64 keys from `distinct` values, runs of `run` sorted stably (payload follows)."""
+def sort_u64_f32(seed: int = 7, shift: int = 0, run: int | None = 1024,
+                 distinct: int = 1 << 20):
+    """uint64 keys from `distinct` values, runs of `run` sorted stably (payload
+    follows; run=None: left unsorted)."""
     r = _rng(seed)
     N = (1 << 27) >> shift
     vals = distinct_values(r, distinct, np.uint64)
     X = vals[r.integers(0, len(vals), size=N)]
     Xv = r.standard_normal(N, dtype=np.float32)
+    if run is None:
+        return X, Xv
     for a0 in range(0, N, run):
         o = np.argsort(X[a0:a0 + run], kind="stable")
         X[a0:a0 + run] = X[a0:a0 + run][o]
