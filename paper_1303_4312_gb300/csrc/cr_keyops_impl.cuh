@@ -212,7 +212,7 @@ cudaError_t KeyOps<K>::partition_batched(const void* A, const void* B, const int
                                             prefix);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || max_tiles <= 0) return e;
-    partition_batched_kernel<K><<<blocks_for(max_tiles, 256), 256, 0, st>>>(
+    partition_batched_kernel<K><<<blocks_for(max_tiles, 255), 256, 0, st>>>(
         static_cast<const K*>(A), static_cast<const K*>(B), a_off, b_off, nseg, tile, prefix, ws,
         order);
     return cudaGetLastError();

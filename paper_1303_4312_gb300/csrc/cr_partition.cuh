@@ -404,31 +404,50 @@ static __global__ void __launch_bounds__(1024) segment_scan_kernel(const int64_t
     }
 }
 
-// Batched merge, step 2: one thread per tile finds its segment in the tile
-// prefix (binary search) and co-ranks both tile ends inside the segment.
+// Batched merge, step 2: a block of 256 threads owns tiles tb .. tb+254
+// (tb = 255 * blockIdx.x) and the 256 tile starts tb .. tb+255.  Thread i
+// finds the segment of tile tb + i in the tile prefix (binary search) and
+// co-ranks that tile's start inside its segment with Algorithm 1 as printed;
+// a tile ends where the next tile of its segment starts (the neighbouring
+// thread's co-rank) or at its segment's end, whose co-rank is m.  So every
+// tile start is searched once.
 template <class K>
-__global__ void partition_batched_kernel(const K* Ap, const K* Bp, const int64_t* a_off,
-                                         const int64_t* b_off, int64_t nseg, int64_t tile,
-                                         const int64_t* prefix, void* ws, int order) {
+__global__ void __launch_bounds__(256) partition_batched_kernel(
+    const K* Ap, const K* Bp, const int64_t* a_off, const int64_t* b_off, int64_t nseg,
+    int64_t tile, const int64_t* prefix, void* ws, int order) {
     const KeyView<K> A{Ap, order}, B{Bp, order};
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    __shared__ int64_t s_j[256];
+    __shared__ int64_t s_seg[256];
     const int64_t ntiles = static_cast<const WsHeader*>(ws)->ntiles;
-    if (t >= ntiles) return;
-    // largest s < nseg with prefix[s] <= t (empty segments are skipped)
-    int64_t lo = 0, hi = nseg;   // invariant: prefix[lo] <= t < prefix[hi]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (prefix[mid] <= t) lo = mid; else hi = mid;
+    const int64_t t = int64_t(blockIdx.x) * 255 + threadIdx.x;
+    int64_t seg = -1, a0 = 0, b0 = 0, m = 0, n = 0, r0 = 0;
+    if (t < ntiles) {
+        // largest s < nseg with prefix[s] <= t (empty segments are skipped)
+        int64_t lo = 0, hi = nseg;   // invariant: prefix[lo] <= t < prefix[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (prefix[mid] <= t) lo = mid; else hi = mid;
+        }
+        seg = lo;
+        a0 = a_off[seg];
+        b0 = b_off[seg];
+        m = a_off[seg + 1] - a0;
+        n = b_off[seg + 1] - b0;
+        r0 = (t - prefix[seg]) * tile;
+        CoRankState st = co_rank_begin(r0, m, n);
+#pragma unroll 1
+        for (int it = 0; it < 128 && !st.done; ++it) co_rank_step(st, A + a0, m, B + b0, n);
+        s_j[threadIdx.x] = co_rank_end(st);
     }
-    const int64_t s = lo;
-    const int64_t a0 = a_off[s], b0 = b_off[s];
-    const int64_t m = a_off[s + 1] - a0;
-    const int64_t n = b_off[s + 1] - b0;
-    const int64_t r0 = (t - prefix[s]) * tile;
-    const int64_t r1 = r0 + tile < m + n ? r0 + tile : m + n;
-    int64_t j0, j1;
-    co_rank_pair(r0, r1, A + a0, m, B + b0, n, j0, j1);
-    ws_recs(ws)[t] = make_rec(a0, b0, a0 + b0, r0, r1, j0, j1);
+    s_seg[threadIdx.x] = seg;   // -1: no tile starts here
+    __syncthreads();
+    if (threadIdx.x < 255 && t < ntiles) {
+        // tile t + 1 exists and lies in this segment: it starts where t ends
+        const bool next_same = s_seg[threadIdx.x + 1] == seg;
+        const int64_t r1 = next_same ? r0 + tile : m + n;
+        const int64_t j1 = next_same ? s_j[threadIdx.x + 1] : m;
+        ws_recs(ws)[t] = make_rec(a0, b0, a0 + b0, r0, r1, s_j[threadIdx.x], j1);
+    }
 }
 
 // co_rank for a list of ranks (C-ABI names: rank k -> (i, j)).
