@@ -353,6 +353,7 @@ static __global__ void __launch_bounds__(1024) segment_scan_kernel(const int64_t
     for (int64_t base = 0; base < nseg; base += 1024 * IT) {
         int64_t cnt[IT];
         int64_t mine = 0;
+        bool bad = false;   // kept in a register: no shared store between the loads
 #pragma unroll
         for (int e = 0; e < IT; ++e) {
             const int64_t s = base + int64_t(tid) * IT + e;
@@ -360,11 +361,12 @@ static __global__ void __launch_bounds__(1024) segment_scan_kernel(const int64_t
             if (s < nseg) {
                 const int64_t ms = a_off[s + 1] - a_off[s];
                 const int64_t ns = b_off[s + 1] - b_off[s];
-                if (ms < 0 || ns < 0) s_bad = 1;
+                if (ms < 0 || ns < 0) bad = true;
                 else cnt[e] = (ms + ns + tile - 1) / tile;
             }
             mine += cnt[e];
         }
+        if (bad) s_bad = 1;
         // block-wide exclusive scan of `mine`
         int64_t incl = mine;
 #pragma unroll
