@@ -155,3 +155,49 @@ def test_merge_beyond_2_31_elements_sampled():
     # the device co-rank at the same ranks agrees with the oracle
     oi, oj = cr.co_rank_many(A, B, torch.from_numpy(ranks).cuda())
     assert np.array_equal(oi.cpu().numpy(), j) and np.array_equal(oj.cpu().numpy(), k)
+
+
+def test_merge_sort_beyond_2_31_elements_properties():
+    """64-bit indexing through the whole sort chain (run formation in the
+    shared-memory stage, then 20 recorded passes) on 2^31 + 4097 unsorted
+    int32 keys with many ties.  The payload of element x is its index x (as
+    uint32 bits), so the result is checked exactly by properties that fix a
+    stable sort at any size: the keys come out ordered, the payloads form a
+    permutation that reproduces them (Y[t] = X[idx[t]]), equal keys keep
+    increasing indices (stability), and the payload gradient is routed
+    through that same permutation (gX[idx[t]] = gY[t]).  The checks run in
+    chunks and are reduced to plain booleans before any assert, so a failure
+    never formats a 2^31-element tensor."""
+    _free()
+    N = (1 << 31) + 4097
+    g = torch.Generator(device="cuda").manual_seed(131)
+    X = torch.randint(0, 1 << 20, (N,), generator=g, device="cuda", dtype=torch.int32)
+    Xv = torch.arange(N, device="cuda", dtype=torch.int64).to(torch.int32)
+    Xv = Xv.view(torch.float32).clone().requires_grad_(True)     # index bits as payload
+    Y, Yv = cr.merge_sort(X, Xv, key_type="i32")
+    gY = torch.arange(N, device="cuda", dtype=torch.int64).mul_(7).remainder_(1 << 23)
+    gY = gY.to(torch.int32).view(torch.float32)                  # exact, distinct bit patterns
+    Yv.backward(gY)
+    torch.cuda.synchronize()
+    ok = {"sorted": True, "gather": True, "stable": True, "grad": True}
+    seen = torch.zeros(N, dtype=torch.int8, device="cuda")
+    gX, gy, pv = Xv.grad.view(torch.int32), gY.view(torch.int32), Yv.detach().view(torch.int32)
+    C = 1 << 28
+    for c0 in range(0, N, C):
+        c1 = min(N, c0 + C)
+        p = pv[c0:c1].to(torch.int64) & 0xFFFFFFFF              # idx[t], read as uint32
+        y = Y[c0:c1]
+        ok["sorted"] &= bool((y[1:] >= y[:-1]).all())
+        ok["stable"] &= bool(((p[1:] > p[:-1]) | (y[1:] != y[:-1])).all())
+        if c0 > 0:                                               # across the chunk seam
+            yp, y0 = int(Y[c0 - 1]), int(y[0])
+            pp, p0 = int(pv[c0 - 1]) & 0xFFFFFFFF, int(p[0])
+            ok["sorted"] &= yp <= y0
+            ok["stable"] &= yp != y0 or pp < p0
+        ok["gather"] &= bool((X[p] == y).all())
+        ok["grad"] &= bool((gX[p] == gy[c0:c1]).all())
+        seen[p] = 1
+        del p, y
+    ok["permutation"] = bool(seen.all())
+    del seen
+    assert all(ok.values()), ok
