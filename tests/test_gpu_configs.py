@@ -199,5 +199,8 @@ def test_merge_sort_beyond_2_31_elements_properties():
         seen[p] = 1
         del p, y
     ok["permutation"] = bool(seen.all())
-    del seen
+    # release the ~115 GB before asserting: a failing test's frame would
+    # otherwise keep it alive for the rest of the session
+    del seen, gX, gy, pv, X, Xv, Y, Yv, gY
+    _free()
     assert all(ok.values()), ok
