@@ -281,7 +281,8 @@ cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int
  * Layout of `flags` (uint32 words, 16-byte aligned, flag_words words): tile
  * t of the pass owns words [t*TILE/32, (t+1)*TILE/32); bit x % 32 of word
  * t*TILE/32 + x/32 is set when the tile's output x came from the pair's
- * second run (TILE is the key type's current tile size, cr_tile_size_for).
+ * second run (TILE = cr_tile_size(key_type, val_bytes): merge passes use the
+ * balanced-class shape).
  * Sizes: cr_merge_pass_record_size gives the workspace bytes and flag words
  * for (key_type, val_bytes, N, width) under the current tile shape.
  *
