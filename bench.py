@@ -900,12 +900,22 @@ def time_oracle(host_inputs, threads: int):
 
 
 def cpu_baseline_from(merges):
+    """The oracle's Algorithm 2 on all host cores over full steps of the same
+    inputs: one warm-up step, then steps until about 10 core-seconds of work
+    (at most 20); elements over the summed step times."""
     hi = _host_inputs(merges)
     cores = os.cpu_count() or 1
-    value, secs = time_oracle(hi, cores)
-    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "one full step (all three merges) on the CPU oracle's Algorithm 2 "
-                      f"with {cores} POSIX threads; {secs:.2f} s"}
+    elems = sum(len(a) + len(b) for _, a, b in hi)
+    time_oracle(hi, cores)
+    total, reps = 0.0, 0
+    while reps < 20 and (reps == 0 or total * cores < 10.0):
+        _, secs = time_oracle(hi, cores)
+        total += secs
+        reps += 1
+    return {"value": reps * elems / total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} full steps (all three merges, {elems} elements each) on the CPU "
+                      f"oracle's Algorithm 2 with {cores} POSIX threads after one warm-up "
+                      f"step; {total:.2f} s wall, about {total * cores:.0f} core-seconds"}
 
 
 def run_reference(args, rank, world):
