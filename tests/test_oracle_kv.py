@@ -118,7 +118,8 @@ def test_batched_vs_per_segment_argsort():
         np.testing.assert_array_equal(gB[b], g[ms[q]:])
 
 
-@pytest.mark.parametrize("N,run", [(1 << 12, 16), (5000, 64), (4096 + 17, 1024), (1, 4), (0, 8)])
+@pytest.mark.parametrize("N,run", [(1 << 12, 16), (5000, 64), (4096 + 17, 1024), (1, 4), (0, 8),
+                                   (3001, 1)])
 def test_merge_sort_vs_stable_argsort(N, run):
     """Bottom-up merge sort from sorted runs = numpy stable argsort (unsigned
     64-bit keys from few distinct values, so ties are common), and its payload
