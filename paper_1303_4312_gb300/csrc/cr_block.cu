@@ -31,6 +31,7 @@
 // is scattered through shared memory.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/corank.h"
@@ -302,6 +303,22 @@ cudaError_t block_sort_runs(int key_type, int vb, int mode, const void* X, const
 cudaError_t chunk_route_recorded(int vb, int64_t N, int64_t chunk, const uint16_t* perm,
                                  const void* gY, void* gX, cudaStream_t st);
 
+void set_last_error(const char* msg);   // cr_abi.cu
+
+namespace {
+// Status with its cr_last_error() detail ("" on success).
+cr_status block_fail(cr_status st, const char* msg) {
+    set_last_error(msg);
+    return st;
+}
+cr_status block_done(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return block_fail(CR_OK, "");
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    return block_fail(CR_ECUDA, buf);
+}
+}  // namespace
+
 }  // namespace cr
 
 extern "C" int64_t cr_merge_runs_block_length(void) { return cr::kBlockR; }
@@ -310,17 +327,22 @@ extern "C" cr_status cr_merge_runs_block(int key_type, int val_bytes, const void
                                          const void* Xv, int64_t N, int64_t width, void* Y,
                                          void* Yv, uint16_t* perm, cr_stream stream) {
     const int ks = cr::key_type_bytes(key_type);
-    if (ks == 0 || N < 0) return CR_EINVAL;
-    if (!(val_bytes == 0 || val_bytes == 4 || val_bytes == 8)) return CR_EINVAL;
-    if (perm != nullptr && val_bytes == 0) return CR_EINVAL;
-    if (width < 1 || width > cr::kBlockR / 2 || (width & (width - 1)) != 0) return CR_EINVAL;
-    if (N == 0) return CR_OK;
+    if (ks == 0) return cr::block_fail(CR_EINVAL, "unknown key type");
+    if (N < 0) return cr::block_fail(CR_EINVAL, "negative size");
+    if (!(val_bytes == 0 || val_bytes == 4 || val_bytes == 8))
+        return cr::block_fail(CR_EINVAL, "payload width must be 0, 4 or 8");
+    if (perm != nullptr && val_bytes == 0)
+        return cr::block_fail(CR_EINVAL, "a permutation needs payloads");
+    if (width < 1 || width > cr::kBlockR / 2 || (width & (width - 1)) != 0)
+        return cr::block_fail(CR_EINVAL, "width must be a power of two in [1, 2048]");
+    if (N == 0) return cr::block_fail(CR_OK, "");
     const void* arrs[5] = {X, Y, val_bytes ? Xv : nullptr, val_bytes ? Yv : nullptr, perm};
     const bool need[5] = {true, true, val_bytes != 0, val_bytes != 0, perm != nullptr};
     for (int i = 0; i < 5; ++i) {
         if (!need[i]) continue;
-        if (arrs[i] == nullptr) return CR_EINVAL;
-        if (reinterpret_cast<uintptr_t>(arrs[i]) & 15u) return CR_EALIGN;
+        if (arrs[i] == nullptr) return cr::block_fail(CR_EINVAL, "NULL array");
+        if (reinterpret_cast<uintptr_t>(arrs[i]) & 15u)
+            return cr::block_fail(CR_EALIGN, "array not 16-byte aligned");
     }
     const int64_t kb = N * ks, vbb = N * val_bytes, pb = perm ? N * 2 : 0;
     if (cr::overlaps(Y, kb, X, kb) || (val_bytes && cr::overlaps(Y, kb, Xv, vbb)) ||
@@ -329,7 +351,7 @@ extern "C" cr_status cr_merge_runs_block(int key_type, int val_bytes, const void
         (perm && (cr::overlaps(perm, pb, X, kb) || cr::overlaps(perm, pb, Y, kb) ||
                   (val_bytes && (cr::overlaps(perm, pb, Xv, vbb) ||
                                  cr::overlaps(perm, pb, Yv, vbb))))))
-        return CR_EALIAS;
+        return cr::block_fail(CR_EALIAS, "an output overlaps another array");
     const int order = cr::key_type_order(key_type);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int w0 = int(width);
@@ -337,21 +359,24 @@ extern "C" cr_status cr_merge_runs_block(int key_type, int val_bytes, const void
         using K = decltype(k);
         return cr::block_dispatch<K>(val_bytes, X, Xv, N, w0, Y, Yv, perm, order, st);
     });
-    return e == cudaSuccess ? CR_OK : CR_ECUDA;
+    return cr::block_done(e, "merge block launch");
 }
 
 extern "C" cr_status cr_merge_runs_block_backward_recorded(int val_bytes, int64_t N,
                                                            const uint16_t* perm, const void* gY,
                                                            void* gX, cr_stream stream) {
-    if (!(val_bytes == 4 || val_bytes == 8) || N < 0) return CR_EINVAL;
-    if (N == 0) return CR_OK;
-    if (!perm || !gY || !gX) return CR_EINVAL;
+    if (!(val_bytes == 4 || val_bytes == 8))
+        return cr::block_fail(CR_EINVAL, "payload width must be 4 or 8");
+    if (N < 0) return cr::block_fail(CR_EINVAL, "negative size");
+    if (N == 0) return cr::block_fail(CR_OK, "");
+    if (!perm || !gY || !gX) return cr::block_fail(CR_EINVAL, "NULL array");
     if ((reinterpret_cast<uintptr_t>(perm) | reinterpret_cast<uintptr_t>(gY) |
          reinterpret_cast<uintptr_t>(gX)) & 15u)
-        return CR_EALIGN;
+        return cr::block_fail(CR_EALIGN, "array not 16-byte aligned");
     const int64_t b = N * val_bytes;
-    if (cr::overlaps(gX, b, gY, b) || cr::overlaps(gX, b, perm, N * 2)) return CR_EALIAS;
+    if (cr::overlaps(gX, b, gY, b) || cr::overlaps(gX, b, perm, N * 2))
+        return cr::block_fail(CR_EALIAS, "gX overlaps another array");
     const cudaError_t e = cr::chunk_route_recorded(val_bytes, N, cr::kBlockR, perm, gY, gX,
                                                    static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? CR_OK : CR_ECUDA;
+    return cr::block_done(e, "merge block backward launch");
 }

@@ -47,14 +47,27 @@ cudaError_t run_check(const void* A, int64_t m, int order, unsigned long long* s
 
 }  // namespace
 
+namespace cr {
+void set_last_error(const char* msg);   // cr_abi.cu
+}
+
+namespace {
+cr_status check_fail(cr_status st, const char* msg) {
+    cr::set_last_error(msg);
+    return st;
+}
+}  // namespace
+
 extern "C" cr_status cr_check_sorted(int key_type, const void* A, int64_t m, int64_t* d_first,
                                      void* ws, size_t ws_bytes, cr_stream stream) {
-    if (cr::key_type_bytes(key_type) == 0 || m < 0) return CR_EINVAL;
-    if ((m > 0 && A == nullptr) || d_first == nullptr || ws == nullptr || ws_bytes < 16)
-        return CR_EINVAL;
+    if (cr::key_type_bytes(key_type) == 0) return check_fail(CR_EINVAL, "unknown key type");
+    if (m < 0) return check_fail(CR_EINVAL, "negative size");
+    if ((m > 0 && A == nullptr) || d_first == nullptr || ws == nullptr)
+        return check_fail(CR_EINVAL, "NULL array");
+    if (ws_bytes < 16) return check_fail(CR_EINVAL, "scratch smaller than 16 bytes");
     if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(ws) & 15u) ||
         (reinterpret_cast<uintptr_t>(d_first) & 7u))
-        return CR_EALIGN;
+        return check_fail(CR_EALIGN, "A or the scratch not 16-byte aligned, or d_first not 8");
     const int order = cr::key_type_order(key_type);
     auto* scratch = static_cast<unsigned long long*>(ws);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -67,5 +80,6 @@ extern "C" cr_status cr_check_sorted(int key_type, const void* A, int64_t m, int
         case CR_KEY_F64: e = run_check<int64_t>(A, m, order, scratch, d_first, st); break;
         default: e = run_check<uint64_t>(A, m, order, scratch, d_first, st); break;
     }
-    return e == cudaSuccess ? CR_OK : CR_ECUDA;
+    if (e != cudaSuccess) return check_fail(CR_ECUDA, cudaGetErrorString(e));
+    return check_fail(CR_OK, "");
 }

@@ -30,13 +30,24 @@ __global__ void bounded_wait_kernel(void* ws, uint64_t limit_ns, uint64_t* elaps
 
 }  // namespace
 
+namespace cr {
+void set_last_error(const char* msg);   // cr_abi.cu
+}
+
 extern "C" cr_status cr_selftest_bounded_wait(void* ws, size_t ws_bytes, uint64_t limit_ns,
                                               uint64_t* d_elapsed_ns, cr_stream stream) {
     if (ws == nullptr || ws_bytes < sizeof(cr::WsHeader) ||
-        (reinterpret_cast<uintptr_t>(ws) & 15u) != 0)
+        (reinterpret_cast<uintptr_t>(ws) & 15u) != 0) {
+        cr::set_last_error("workspace NULL, too small or not 16-byte aligned");
         return CR_EINVAL;
-    if (limit_ns == 0 || limit_ns > 100000000ull) return CR_EINVAL;   // at most 100 ms
+    }
+    if (limit_ns == 0 || limit_ns > 100000000ull) {   // at most 100 ms
+        cr::set_last_error("limit_ns must be in [1, 10^8]");
+        return CR_EINVAL;
+    }
     bounded_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(ws, limit_ns,
                                                                         d_elapsed_ns);
-    return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ECUDA;
+    const cudaError_t e = cudaGetLastError();
+    cr::set_last_error(e == cudaSuccess ? "" : cudaGetErrorString(e));
+    return e == cudaSuccess ? CR_OK : CR_ECUDA;
 }

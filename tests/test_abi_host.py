@@ -258,6 +258,7 @@ def test_merge_runs_block_validation(lib):
     assert R == 4096
     for bad in (0, -1, 3, 6, 12, R, 2 * R):
         assert lib.cr_merge_runs_block(0, 4, X, Xv, N, bad, Y, Yv, P, None) == 1, bad
+        assert b"width" in lib.cr_last_error()
     assert lib.cr_merge_runs_block(0, 2, X, Xv, N, 1, Y, Yv, P, None) == 1
     assert lib.cr_merge_runs_block(0, 0, X, None, N, 1, Y, None, P, None) == 1
     assert lib.cr_merge_runs_block(99, 4, X, Xv, N, 1, Y, Yv, P, None) == 1
@@ -268,7 +269,9 @@ def test_merge_runs_block_validation(lib):
                                    None) == 2
     assert lib.cr_merge_runs_block(0, 4, X, Xv, N, 1, Y, Yv, ctypes.c_void_p(0x300100),
                                    None) == 2
+    assert b"overlap" in lib.cr_last_error()
     assert lib.cr_merge_runs_block(0, 4, X, Xv, 0, 1, Y, Yv, P, None) == 0
+    assert lib.cr_last_error() == b""
     G, GX = ctypes.c_void_p(0x600000), ctypes.c_void_p(0x700000)
     assert lib.cr_merge_runs_block_backward_recorded(0, N, P, G, GX, None) == 1
     assert lib.cr_merge_runs_block_backward_recorded(4, N, P, G, ctypes.c_void_p(0x600100),
@@ -304,6 +307,7 @@ def test_selftest_argument_checks(lib):
     assert lib.cr_selftest_bounded_wait(ctypes.c_void_p(0x100004), 256, 1000, None, None) == 1
     assert lib.cr_selftest_bounded_wait(WS, 256, 0, None, None) == 1
     assert lib.cr_selftest_bounded_wait(WS, 256, 10**9, None, None) == 1
+    assert b"limit_ns" in lib.cr_last_error()
 
 
 def test_check_sorted_argument_checks(lib):
@@ -314,3 +318,4 @@ def test_check_sorted_argument_checks(lib):
     assert lib.cr_check_sorted(0, A, 10, None, WS, 16, None) == 1
     assert lib.cr_check_sorted(0, A, 10, O, WS, 8, None) == 1
     assert lib.cr_check_sorted(0, ctypes.c_void_p(0x100004), 10, O, WS, 16, None) == 3
+    assert b"aligned" in lib.cr_last_error()
