@@ -322,6 +322,7 @@ def run_ours(args, rank, world, local, dist):
         api.workspace_status(mg["ws"])
 
     total_ms = evs[0][0][0].elapsed_time(evs[K - 1][-1][2])
+    step_spans = sorted(evs[k][0][0].elapsed_time(evs[k][-1][2]) for k in range(K))
     part_ms = {mg["name"]: sum(evs[k][q][0].elapsed_time(evs[k][q][1]) for k in range(K)) / K
                for q, mg in enumerate(merges)}
     tile_ms = {mg["name"]: sum(evs[k][q][1].elapsed_time(evs[k][q][2]) for k in range(K))
@@ -364,6 +365,8 @@ def run_ours(args, rank, world, local, dist):
         "frac_of_peak_step": round(step_gbs / peak, 4),
         "per_merge": per_merge,
         "partition_ms_per_step": round(sum(part_ms.values()), 4),
+        "step_ms": {"median": round(step_spans[K // 2], 4), "best": round(step_spans[0], 4),
+                    "worst": round(step_spans[-1], 4)},
 
         "roofline": {"kernel": "merge_tiles_kernel", "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
