@@ -160,6 +160,43 @@ def test_batched(dt, vdt):
         assert same_bits(host(gB, vdt), gb)
 
 
+@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+def test_batched_segments_across_partition_blocks(dt):
+    """Segments whose tiles span several blocks of the batched partition (a
+    block owns 255 tiles and takes the end of its last tile from the next
+    block's first co-rank), a lone segment, segments of exactly 255 tiles,
+    and a table of empty segments only: keys, payloads and gradients equal
+    the oracle's."""
+    rng = np.random.default_rng(109)
+    kt = key_type(np.empty(0, dt))
+    t = cr.tile_size(kt, 4)                 # batched calls use the balanced shape
+    cases = [
+        ([255 * t // 2 + 7, 3, 600 * t // 2], [255 * t // 2 - 5, 0, 600 * t // 2 + 11]),
+        ([5 * t + 1], [7 * t - 3]),
+        ([0, 255 * t, 0, 1], [1, 0, 255 * t, 0]),
+        ([0, 0, 0], [0, 0, 0]),
+    ]
+    for ms, ns in cases:
+        ms, ns = np.array(ms, np.int64), np.array(ns, np.int64)
+        a_off = np.concatenate([[0], np.cumsum(ms)])
+        b_off = np.concatenate([[0], np.cumsum(ns)])
+        A = np.concatenate([sorted_keys(rng, int(x), dt, 900) for x in ms])
+        B = np.concatenate([sorted_keys(rng, int(x), dt, 900) for x in ns])
+        Av = rng.standard_normal(len(A)).astype(np.float32)
+        Bv = rng.standard_normal(len(B)).astype(np.float32)
+        Ck, Cv = cr.batched_merge_kv(a_off, b_off, dev(A), dev(Av), dev(B), dev(Bv),
+                                     key_type=kt)
+        gC = rng.standard_normal(len(A) + len(B)).astype(np.float32)
+        gA, gB = cr.batched_merge_kv_backward(a_off, b_off, dev(A), dev(B), dev(gC),
+                                              key_type=kt)
+        torch.cuda.synchronize()
+        wk, wv = oracle.batched_merge_kv(a_off, b_off, A, Av, B, Bv)
+        ga, gb = oracle.batched_merge_grad(a_off, b_off, A, B, gC)
+        assert same_bits(host(Ck, dt), wk), (list(ms), list(ns))
+        assert same_bits(host(Cv, np.float32), wv), (list(ms), list(ns))
+        assert same_bits(host(gA, np.float32), ga) and same_bits(host(gB, np.float32), gb)
+
+
 def test_batched_bad_table_reports():
     A = np.arange(100, dtype=np.int32)
     B = np.arange(100, dtype=np.int32)
