@@ -44,7 +44,8 @@ namespace {
 constexpr int kBlockR = 4096;
 constexpr int kBlockIPT = 8;
 constexpr int kBlockNT = kBlockR / kBlockIPT;   // 512
-constexpr int kBlockMinWidth = kBlockIPT;       // narrowest merge round: 2w multiple of IPT
+// merge rounds start at width >= IPT (below it, FORM sorts groups of IPT),
+// so 2w is a multiple of IPT and a thread's outputs lie in one pair
 static_assert(kBlockR == kSortRun, "run formation sorts chunks of the merge stage");
 
 template <class K>
