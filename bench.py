@@ -829,6 +829,30 @@ def run_row(args):
         torch.cuda.synchronize()
         un = {lb: round(ms / K, 4) for lb, ms in timer.totals().items()}
         stages_un = [f"{kd}:{w}" for kd, w in plan.stages]
+        del plan
+        torch.cuda.empty_cache()
+        # the same from unsorted input in the recompute form: runs of 4096
+        # formed by cr_sort_runs, backward by replaying it and re-merging
+        plan = api.MergeSortPlan(N, None, Xu.dtype, Xuv.dtype, dev, key_type="u64", graph=True,
+                                 record=False)
+        plan.forward(Xu, Xuv)
+        plan.backward(gY)
+        timer = KernelTimer(stream)
+        for k in range(Wm + K):
+            t = k >= Wm
+            plan._load(Xu, Xuv)
+            plan.grads[plan.passes & 1].copy_(gY)
+            if t:
+                timer.mark()
+            plan._gf.replay()
+            if t:
+                timer.mark("fwd_graph")
+            plan._gb.replay()
+            if t:
+                timer.mark("bwd_graph")
+                timer.marks.append((None, timer.marks[-1][1]))
+        torch.cuda.synchronize()
+        un_re = {lb: round(ms / K, 4) for lb, ms in timer.totals().items()}
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         Yk, Yv = torch.empty_like(Xu), torch.empty_like(Xuv)
         gXr = torch.empty_like(gY)
@@ -853,9 +877,13 @@ def run_row(args):
         # sort_runs_record's launch).  Bytes per element: keys + payloads in
         # and out; backward replay reads keys and gY, writes gX; the recorded
         # forms add / read the 2-byte permutation instead of the keys
-        unsorted = {"stages": stages_un, "passes": plan.passes,
+        unsorted = {"stages": stages_un, "passes": len(stages_un),
                     "fwd_graph_ms": un["fwd_graph"], "bwd_graph_ms": un["bwd_graph"],
                     "elements_per_s": N / ((un["fwd_graph"] + un["bwd_graph"]) / 1e3),
+                    "recompute": {"fwd_graph_ms": un_re["fwd_graph"],
+                                  "bwd_graph_ms": un_re["bwd_graph"],
+                                  "elements_per_s":
+                                      N / ((un_re["fwd_graph"] + un_re["bwd_graph"]) / 1e3)},
                     "sort_runs_run": api.sort_run_length(),
                     "sort_runs": row(tms[0], 24), "sort_runs_backward": row(tms[1], 16),
                     "sort_runs_record": row(tms[2], 26),
