@@ -25,6 +25,14 @@ MUTANTS = {
     "k_low_update": ("k_low = k; k_low_set = 1;", "k_low_set = 1;"),
     # j_low not raised on the second condition
     "j_low_update": ("j_low = j;", "(void)0;"),
+    # merge pass: payloads taken from the pair-relative position (offset lost)
+    "pass_payload_offset": ("int64_t from = a0 + s[i];", "int64_t from = s[i];"),
+    # merge pass: pairs advance by one run instead of two
+    "pass_stride": ("for (int64_t a0 = 0; a0 < N; a0 += 2 * w) {",
+                    "for (int64_t a0 = 0; a0 < N; a0 += w) {"),
+    # Algorithm 2: block end rounded on its own instead of floor((r+1)(m+n)/p)
+    "alg2_block_end": ("int64_t i1 = (pe->r + 1) * mn / pe->p;",
+                       "int64_t i1 = pe->r * mn / pe->p + mn / pe->p;"),
 }
 
 
