@@ -35,6 +35,56 @@ def test_every_declared_symbol_exported(lib):
         assert name in _lib.SIGNATURES, f"binding lacks {name}"
 
 
+def _header_declarations():
+    """name -> (return type, [parameter types]) for every cr_* function
+    declared in include/corank.h."""
+    src = open(os.path.join(ROOT, "include", "corank.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for ret, name, params in re.findall(
+            r"((?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\*?)\s*\b(cr_[a-z_0-9]+)\s*\(([^)]*)\)\s*;",
+            src):
+        ps = [q.strip() for q in params.split(",") if q.strip() and q.strip() != "void"]
+        types = [re.sub(r"\s*\b[A-Za-z_][A-Za-z_0-9]*$", "", q) if not q.endswith("*")
+                 else q for q in ps]
+        out[name] = (ret.strip(), types)
+    return out
+
+
+def _c_kind(t):
+    t = t.replace("const ", "").strip()
+    if "*" in t or t == "cr_stream":
+        return "ptr"
+    return {"int": "i32", "int64_t": "i64", "size_t": "u64", "uint64_t": "u64",
+            "cr_status": "i32"}[t]
+
+
+def _ctypes_kind(ct):
+    if ct is None:
+        return "void"
+    if ct in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(ct, ctypes._Pointer):
+        return "ptr"
+    if ct is ctypes.c_int:
+        return "i32"
+    if ctypes.sizeof(ct) == 8:
+        return "u64" if ct(-1).value > 0 else "i64"
+    raise AssertionError(ct)
+
+
+def test_binding_signatures_match_header():
+    """Every declaration's parameter kinds (pointer, int, int64, uint64 or
+    size_t) and return kind equal the ctypes signature the binding uses."""
+    decls = _header_declarations()
+    assert set(decls) == set(declared_symbols())
+    for name, (ret, params) in decls.items():
+        argtypes, restype = _lib.SIGNATURES[name]
+        want = [_c_kind(p) for p in params]
+        got = [_ctypes_kind(a) for a in argtypes]
+        assert got == want, (name, params)
+        assert _ctypes_kind(restype) == _c_kind(ret), (name, ret)
+
+
 def test_status_strings(lib):
     for code, name in _lib.STATUS.items():
         assert lib.cr_status_string(code).decode() == name
