@@ -199,3 +199,85 @@ def test_remote_key_order_matches_oracle(kt):
     ref = np.argsort(oracle.order_key(bits, kt if base[0] != "f" else kt), kind="stable")
     got = sorted(range(len(keys)), key=lambda i: keys[i])
     assert np.array_equal(got, ref)
+
+
+def _dist_order_worker(rank, world, port, cases, out_q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        for ci, (A, B, a_cuts, b_cuts, kt) in enumerate(cases):
+            dt = A.dtype
+            carrier = np.int64 if dt.itemsize == 8 else np.int32
+
+            def merge(x, y):
+                c, _ = oracle.merge_in_order(x.numpy().view(dt), y.numpy().view(dt), kt)
+                return torch.from_numpy(c.view(carrier))
+
+            a_t = torch.from_numpy(A[a_cuts[rank]:a_cuts[rank + 1]].copy().view(carrier))
+            b_t = torch.from_numpy(B[b_cuts[rank]:b_cuts[rank + 1]].copy().view(carrier))
+            C, p = shard.distributed_merge(a_t, b_t, kt, merge=merge)
+            out_q.put((ci, rank, (p.k0, p.k1, p.i0, p.i1, p.j0, p.j1), C.numpy().tobytes()))
+    finally:
+        dist.destroy_process_group()
+
+
+def _in_order(x, kt):
+    import oracle
+    return x[np.argsort(oracle.order_key(x, kt), kind="stable")]
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_distributed_merge_in_key_orders(world):
+    """Block-distributed A and B in other key orders (IEEE totalOrder floats
+    with NaNs of both signs, signed zeros and infinities; descending; signed
+    32-bit pairs): the remote co-ranks equal the oracle's co-ranks of the
+    order keys, and every rank's block equals that slice of the oracle's
+    merge in that order."""
+    import oracle
+    rng = np.random.default_rng(140 + world)
+    specials32 = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, -np.nan], np.float32)
+    cases = []
+    for kt, m, n in [("f32", 700, 555), ("f64:desc", 300, 901), ("i64:desc", 64, 0),
+                     ("pair_i32", 1000, 777), ("f32:desc", 0, 33)]:
+        base = kt.split(":")[0]
+        if base == "f32":
+            A = rng.standard_normal(m).astype(np.float32)
+            B = rng.standard_normal(n).astype(np.float32)
+            A[: min(m, 6)] = specials32[: min(m, 6)]
+            B[: min(n, 6)] = specials32[: min(n, 6)]
+        elif base == "f64":
+            A = np.round(rng.standard_normal(m), 1)
+            B = np.round(rng.standard_normal(n), 1)
+        elif base == "i64":
+            A = rng.integers(-5, 5, m).astype(np.int64)
+            B = rng.integers(-5, 5, n).astype(np.int64)
+        else:
+            major = rng.integers(0, 4, m + n).astype(np.uint64) * np.uint64(0x7FFFFFFF)
+            minor = rng.integers(0, 2**32, m + n, dtype=np.uint64)
+            w = (major << np.uint64(32)) | minor
+            A, B = w[:m].copy(), w[m:].copy()
+        A, B = _in_order(A, kt), _in_order(B, kt)
+        cases.append((A, B, _cuts(rng, m, world), _cuts(rng, n, world), kt))
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dist_order_worker, args=(r, world, port, cases, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=180) for _ in range(world * len(cases))]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for ci, (A, B, _, _, kt) in enumerate(cases):
+        want, _ = oracle.merge_in_order(A, B, kt)
+        ka, kb = oracle.order_key(A, kt), oracle.order_key(B, kt)
+        got = sorted((r for r in results if r[0] == ci), key=lambda r: r[1])
+        assert len(got) == world
+        for rank, (_, _, (k0, k1, i0, i1, j0, j1), cb) in enumerate(got):
+            assert (k0, k1) == shard.block_bounds(len(A) + len(B), world, rank)
+            assert (i0, j0) == tuple(oracle.co_rank(k0, ka, kb)[:2]), (kt, rank)
+            assert (i1, j1) == tuple(oracle.co_rank(k1, ka, kb)[:2]), (kt, rank)
+            assert cb == want[k0:k1].tobytes(), (kt, rank)
