@@ -141,61 +141,6 @@ __host__ __device__ inline TileRec* ws_recs(void* ws) {
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1 (Section 2): co-ranks of output rank i.
-//
-// Paper notation: rank i, co-ranks j (into A) and k (into B), j + k = i;
-// the C-ABI calls the same triple (k; i, j).  Starting from j = min(i, m),
-// the search keeps j + k = i and lower bounds j_low, k_low, and halves
-// [j_low, j] while the first Lemma-1 condition fails (A[j-1] > B[k]) or
-// [k_low, k] while the second fails (B[k-1] >= A[j]).  The "conditional
-// and" becomes index guards; the four candidate keys of an iteration are
-// loaded together so that each iteration costs one memory round trip.
-// k_low is set to the starting k: the paper proves it is written before it
-// is read (the first move is always on the first condition).
-//
-// The loop is capped at 128 iterations (Proposition 1 bounds it by about
-// log2 min(m, n) + 1 <= 64 for any int64 size) and every load is
-// range-checked, so unsorted input can give a wrong split but never an
-// out-of-range access or an endless loop; the result is clamped to the
-// valid range [max(0, i-n), min(i, m)].
-// ---------------------------------------------------------------------------
-template <class K, class Idx, class GetA, class GetB>
-__device__ __forceinline__ Idx co_rank(Idx i, Idx m, Idx n, GetA getA, GetB getB) {
-    Idx j = i < m ? i : m;
-    Idx k = i - j;
-    Idx j_low = i - n > 0 ? i - n : Idx(0);
-    Idx k_low = k;
-    const Idx j_min = j_low, j_max = j;
-#pragma unroll 1
-    for (int it = 0; it < 128; ++it) {
-        const bool okA1 = j > 0 && j - 1 < m;   // A[j-1] exists
-        const bool okB0 = k >= 0 && k < n;      // B[k]   exists
-        const bool okB1 = k > 0 && k - 1 < n;   // B[k-1] exists
-        const bool okA0 = j >= 0 && j < m;      // A[j]   exists
-        const K a1 = okA1 ? getA(j - 1) : K(0);
-        const K b0 = okB0 ? getB(k) : K(0);
-        const K b1 = okB1 ? getB(k - 1) : K(0);
-        const K a0 = okA0 ? getA(j) : K(0);
-        if (okA1 && okB0 && a1 > b0) {            // first condition violated
-            const Idx d = (j - j_low + 1) >> 1;
-            k_low = k;
-            j -= d;
-            k += d;
-        } else if (okB1 && okA0 && b1 >= a0) {    // second condition violated
-            const Idx d = (k - k_low + 1) >> 1;
-            j_low = j;
-            j += d;
-            k -= d;
-        } else {
-            break;
-        }
-    }
-    j = j < j_min ? j_min : j;
-    j = j > j_max ? j_max : j;
-    return j;
-}
-
-// ---------------------------------------------------------------------------
 // PTX wrappers (sm_90+ forms, valid on sm_103a).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

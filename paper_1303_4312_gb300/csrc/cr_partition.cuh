@@ -1,19 +1,33 @@
 // cr_partition.cuh -- kernels that place the output tiles: for every tile,
-// the co-ranks of its first and last output rank (Algorithm 1 over the
-// arrays in HBM), written as a TileRec.  These are the "grid-level" co-rank
-// passes; the merge kernel reads the records.
-//
-// Every tile computes both of its ends independently, as each processing
-// element does in Algorithm 2 (no synchronisation between tiles).  The two
-// searches run in lock step so that one round trip to memory serves both.
+// the co-ranks of its first and last output rank over the arrays in HBM,
+// written as a TileRec.  These are the "grid-level" co-rank passes; the
+// merge kernel reads the records.  Single merges and merge passes share each
+// tile boundary between its two tiles (block-level searches, then
+// bisection); the batched partition searches each tile start once with
+// Algorithm 1; the sync-free form gives every tile both of its ends, as each
+// processing element does in Algorithm 2, with the two searches in lock step
+// so that one round trip to memory serves both.  The list-of-ranks and
+// single-rank co-rank kernels of the C ABI are here too.
 #pragma once
 
 #include "cr_device.cuh"
 
 namespace cr {
 
-// Lock-step state of Algorithm 1 (see co_rank in cr_device.cuh for the
-// method; this form advances one iteration per call).
+// Algorithm 1 (Section 2), one iteration per call.  Paper notation: rank i,
+// co-ranks j (into A) and k (into B), j + k = i (the C ABI calls the same
+// triple (k; i, j)).  Starting from j = min(i, m) the search keeps j + k = i
+// and lower bounds j_low, k_low, and halves [j_low, j] while the first
+// Lemma-1 condition fails (A[j-1] > B[k]) or [k_low, k] while the second
+// fails (B[k-1] >= A[j]).  The "conditional and" becomes index guards; the
+// four candidate keys of an iteration are loaded together, one memory round
+// trip per iteration.  k_low starts at the first k: the paper shows it is
+// written before it is read (the first move is on the first condition).
+// Callers cap the loop at 128 iterations (Proposition 1 bounds it by about
+// log2 min(m, n) + 1 <= 64 for any int64 size) and every load is
+// range-checked, so unsorted input can give a wrong split but never an
+// out-of-range access or an endless loop; co_rank_end clamps the result to
+// [max(0, i-n), min(i, m)].
 struct CoRankState {
     int64_t j, k, j_low, k_low, j_min, j_max;
     bool done;
