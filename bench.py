@@ -20,7 +20,14 @@ than L2 (129 MB), so no flush is needed between steps.
             once, each output written once) / its CUDA-event time, against the
             measured HBM copy bandwidth
   cpu_baseline  the CPU oracle (Algorithm 2 on POSIX threads over all host
-            cores) on one full step of the same inputs
+            cores) on full steps of the same inputs
+  rows      the task's other configurations, forward and backward, each timed
+            on its own inputs with CUDA events after the headline (N=1 only):
+            single_i32_tag (keys + tags, L2 flushed), kv_u32_f32 (forward
+            merge, backward with recomputed co-ranks), batched_i32_f32 (8192
+            segment pairs, one call per direction) and sort_u64_f32 (recorded
+            merge-sort chain, one CUDA graph per direction), with a clock
+            record of their own
 
 `--impl reference` times the CPU oracle as the reference arm.
 Launch: python bench.py [--gpus N] [--steps K] [--warmup W]; N>1 via
@@ -65,6 +72,9 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=None,
                    help="steps of the end-to-end measurement (default: --steps)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-rows", action="store_true",
+                   help="skip the other configurations' forward/backward rows of the default "
+                        "line")
     p.add_argument("--shift", type=int, default=0,
                    help="divide every workload size by 2^shift (for quick runs)")
     p.add_argument("--workload", default=WORKLOAD,
@@ -344,6 +354,15 @@ def run_ours(args, rank, world, local, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_from(merges)
 
+    # the other configurations (forward and backward), one GPU only
+    rows = None
+    if world == 1 and not args.no_rows:
+        for mg in merges:
+            del mg["A"], mg["B"], mg["C"], mg["ws"]
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        rows = run_rows(args, lib, dev, stream, peak)
+
     if rank != 0:
         return None
     per_merge = {mg["name"]: {
@@ -359,8 +378,8 @@ def run_ours(args, rank, world, local, dist):
         "data": "synthetic (seeded, sorted; device-generated)",
         "config": {"workload": WORKLOAD, "merges": [f"{m[0]}" for m in MERGES],
                    "elements_per_step": elems, "l2": "inputs larger than L2 (no flush)",
-                   "size_shift": args.shift, "parallelism": f"replicas x{world}",
-                   "tile_shapes": tile_shapes(lib, [("int32", 0, 0), ("uint64", 3, 0)])},
+                   "size_shift": args.shift, "parallelism": f"replicas x{world}"},
+        "tile_shapes": tile_shapes(lib, [("int32", 0, 0), ("uint64", 3, 0)]),
         "hbm_gbs_step": round(step_gbs, 1),
         "frac_of_peak_step": round(step_gbs / peak, 4),
         "per_merge": per_merge,
@@ -377,6 +396,7 @@ def run_ours(args, rank, world, local, dist):
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "algorithmic_bytes_per_launch": alg_bytes / len(merges)},
         "e2e": e2e,
+        "rows": rows,
         "gpu_launches": 2 * len(merges) * K,
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -423,6 +443,237 @@ def run_e2e(args, merges, lib, dev, stream, dist, world):
     return {"value": world * elems * K / (ms / 1e3), "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": K,
             "ms_per_step": ms / K, "api": "HostMerger (pinned host buffers, 3 streams)"}
+
+
+# ---------------------------------------------------------------------------
+# the other configurations, forward and backward, in the default line
+# ---------------------------------------------------------------------------
+def _gbs(nbytes, ms):
+    return nbytes / (ms / 1e3) / 1e9
+
+
+def _dir_row(N, ms, alg_bytes, peak, kernel_ms=None, kernel_bytes=None, launches=None):
+    """One direction of a row: its whole time (every kernel of the call)
+    and, when given, its merge kernel's own time, each as algorithmic GB/s
+    and fractions of the measured and the nominal HBM bandwidth."""
+    g = _gbs(alg_bytes, ms)
+    out = {"ms": round(ms, 4), "elements_per_s": N / (ms / 1e3), "gbs": round(g, 1),
+           "frac": round(g / peak, 4), "frac_nominal": round(g / NOMINAL_HBM_GBS, 4),
+           "alg_bytes": int(alg_bytes)}
+    if kernel_ms is not None:
+        gk = _gbs(kernel_bytes if kernel_bytes is not None else alg_bytes, kernel_ms)
+        out["merge_kernel"] = {"ms": round(kernel_ms, 4), "gbs": round(gk, 1),
+                               "frac": round(gk / peak, 4),
+                               "frac_nominal": round(gk / NOMINAL_HBM_GBS, 4)}
+    if launches is not None:
+        out["launches_per_step"] = launches
+    return out
+
+
+def _timed(stream, K, W, body, labels):
+    """Run body(mark) W + K times; `mark(label)` records an event after a
+    launch (label None opens a step).  Returns per-label mean ms over the K
+    timed steps."""
+    import torch
+    tot = {lb: 0.0 for lb in labels}
+    marks = []
+    for k in range(W + K):
+        cur = []
+
+        def mark(label=None):
+            if k >= W:
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(stream)
+                cur.append((label, ev))
+        body(mark)
+        if k >= W:
+            marks.append(cur)
+    torch.cuda.synchronize()
+    for cur in marks:
+        for (_, a), (label, b) in zip(cur, cur[1:]):
+            if label is not None:
+                tot[label] += a.elapsed_time(b)
+    return {lb: v / K for lb, v in tot.items()}
+
+
+def row_single_tag(lib, dev, stream, K, W, peak, shift):
+    """single_i32_tag: keys and source tags, L2 flushed before every step."""
+    import torch
+    from paper_1303_4312_gb300 import _lib, api
+    from paper_1303_4312_gb300 import workloads as Wk
+    A, B = Wk.single_i32_tag(seed=1, shift=shift)
+    A, B = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    m, n = A.numel(), B.numel()
+    C = torch.empty(m + n, dtype=torch.int32, device=dev)
+    T = torch.empty(m + n, dtype=torch.int32, device=dev)
+    ws = torch.empty(api.merge_workspace_bytes("i32", 0, m, n), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sp = stream.cuda_stream
+    p = lambda t: t.data_ptr()
+
+    def body(mark):
+        flush.fill_(1)
+        mark()
+        _lib.check(lib.cr_merge_partition(0, 0, p(A), m, p(B), n, p(ws), ws.numel(), sp))
+        mark("partition")
+        _lib.check(lib.cr_merge_tiles(0, 0, p(A), None, m, p(B), None, n, p(C), None, p(T),
+                                      p(ws), ws.numel(), sp))
+        mark("tiles")
+    t = _timed(stream, K, W, body, ["partition", "tiles"])
+    api.workspace_status(ws)
+    N = m + n
+    return {"workload": "single_i32_tag", "elements": N, "l2": "flushed before every step",
+            "fwd": _dir_row(N, t["partition"] + t["tiles"], 12 * N, peak, t["tiles"],
+                            launches=2),
+            "note": "2.6M elements: launch- and latency-bound, not an HBM-roofline case"}
+
+
+def row_kv(lib, dev, stream, K, W, peak, shift):
+    """kv_u32_f32: forward key-value merge, backward payload routing with
+    the co-ranks recomputed from the keys (a partition launch of its own)."""
+    import torch
+    from paper_1303_4312_gb300 import _lib, api
+    from paper_1303_4312_gb300 import workloads as Wk
+    Ak, Av, Bk, Bv = Wk.t_kv_u32_f32(device=dev, shift=shift)
+    m, n = Ak.numel(), Bk.numel()
+    N = m + n
+    Ck = torch.empty(N, dtype=torch.int32, device=dev)
+    Cv = torch.empty(N, dtype=torch.float32, device=dev)
+    gC = torch.randn(N, device=dev, generator=torch.Generator(device=dev).manual_seed(15))
+    gA = torch.empty(m, device=dev)
+    gB = torch.empty(n, device=dev)
+    ws = torch.empty(api.merge_workspace_bytes("u32", 4, m, n), dtype=torch.uint8, device=dev)
+    sp = stream.cuda_stream
+    p = lambda t: t.data_ptr()
+
+    def body(mark):
+        mark()
+        _lib.check(lib.cr_merge_partition(1, 4, p(Ak), m, p(Bk), n, p(ws), ws.numel(), sp))
+        mark("fwd_partition")
+        _lib.check(lib.cr_merge_tiles(1, 4, p(Ak), p(Av), m, p(Bk), p(Bv), n, p(Ck), p(Cv), None,
+                                      p(ws), ws.numel(), sp))
+        mark("fwd_tiles")
+        _lib.check(lib.cr_merge_partition(1, 4, p(Ak), m, p(Bk), n, p(ws), ws.numel(), sp))
+        mark("bwd_partition")
+        _lib.check(lib.cr_merge_tiles_backward(1, 4, p(Ak), m, p(Bk), n, p(gC), p(gA), p(gB),
+                                               p(ws), ws.numel(), sp))
+        mark("bwd_tiles")
+    t = _timed(stream, K, W, body, ["fwd_partition", "fwd_tiles", "bwd_partition", "bwd_tiles"])
+    api.workspace_status(ws)
+    return {"workload": "kv_u32_f32", "elements": N,
+            "fwd": _dir_row(N, t["fwd_partition"] + t["fwd_tiles"], 16 * N, peak, t["fwd_tiles"],
+                            launches=2),
+            "bwd": _dir_row(N, t["bwd_partition"] + t["bwd_tiles"], 12 * N, peak, t["bwd_tiles"],
+                            launches=2),
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+def row_batched(lib, dev, stream, K, W, peak, pairs=8192):
+    """batched_i32_f32: one cr_batched_merge_kv call (segment scan,
+    partition, persistent tile merge) and its backward."""
+    import ctypes
+    import torch
+    from paper_1303_4312_gb300 import _lib, api
+    from paper_1303_4312_gb300 import workloads as Wk
+    a_off, b_off, A, Av, B, Bv = Wk.t_batched_i32_f32(device=dev, nseg=pairs)
+    ao = torch.from_numpy(a_off).to(dev)
+    bo = torch.from_numpy(b_off).to(dev)
+    at, bt = A.numel(), B.numel()
+    nseg = len(a_off) - 1
+    N = at + bt
+    Ck = torch.empty(N, dtype=torch.int32, device=dev)
+    Cv = torch.empty(N, dtype=torch.float32, device=dev)
+    gC = torch.randn(N, device=dev, generator=torch.Generator(device=dev).manual_seed(16))
+    gA = torch.empty(at, device=dev)
+    gB = torch.empty(bt, device=dev)
+    need = ctypes.c_size_t()
+    _lib.check(lib.cr_batched_workspace_size(0, 4, nseg, at, bt, ctypes.byref(need)))
+    ws = torch.empty(need.value, dtype=torch.uint8, device=dev)
+    sp = stream.cuda_stream
+    p = lambda t: t.data_ptr()
+
+    def body(mark):
+        mark()
+        _lib.check(lib.cr_batched_merge_kv(0, 4, nseg, p(ao), p(bo), p(A), p(Av), at, p(B), p(Bv),
+                                           bt, p(Ck), p(Cv), p(ws), ws.numel(), sp))
+        mark("fwd")
+        _lib.check(lib.cr_batched_merge_kv_backward(0, 4, nseg, p(ao), p(bo), p(A), at, p(B), bt,
+                                                    p(gC), p(gA), p(gB), p(ws), ws.numel(), sp))
+        mark("bwd")
+    t = _timed(stream, K, W, body, ["fwd", "bwd"])
+    api.workspace_status(ws)
+    nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    shape = lib.cr_get_tile_shape_for(0, 4, 0)
+    lib.cr_tile_shape_info(shape, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
+    return {"workload": "batched_i32_f32", "elements": N, "segments": nseg,
+            "tile_shape": f"{nt.value}x{ipt.value}x{ilp.value}",
+            "fwd": _dir_row(N, t["fwd"], 16 * N, peak, launches=3),
+            "bwd": _dir_row(N, t["bwd"], 12 * N, peak, launches=3),
+            "note": "each direction is one call: segment scan + partition + tile merge"}
+
+
+def row_sort(lib, dev, stream, K, W, peak, shift):
+    """sort_u64_f32: the recorded merge-sort chain from runs of 1024, each
+    direction one CUDA-graph replay (shared-memory stage for the widths below
+    4096, then HBM passes)."""
+    import torch
+    from paper_1303_4312_gb300 import api
+    from paper_1303_4312_gb300 import workloads as Wk
+    X, Xv = Wk.t_sort_u64_f32(device=dev, shift=shift)
+    N = X.numel()
+    gY = torch.randn(N, device=dev, generator=torch.Generator(device=dev).manual_seed(17))
+    plan = api.MergeSortPlan(N, 1024, X.dtype, Xv.dtype, dev, key_type="u64", graph=True,
+                             record=True)
+    plan.forward(X, Xv)
+    plan.backward(gY)
+    fwd_b = sum(26.0 if kd == "block" else 24 + 1 / 8 for kd, _ in plan.stages) * N
+    bwd_b = sum(10.0 if kd == "block" else 8 + 1 / 8 for kd, _ in plan.stages) * N
+
+    def body(mark):
+        plan.keys[0].copy_(X)
+        plan.vals[0].copy_(Xv)
+        plan.grads[plan.passes & 1].copy_(gY)
+        mark()
+        plan._gf.replay()
+        mark("fwd")
+        plan._gb.replay()
+        mark("bwd")
+    t = _timed(stream, K, W, body, ["fwd", "bwd"])
+    launches = len(plan.stages)
+    stages = [f"{kd}:{w}" for kd, w in plan.stages]
+    del plan
+    return {"workload": "sort_u64_f32", "elements": N, "stages": stages,
+            "fwd": _dir_row(N, t["fwd"], fwd_b, peak),
+            "bwd": _dir_row(N, t["bwd"], bwd_b, peak),
+            "note": "bytes summed over stages (keys + payloads in and out, plus the recorded "
+                    "flag bit or chunk permutation; backward gY in, gX out plus the record); "
+                    f"{launches} stages, each one or two kernel launches, in one graph per "
+                    "direction"}
+
+
+def run_rows(args, lib, dev, stream, peak):
+    """The task's other configurations, forward and backward, each on its
+    own inputs (created, timed and freed in turn), inside one clock-sampling
+    window."""
+    import torch
+    K, W = args.steps, max(3, args.warmup)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    rows = {}
+    for name, fn in (("single_i32_tag", lambda: row_single_tag(lib, dev, stream, K, W, peak,
+                                                                args.shift)),
+                     ("kv_u32_f32", lambda: row_kv(lib, dev, stream, K, W, peak, args.shift)),
+                     ("batched_i32_f32", lambda: row_batched(lib, dev, stream, K, W, peak,
+                                                             args.batched_pairs)),
+                     ("sort_u64_f32", lambda: row_sort(lib, dev, stream, K, W, peak,
+                                                       args.shift))):
+        rows[name] = fn()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    rows["clocks"] = clocks.stop()
+    rows["steps"], rows["warmup"] = K, W
+    return rows
 
 
 # ---------------------------------------------------------------------------
@@ -956,9 +1207,11 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
-    # Each reference step merges the same three workloads cut to 1/8 of their
-    # sizes (a bounded sample), so K + W steps finish in minutes.
-    merges = make_inputs(dev, args.shift + 3)
+    # Each reference step merges the same three full-size workloads (the
+    # oracle's Algorithm 2 takes about 0.2 s per step on 16 cores, so K + W
+    # steps finish well within minutes).
+    merges = make_inputs(dev, args.shift)
+    elems = sum(mg["m"] + mg["n"] for mg in merges)
     hi = _host_inputs(merges)
     del merges
     cores = os.cpu_count() or 1
@@ -976,10 +1229,13 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32+uint64 keys",
             "data": "synthetic (seeded, sorted; device-generated)", "impl": "reference",
             "config": {"workload": WORKLOAD, "merges": [m[0] for m in MERGES],
-                       "size_shift": args.shift + 3},
+                       "elements_per_step": elems, "l2": "inputs larger than L2 (no flush)",
+                       "size_shift": args.shift, "parallelism": f"replicas x{world}"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "the three merges at 1/8 size per step, CPU oracle "
-                                       f"Algorithm 2 on {cores} POSIX threads"},
+                             "sample": f"{args.steps} full steps (the three merges, {elems} "
+                                       "elements each step) of the CPU oracle's Algorithm 2 "
+                                       f"on {cores} POSIX threads after {args.warmup} "
+                                       "warm-up steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

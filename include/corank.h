@@ -32,10 +32,13 @@
  * unspecified result but never an out-of-bounds access or a hang.
  *
  * MEMORY.  Every pointer argument marked "device" is a device pointer owned by
- * the caller; the library allocates nothing.  Base pointers of key, payload,
- * tag and workspace arrays must be 16-byte aligned (CR_EALIGN otherwise);
- * element offsets inside them are arbitrary.  Outputs must not overlap inputs
- * (CR_EALIAS).  Sizes are element counts (int64).
+ * the caller; the library allocates nothing.  Key, payload, tag, gradient and
+ * permutation arrays may start at any address aligned to their element size
+ * (so a window A + i0 of a larger array is passed as it is; CR_EALIGN for a
+ * pointer that is not).  Library-format buffers -- workspaces and the source
+ * flags of recorded merge passes -- must be 16-byte aligned.  Outputs must
+ * not overlap inputs (CR_EALIAS).  Sizes are element counts (int64), at most
+ * 2^59 per array (CR_EINVAL beyond).
  *
  * STREAMS AND ERRORS.  Every call is asynchronous and stream-ordered on
  * `stream` (a cudaStream_t; NULL = the legacy default stream).  Argument
@@ -62,7 +65,7 @@ typedef enum {
     CR_OK = 0,
     CR_EINVAL = 1,        /* bad size, rank, type, null pointer with nonzero size */
     CR_EALIAS = 2,        /* an output range overlaps an input range */
-    CR_EALIGN = 3,        /* a base pointer is not 16-byte aligned */
+    CR_EALIGN = 3,        /* a pointer is not aligned as its argument requires */
     CR_ENOSPACE = 4,      /* workspace smaller than the *_workspace_size answer */
     CR_ECUDA = 5,         /* a CUDA runtime call failed; see cr_last_error() */
     CR_ETIMEOUT = 6,      /* (device) a bounded wait inside a kernel gave up */
@@ -124,16 +127,23 @@ cr_status cr_set_tile_shape(int key_type, int val_bytes, int shape);
 /* Current shape for this key type and payload width (-1 if invalid). */
 int cr_get_tile_shape(int key_type, int val_bytes);
 
-/* Single merges choose among three shapes per key type and payload width by
- * geometry class: 2 "small" when m + n <= 2^23 (few tiles per CTA slot),
- * else 1 "skewed" when one input is more than 16 times longer than the other
- * (16 * min(m, n) < max(m, n)), else 0 "balanced".  Batched and merge-pass
- * calls use the balanced shape.  cr_set_tile_shape sets every class; these
- * set and read one (cls = 0, 1 or 2; CR_EINVAL / -1 for another value). */
+/* Shapes are chosen per key type, payload width and class.  Single merges
+ * take one of three geometry classes: 2 "small" when m + n <= 2^23 (few
+ * tiles per CTA slot), else 1 "skewed" when one input is more than 16 times
+ * longer than the other (16 * min(m, n) < max(m, n)), else 0 "balanced".
+ * Batched calls take class 3 "batched" and merge passes (plain and recorded)
+ * class 4 "pass".  cr_set_tile_shape sets every class (except, for payload
+ * widths 4 and 8, the pass class when the shape's TILE exceeds 4096: a
+ * recorded pass keeps a tile's flags in one CTA of its backward); these set
+ * and read one (cls = 0 .. 4; CR_EINVAL / -1 for another value;
+ * CR_EUNSUPPORTED for a pass-class shape over 4096 elements with payloads). */
 cr_status cr_set_tile_shape_for(int key_type, int val_bytes, int cls, int shape);
 int cr_get_tile_shape_for(int key_type, int val_bytes, int cls);
 /* TILE a single merge of m and n elements uses (0 for invalid arguments). */
 int64_t cr_tile_size_for(int key_type, int val_bytes, int64_t m, int64_t n);
+/* TILE of class cls (0 .. 4, as above; 0 for invalid arguments).  Batched
+ * calls use cls 3, merge passes cls 4. */
+int64_t cr_tile_size_class(int key_type, int val_bytes, int cls);
 
 /* ------------------------------------------------------------------------
  * co_rank -- Algorithm 1 (Section 2), Lemma 1.
@@ -144,10 +154,21 @@ int64_t cr_tile_size_for(int key_type, int val_bytes, int64_t m, int64_t n);
  * k == m + n (used by Algorithm 2 for the last block end) gives (m, n).
  * ------------------------------------------------------------------------ */
 
-/* One rank; result written to device memory: d_ij[0] = i, d_ij[1] = j.
- * A, B: device, m and n keys.  k outside [0, m+n] -> CR_EINVAL. */
+/* One rank, result on the host: *i_out = i, *j_out = j.  A, B: device, m and
+ * n keys.  k outside [0, m+n] -> CR_EINVAL.  Synchronous: the search runs as
+ * one kernel on `stream`, the two results are copied back and `stream` is
+ * synchronised before the call returns (so it cannot be captured into a CUDA
+ * graph; use cr_co_rank_async there).  The kernel writes into a two-word
+ * result slot in the library's device image (nothing is allocated); calls
+ * on one device take turns on it. */
 cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int64_t n,
-                     int64_t k, int64_t* d_ij, cr_stream stream);
+                     int64_t k, int64_t* i_out, int64_t* j_out, cr_stream stream);
+
+/* One rank, result written to device memory on `stream` without waiting:
+ * d_ij[0] = i, d_ij[1] = j (d_ij: device, 8-byte aligned).  Same arguments
+ * and errors as cr_co_rank otherwise. */
+cr_status cr_co_rank_async(int key_type, const void* A, int64_t m, const void* B, int64_t n,
+                           int64_t k, int64_t* d_ij, cr_stream stream);
 
 /* cnt ranks d_k[0..cnt) (device) -> d_i, d_j (device, cnt each).  A rank
  * outside [0, m+n] gives i = j = -1 for that entry. */
@@ -281,8 +302,8 @@ cr_status cr_merge_pass_backward(int key_type, int val_bytes, const void* X, int
  * Layout of `flags` (uint32 words, 16-byte aligned, flag_words words): tile
  * t of the pass owns words [t*TILE/32, (t+1)*TILE/32); bit x % 32 of word
  * t*TILE/32 + x/32 is set when the tile's output x came from the pair's
- * second run (TILE = cr_tile_size(key_type, val_bytes): merge passes use the
- * balanced-class shape).
+ * second run (TILE = cr_tile_size_class(key_type, val_bytes, 4): merge
+ * passes use the pass-class shape, at most 4096 elements).
  * Sizes: cr_merge_pass_record_size gives the workspace bytes and flag words
  * for (key_type, val_bytes, N, width) under the current tile shape.
  *
@@ -326,7 +347,7 @@ cr_status cr_sort_runs_backward(int key_type, int val_bytes, const void* X, int6
 /* Recorded run formation: the same forward as cr_sort_runs (val_bytes 4 or
  * 8) that also writes each run's permutation, perm[base + x] = index inside
  * the run of the input element that became output x (uint16, N entries,
- * 16-byte aligned, must not overlap the other arrays).  Its backward
+ * 2-byte aligned, must not overlap the other arrays).  Its backward
  * cr_sort_runs_backward_recorded reads no keys: gX[base + perm[base + x]] =
  * gY[base + x] within every run.  It must get the perm written by the
  * forward for the same N (entries pointing outside their run are skipped). */
@@ -348,12 +369,16 @@ cr_status cr_sort_runs_backward_recorded(int val_bytes, int64_t N, const uint16_
  * input and output buffers.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture begins.
+ *     before any stream capture begins.  Only a successful lookup is kept
+ *     (a failed one is retried by the next call).  The address belongs to
+ *     the device context it was found in: do not call this entry point
+ *     again after cudaDeviceReset in the same process.
  *   - Size limit: m + n at most 131064 tiles of cr_tile_size_for(key_type,
  *     0, m, n) elements each (with the compiled-in shapes: 503,285,760
  *     elements for 4-byte keys, 234,866,688 for 8-byte keys; more with
- *     larger tiles selected).  Larger requests return CR_EINVAL and launch
- *     nothing.
+ *     larger tiles selected).  Larger requests (including sizes whose sum
+ *     would overflow) return CR_EINVAL and launch nothing.
+ *   - A, B, C and C_tag need only be aligned to their element size.
  *   - Every call shares the array; calls whose kernels overlap on the GPU
  *     (other streams, other host threads) race and may give wrong output, so
  *     serialise them on one stream.  Device-side status is not reported for
@@ -385,8 +410,9 @@ cr_status cr_workspace_status(const void* ws, cr_stream stream);
  * only) the chunk permutation is written: perm[base + x] = index inside the
  * chunk of the input element that became output x; its backward
  * cr_merge_runs_block_backward_recorded routes gY to gX through it without
- * keys.  Arrays 16-byte aligned (CR_EALIGN); outputs must not overlap
- * inputs (CR_EALIAS); CR_EINVAL for a bad width, key type or payload width.
+ * keys.  Arrays aligned to their element size (CR_EALIGN); outputs must not
+ * overlap inputs (CR_EALIAS); CR_EINVAL for a bad width, key type or payload
+ * width.
  * ------------------------------------------------------------------------ */
 int64_t cr_merge_runs_block_length(void);
 
@@ -402,7 +428,8 @@ cr_status cr_merge_runs_block_backward_recorded(int val_bytes, int64_t N, const 
  * A[0, m) sorted in key_type's order (including float and descending orders)?
  * d_first (device, one int64) receives -1 when it is, else the smallest p
  * with A[p] before A[p-1] in that order.  ws: device scratch of at least 16
- * bytes (16-byte aligned); A 16-byte aligned.  Asynchronous on `stream`.
+ * bytes (16-byte aligned); A aligned to its key size.  Asynchronous on
+ * `stream`.
  * CR_EINVAL / CR_EALIGN for bad arguments.
  * ------------------------------------------------------------------------ */
 cr_status cr_check_sorted(int key_type, const void* A, int64_t m, int64_t* d_first, void* ws,

@@ -35,7 +35,9 @@ SIGNATURES = {
     "cr_set_tile_shape_for": ([INT, INT, INT, INT], INT),
     "cr_get_tile_shape_for": ([INT, INT, INT], INT),
     "cr_tile_size_for": ([INT, INT, I64, I64], I64),
-    "cr_co_rank": ([INT, P, I64, P, I64, I64, P, P], INT),
+    "cr_tile_size_class": ([INT, INT, INT], I64),
+    "cr_co_rank": ([INT, P, I64, P, I64, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), P], INT),
+    "cr_co_rank_async": ([INT, P, I64, P, I64, I64, P, P], INT),
     "cr_co_rank_many": ([INT, P, I64, P, I64, P, I64, P, P, P], INT),
     "cr_merge_workspace_size": ([INT, INT, I64, I64, ctypes.POINTER(SZ)], INT),
     "cr_stable_merge": ([INT, P, I64, P, I64, P, P, P, SZ, P], INT),

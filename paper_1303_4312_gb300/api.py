@@ -2,8 +2,8 @@
 
 PyTorch supplies device memory, the current stream and autograd; every
 co-rank and merge step runs in the library's CUDA kernels.  Tensors must be
-contiguous CUDA tensors; base pointers must be 16-byte aligned (fresh
-allocations are; offset views may not be).
+contiguous CUDA tensors; offset views (``A[i0:i1]``) are accepted as they
+are (arrays need only be aligned to their element size).
 
 Key types: int32 -> "i32", int64 -> "i64", uint32 -> "u32", uint64 -> "u64".
 Unsigned keys can also travel in signed containers of the same width when
@@ -101,11 +101,29 @@ def co_rank(A: torch.Tensor, B: torch.Tensor, k: int, key_type: str | None = Non
     kt = _key_code(A, key_type)
     if B.dtype != A.dtype:
         raise TypeError("A and B dtypes differ")
-    out = torch.empty(2, dtype=torch.int64, device=dev)
-    _lib.check(lib.cr_co_rank(kt, _ptr(A), A.numel(), _ptr(B), B.numel(), int(k), _ptr(out),
-                              _stream(dev)))
-    i, j = out.tolist()
-    return i, j
+    i, j = ctypes.c_int64(), ctypes.c_int64()
+    with torch.cuda.device(dev):
+        _lib.check(lib.cr_co_rank(kt, _ptr(A), A.numel(), _ptr(B), B.numel(), int(k),
+                                  ctypes.byref(i), ctypes.byref(j), _stream(dev)))
+    return i.value, j.value
+
+
+def co_rank_async(A: torch.Tensor, B: torch.Tensor, k: int, out: torch.Tensor | None = None,
+                  key_type: str | None = None) -> torch.Tensor:
+    """(i, j) of rank k written to a 2-element int64 device tensor on the
+    current stream, without waiting (usable inside CUDA-graph capture)."""
+    lib = _lib.load()
+    dev = _dev(A, B, out)
+    kt = _key_code(A, key_type)
+    if B.dtype != A.dtype:
+        raise TypeError("A and B dtypes differ")
+    if out is None:
+        out = torch.empty(2, dtype=torch.int64, device=dev)
+    elif out.dtype != torch.int64 or out.numel() < 2:
+        raise ValueError("out must hold two int64 values")
+    _lib.check(lib.cr_co_rank_async(kt, _ptr(A), A.numel(), _ptr(B), B.numel(), int(k),
+                                    _ptr(out), _stream(dev)))
+    return out
 
 
 def co_rank_many(A: torch.Tensor, B: torch.Tensor, ks: torch.Tensor, key_type: str | None = None):

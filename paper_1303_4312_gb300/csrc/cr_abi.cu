@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <atomic>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -42,21 +43,37 @@ int key_order(int key_type) { return cr::key_type_order(key_type); }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// A device array argument: `count` elements of `elem` bytes.
+// A device array argument: `count` elements of `elem` bytes.  Data arrays
+// (keys, payloads, tags, gradients) may start at any multiple of their
+// element size, so that a window of a larger array can be passed as it is;
+// library-format buffers (source flags) set `align` to 16.
 struct Arr {
     const void* p;
     int64_t count;
     int64_t elem;
     const char* name;
+    int64_t align = 0;   // 0: the element size
     int64_t bytes() const { return count * elem; }
 };
+
+// Largest element count accepted for one array: every sum of two counts and
+// every count times an element width (at most 8 bytes) stays inside int64.
+constexpr int64_t kMaxElems = int64_t(1) << 59;
+
+bool bad_size(int64_t x) { return x < 0 || x > kMaxElems; }
 
 cr_status check_arr(const Arr& a) {
     if (a.count < 0) return fail(CR_EINVAL, "%s: negative length", a.name);
     if (a.count == 0) return CR_OK;
     if (a.p == nullptr) return fail(CR_EINVAL, "%s is NULL with %lld elements", a.name,
                                     static_cast<long long>(a.count));
-    if (!aligned16(a.p)) return fail(CR_EALIGN, "%s is not 16-byte aligned", a.name);
+    const int64_t al = a.align > 0 ? a.align : a.elem;
+    if (a.count > INT64_MAX / a.elem)
+        return fail(CR_EINVAL, "%s: %lld elements of %lld bytes overflow the address space",
+                    a.name, static_cast<long long>(a.count), static_cast<long long>(a.elem));
+    if (reinterpret_cast<uintptr_t>(a.p) % uintptr_t(al) != 0)
+        return fail(CR_EALIGN, "%s is not aligned to %lld bytes", a.name,
+                    static_cast<long long>(al));
     return CR_OK;
 }
 
@@ -78,6 +95,14 @@ cr_status check_no_alias(const Arr* outs, int nout, const Arr* ins, int nin) {
     }
     return CR_OK;
 }
+
+// Result slot of the host-result cr_co_rank: one pair per device, in this
+// library's device image (the call allocates nothing).  Its device address is
+// looked up once per device; calls on one device take turns on it.
+constexpr int kMaxResultDevices = 64;
+__device__ int64_t g_co_rank_result[2];
+std::mutex g_result_mu[kMaxResultDevices];
+int64_t* g_result_ptr[kMaxResultDevices];
 
 constexpr size_t kRecBytes = sizeof(cr::TileRec);
 
@@ -130,7 +155,7 @@ cr_status check_forward(int key_type, int vb, const void* Ak, const void* Av, in
                         const void* Cv, const uint32_t* tag) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(vb, true));
-    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size (m=%lld, n=%lld)",
+    if (bad_size(m) || bad_size(n)) return fail(CR_EINVAL, "bad size (m=%lld, n=%lld)",
                                     static_cast<long long>(m), static_cast<long long>(n));
     const int ks = key_bytes(key_type);
     const int64_t mn = m + n;
@@ -152,7 +177,7 @@ cr_status check_backward(int key_type, int vb, const void* Ak, int64_t m, const 
                          int64_t n, const void* gC, const void* gA, const void* gB) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(vb, false));
-    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(m) || bad_size(n)) return fail(CR_EINVAL, "negative or too large size");
     const int ks = key_bytes(key_type);
     const Arr ins[3] = {{Ak, m, ks, "A"}, {Bk, n, ks, "B"}, {gC, m + n, vb, "gC"}};
     const Arr outs[2] = {{gA, m, vb, "gA"}, {gB, n, vb, "gB"}};
@@ -166,9 +191,14 @@ int shape_of(int key_type, int vb, int64_t m, int64_t n) {
     return cr::current_shape(key_bytes(key_type), vb, cr::geometry_class(m, n));
 }
 
-// Shape of batched and merge-pass calls: the balanced class (their segments
-// are not known on the host).
-int shape_of(int key_type, int vb) { return cr::current_shape(key_bytes(key_type), vb, 0); }
+// Shapes of batched and merge-pass calls: classes of their own (their
+// segments and runs are not known on the host).
+int shape_batched(int key_type, int vb) {
+    return cr::current_shape(key_bytes(key_type), vb, cr::kClassBatched);
+}
+int shape_pass(int key_type, int vb) {
+    return cr::current_shape(key_bytes(key_type), vb, cr::kClassPass);
+}
 
 int64_t single_tiles(int shape, int64_t m, int64_t n, int64_t* tile_out) {
     const int64_t tile = cr::tile_of_shape(shape);
@@ -243,12 +273,12 @@ cr_status launch_tiles_backward(int shape, int key_type, int vb, const void* Ak,
 namespace cr {
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
-// Selected tile shape per (key size 4|8, payload width 0|4|8, geometry
-// class balanced|skewed|small).  Defaults: 256 x 15 for keys without payload
+// Selected tile shape per (key size 4|8, payload width 0|4|8, class
+// balanced|skewed|small|batched|pass).  Defaults: 256 x 15 for keys without payload
 // (128 x 31 for skewed 8-byte merges), 256 x 7 otherwise.
 static std::atomic<int> g_shape[2][3][kNumClasses] = {
-    {{{0}, {0}, {0}}, {{2}, {2}, {2}}, {{2}, {2}, {2}}},
-    {{{0}, {1}, {0}}, {{2}, {2}, {2}}, {{2}, {2}, {2}}}};
+    {{{0}, {0}, {0}, {0}, {0}}, {{2}, {2}, {2}, {2}, {2}}, {{2}, {2}, {2}, {2}, {2}}},
+    {{{0}, {1}, {0}, {0}, {0}}, {{2}, {2}, {2}, {2}, {2}}, {{2}, {2}, {2}, {2}, {2}}}};
 
 int current_shape(int key_bytes, int vb, int cls) {
     return g_shape[key_bytes == 8 ? 1 : 0][vb / 4][cls].load(std::memory_order_relaxed);
@@ -275,7 +305,7 @@ const char* cr_status_string(int status) {
 
 const char* cr_last_error(void) { return g_last_error.c_str(); }
 
-int cr_abi_version(void) { return 101; }
+int cr_abi_version(void) { return 200; }
 
 int64_t cr_tile_size(int key_type, int val_bytes) {
     const int ks = key_bytes(key_type);
@@ -301,8 +331,10 @@ cr_status cr_set_tile_shape(int key_type, int val_bytes, int shape) {
     if (!cr::shape_available(ks, val_bytes, shape))
         return fail(CR_EUNSUPPORTED, "tile shape %d does not fit %d-byte keys with %d-byte payloads",
                     shape, ks, val_bytes);
+    const bool pass_ok = val_bytes == 0 || cr::tile_of_shape(shape) <= cr::kMaxRecordTile;
     for (int cls = 0; cls < cr::kNumClasses; ++cls)
-        cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4][cls].store(shape, std::memory_order_relaxed);
+        if (cls != cr::kClassPass || pass_ok)
+            cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4][cls].store(shape, std::memory_order_relaxed);
     return ok();
 }
 
@@ -318,6 +350,10 @@ cr_status cr_set_tile_shape_for(int key_type, int val_bytes, int cls, int shape)
     if (!cr::shape_available(ks, val_bytes, shape))
         return fail(CR_EUNSUPPORTED, "tile shape %d does not fit %d-byte keys with %d-byte payloads",
                     shape, ks, val_bytes);
+    if (cls == cr::kClassPass && val_bytes != 0 && cr::tile_of_shape(shape) > cr::kMaxRecordTile)
+        return fail(CR_EUNSUPPORTED,
+                    "tile shape %d: merge passes with payloads are recorded in tiles of at most "
+                    "%lld elements", shape, static_cast<long long>(cr::kMaxRecordTile));
     cr::g_shape[ks == 8 ? 1 : 0][val_bytes / 4][cls].store(shape, std::memory_order_relaxed);
     return ok();
 }
@@ -329,18 +365,25 @@ int cr_get_tile_shape_for(int key_type, int val_bytes, int cls) {
     return cr::current_shape(ks, val_bytes, cls);
 }
 
+int64_t cr_tile_size_class(int key_type, int val_bytes, int cls) {
+    const int ks = key_bytes(key_type);
+    if (ks == 0 || (val_bytes != 0 && val_bytes != 4 && val_bytes != 8)) return 0;
+    if (cls < 0 || cls >= cr::kNumClasses) return 0;
+    return cr::tile_of_shape(cr::current_shape(ks, val_bytes, cls));
+}
+
 int64_t cr_tile_size_for(int key_type, int val_bytes, int64_t m, int64_t n) {
     const int ks = key_bytes(key_type);
-    if (ks == 0 || (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) || m < 0 || n < 0)
+    if (ks == 0 || (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) || bad_size(m) || bad_size(n))
         return 0;
     return cr::tile_of_shape(cr::current_shape(ks, val_bytes, cr::geometry_class(m, n)));
 }
 
-cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int64_t n, int64_t k,
-                     int64_t* d_ij, cr_stream stream) {
+cr_status cr_co_rank_async(int key_type, const void* A, int64_t m, const void* B, int64_t n,
+                           int64_t k, int64_t* d_ij, cr_stream stream) {
     CR_TRY(check_key_type(key_type));
     const int ks = key_bytes(key_type);
-    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(m) || bad_size(n)) return fail(CR_EINVAL, "negative or too large size");
     if (k < 0 || k > m + n)
         return fail(CR_EINVAL, "rank %lld outside [0, %lld]", static_cast<long long>(k),
                     static_cast<long long>(m + n));
@@ -356,12 +399,61 @@ cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int6
     return ok();
 }
 
+cr_status cr_co_rank(int key_type, const void* A, int64_t m, const void* B, int64_t n, int64_t k,
+                     int64_t* i_out, int64_t* j_out, cr_stream stream) {
+    if (i_out == nullptr || j_out == nullptr) return fail(CR_EINVAL, "result pointer is NULL");
+    CR_TRY(check_key_type(key_type));
+    if (bad_size(m) || bad_size(n)) return fail(CR_EINVAL, "negative or too large size");
+    if (k < 0 || k > m + n)
+        return fail(CR_EINVAL, "rank %lld outside [0, %lld]", static_cast<long long>(k),
+                    static_cast<long long>(m + n));
+    // trivial ranks need no search
+    if (k == 0 || k == m + n || m == 0 || n == 0) {
+        CR_TRY(check_arr({A, m, key_bytes(key_type), "A"}));
+        CR_TRY(check_arr({B, n, key_bytes(key_type), "B"}));
+        *i_out = k == 0 ? 0 : (k == m + n ? m : (m == 0 ? 0 : k));
+        *j_out = k - *i_out;
+        return ok();
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxResultDevices)
+        return fail(CR_EUNSUPPORTED, "device %d out of range", dev);
+    // The kernel writes into this library's one result slot of the device;
+    // the lock keeps it to one call at a time from launch to read-back.
+    std::lock_guard<std::mutex> lock(g_result_mu[dev]);
+    if (g_result_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_co_rank_result);
+        if (e != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            return cuda_fail(e, "result slot lookup");
+        }
+        g_result_ptr[dev] = static_cast<int64_t*>(p);
+    }
+    CR_TRY(cr_co_rank_async(key_type, A, m, B, n, k, g_result_ptr[dev], stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t ij[2] = {-1, -1};
+    e = cudaMemcpyAsync(ij, g_result_ptr[dev], sizeof(ij), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "co_rank result read");
+    if (ij[0] < 0 || ij[1] < 0 || ij[0] + ij[1] != k)
+        return fail(CR_EINTERNAL, "co_rank result (%lld, %lld) is not a split of rank %lld",
+                    static_cast<long long>(ij[0]), static_cast<long long>(ij[1]),
+                    static_cast<long long>(k));
+    *i_out = ij[0];
+    *j_out = ij[1];
+    return ok();
+}
+
 cr_status cr_co_rank_many(int key_type, const void* A, int64_t m, const void* B, int64_t n,
                           const int64_t* d_k, int64_t cnt, int64_t* d_i, int64_t* d_j,
                           cr_stream stream) {
     CR_TRY(check_key_type(key_type));
     const int ks = key_bytes(key_type);
-    if (m < 0 || n < 0 || cnt < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(m) || bad_size(n) || bad_size(cnt))
+        return fail(CR_EINVAL, "negative or too large size");
     CR_TRY(check_arr({A, m, ks, "A"}));
     CR_TRY(check_arr({B, n, ks, "B"}));
     if (cnt == 0) return ok();
@@ -381,7 +473,7 @@ cr_status cr_merge_workspace_size(int key_type, int val_bytes, int64_t m, int64_
                                   size_t* bytes) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, true));
-    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(m) || bad_size(n)) return fail(CR_EINVAL, "negative or too large size");
     if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
     *bytes = single_ws_bytes(single_tiles(shape_of(key_type, val_bytes, m, n), m, n, nullptr));
     return ok();
@@ -424,7 +516,7 @@ cr_status cr_merge_partition(int key_type, int val_bytes, const void* A, int64_t
                              int64_t n, void* ws, size_t ws_bytes, cr_stream stream) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, true));
-    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(m) || bad_size(n)) return fail(CR_EINVAL, "negative or too large size");
     const int ks = key_bytes(key_type);
     CR_TRY(check_arr({A, m, ks, "A"}));
     CR_TRY(check_arr({B, n, ks, "B"}));
@@ -439,7 +531,7 @@ cr_status cr_merge_partition_alg2(int key_type, int val_bytes, const void* A, in
                                   cr_stream stream) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, true));
-    if (m < 0 || n < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(m) || bad_size(n)) return fail(CR_EINVAL, "negative or too large size");
     const int ks = key_bytes(key_type);
     CR_TRY(check_arr({A, m, ks, "A"}));
     CR_TRY(check_arr({B, n, ks, "B"}));
@@ -479,9 +571,10 @@ cr_status cr_batched_workspace_size(int key_type, int val_bytes, int64_t nseg, i
                                     int64_t b_total, size_t* bytes) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, true));
-    if (nseg < 0 || a_total < 0 || b_total < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(nseg) || bad_size(a_total) || bad_size(b_total))
+        return fail(CR_EINVAL, "negative or too large size");
     if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
-    const int64_t tile = cr::tile_of_shape(shape_of(key_type, val_bytes));
+    const int64_t tile = cr::tile_of_shape(shape_batched(key_type, val_bytes));
     *bytes = batched_ws_bytes(batched_max_tiles(tile, nseg, a_total, b_total), nseg);
     return ok();
 }
@@ -495,7 +588,8 @@ cr_status batched_common(bool backward, int key_type, int val_bytes, int64_t nse
                          void* ws, size_t ws_bytes, cr_stream stream) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, !backward));
-    if (nseg < 0 || a_total < 0 || b_total < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(nseg) || bad_size(a_total) || bad_size(b_total))
+        return fail(CR_EINVAL, "negative or too large size");
     const int ks = key_bytes(key_type);
     const int vb = val_bytes;
     const int64_t ct = a_total + b_total;
@@ -518,7 +612,7 @@ cr_status batched_common(bool backward, int key_type, int val_bytes, int64_t nse
         for (const Arr& a : outs) CR_TRY(check_arr(a));
         CR_TRY(check_no_alias(outs, 2, ins, 3));
     }
-    const int shape = shape_of(key_type, vb);
+    const int shape = shape_batched(key_type, vb);
     const int64_t tile = cr::tile_of_shape(shape);
     const int64_t max_tiles = batched_max_tiles(tile, nseg, a_total, b_total);
     CR_TRY(check_ws(ws, ws_bytes, batched_ws_bytes(max_tiles, nseg)));
@@ -560,13 +654,13 @@ cr_status pass_common(Pass mode, int key_type, int val_bytes, const void* X, con
                       cr_stream stream) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, mode == Pass::kForward));
-    if (N < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(N)) return fail(CR_EINVAL, "negative or too large size");
     if (width < 1) return fail(CR_EINVAL, "run width must be >= 1");
     if (flag_words > size_t(INT64_MAX / 4)) return fail(CR_EINVAL, "flag_words too large");
     const int ks = key_bytes(key_type);
     const int vb = val_bytes;
     const bool rec = mode == Pass::kRecord || mode == Pass::kReplay;
-    const Arr fl = {rec ? flags : nullptr, rec ? int64_t(flag_words) : 0, 4, "flags"};
+    const Arr fl = {rec ? flags : nullptr, rec ? int64_t(flag_words) : 0, 4, "flags", 16};
     if (mode == Pass::kForward || mode == Pass::kRecord) {
         const Arr ins[2] = {{X, N, ks, "X"}, {vb ? Xv : nullptr, vb ? N : 0, vb, "X payload"}};
         const Arr outs[3] = {{Y, N, ks, "Y"}, {vb ? Yv : nullptr, vb ? N : 0, vb, "Y payload"},
@@ -589,8 +683,11 @@ cr_status pass_common(Pass mode, int key_type, int val_bytes, const void* X, con
     }
     if (N == 0) return ok();
     if (width > N) width = N;   // one pair with an empty second run: the same result
-    const int shape = shape_of(key_type, vb);
+    const int shape = shape_pass(key_type, vb);
     const int64_t tile = cr::tile_of_shape(shape);
+    if (rec && tile > cr::kMaxRecordTile)
+        return fail(CR_EUNSUPPORTED, "recorded passes need tiles of at most %lld elements",
+                    static_cast<long long>(cr::kMaxRecordTile));
     const int64_t ntiles = cr::pass_tiles(N, width, tile, nullptr, nullptr);
     CR_TRY(check_ws(ws, ws_bytes, single_ws_bytes(ntiles)));
     if (rec) {
@@ -659,9 +756,9 @@ cr_status cr_merge_pass_workspace_size(int key_type, int val_bytes, int64_t N, i
                                        size_t* bytes) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, true));
-    if (N < 0 || width < 1) return fail(CR_EINVAL, "bad size or width");
+    if (bad_size(N) || width < 1) return fail(CR_EINVAL, "bad size or width");
     if (!bytes) return fail(CR_EINVAL, "bytes is NULL");
-    const int64_t tile = cr::tile_of_shape(shape_of(key_type, val_bytes));
+    const int64_t tile = cr::tile_of_shape(shape_pass(key_type, val_bytes));
     if (width > N) width = N > 0 ? N : 1;
     *bytes = single_ws_bytes(cr::pass_tiles(N, width, tile, nullptr, nullptr));
     return ok();
@@ -685,9 +782,9 @@ cr_status cr_merge_pass_record_size(int key_type, int val_bytes, int64_t N, int6
                                     size_t* ws_bytes, size_t* flag_words) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, false));
-    if (N < 0 || width < 1) return fail(CR_EINVAL, "bad size or width");
+    if (bad_size(N) || width < 1) return fail(CR_EINVAL, "bad size or width");
     if (!ws_bytes || !flag_words) return fail(CR_EINVAL, "output pointer is NULL");
-    const int64_t tile = cr::tile_of_shape(shape_of(key_type, val_bytes));
+    const int64_t tile = cr::tile_of_shape(shape_pass(key_type, val_bytes));
     if (width > N) width = N > 0 ? N : 1;
     const int64_t nt = cr::pass_tiles(N, width, tile, nullptr, nullptr);
     *ws_bytes = single_ws_bytes(nt);
@@ -719,7 +816,7 @@ cr_status sort_runs_common(int key_type, int val_bytes, const void* X, const voi
                            void* Y, void* Yv, uint16_t* perm, cr_stream stream) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, perm == nullptr));
-    if (N < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(N)) return fail(CR_EINVAL, "negative or too large size");
     const int ks = key_bytes(key_type);
     const int vb = val_bytes;
     const Arr ins[2] = {{X, N, ks, "X"}, {vb ? Xv : nullptr, vb ? N : 0, vb, "X payload"}};
@@ -752,7 +849,7 @@ cr_status cr_sort_runs_record(int key_type, int val_bytes, const void* X, const 
 cr_status cr_sort_runs_backward_recorded(int val_bytes, int64_t N, const uint16_t* perm,
                                          const void* gY, void* gX, cr_stream stream) {
     CR_TRY(check_vb(val_bytes, false));
-    if (N < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(N)) return fail(CR_EINVAL, "negative or too large size");
     const Arr ins[2] = {{perm, N, 2, "perm"}, {gY, N, val_bytes, "gY"}};
     const Arr outs[1] = {{gX, N, val_bytes, "gX"}};
     for (const Arr& a : ins) CR_TRY(check_arr(a));
@@ -769,7 +866,7 @@ cr_status cr_sort_runs_backward(int key_type, int val_bytes, const void* X, int6
                                 const void* gY, void* gX, cr_stream stream) {
     CR_TRY(check_key_type(key_type));
     CR_TRY(check_vb(val_bytes, false));
-    if (N < 0) return fail(CR_EINVAL, "negative size");
+    if (bad_size(N)) return fail(CR_EINVAL, "negative or too large size");
     const int ks = key_bytes(key_type);
     const Arr ins[2] = {{X, N, ks, "X"}, {gY, N, val_bytes, "gY"}};
     const Arr outs[1] = {{gX, N, val_bytes, "gX"}};

@@ -329,7 +329,8 @@ extern "C" cr_status cr_merge_runs_block(int key_type, int val_bytes, const void
                                          void* Yv, uint16_t* perm, cr_stream stream) {
     const int ks = cr::key_type_bytes(key_type);
     if (ks == 0) return cr::block_fail(CR_EINVAL, "unknown key type");
-    if (N < 0) return cr::block_fail(CR_EINVAL, "negative size");
+    if (N < 0 || N > (int64_t(1) << 59))
+        return cr::block_fail(CR_EINVAL, "negative or too large size");
     if (!(val_bytes == 0 || val_bytes == 4 || val_bytes == 8))
         return cr::block_fail(CR_EINVAL, "payload width must be 0, 4 or 8");
     if (perm != nullptr && val_bytes == 0)
@@ -339,11 +340,13 @@ extern "C" cr_status cr_merge_runs_block(int key_type, int val_bytes, const void
     if (N == 0) return cr::block_fail(CR_OK, "");
     const void* arrs[5] = {X, Y, val_bytes ? Xv : nullptr, val_bytes ? Yv : nullptr, perm};
     const bool need[5] = {true, true, val_bytes != 0, val_bytes != 0, perm != nullptr};
+    const uintptr_t elem[5] = {uintptr_t(ks), uintptr_t(ks), uintptr_t(val_bytes),
+                               uintptr_t(val_bytes), 2};
     for (int i = 0; i < 5; ++i) {
         if (!need[i]) continue;
         if (arrs[i] == nullptr) return cr::block_fail(CR_EINVAL, "NULL array");
-        if (reinterpret_cast<uintptr_t>(arrs[i]) & 15u)
-            return cr::block_fail(CR_EALIGN, "array not 16-byte aligned");
+        if (reinterpret_cast<uintptr_t>(arrs[i]) % elem[i])
+            return cr::block_fail(CR_EALIGN, "array not aligned to its element size");
     }
     const int64_t kb = N * ks, vbb = N * val_bytes, pb = perm ? N * 2 : 0;
     if (cr::overlaps(Y, kb, X, kb) || (val_bytes && cr::overlaps(Y, kb, Xv, vbb)) ||
@@ -368,12 +371,14 @@ extern "C" cr_status cr_merge_runs_block_backward_recorded(int val_bytes, int64_
                                                            void* gX, cr_stream stream) {
     if (!(val_bytes == 4 || val_bytes == 8))
         return cr::block_fail(CR_EINVAL, "payload width must be 4 or 8");
-    if (N < 0) return cr::block_fail(CR_EINVAL, "negative size");
+    if (N < 0 || N > (int64_t(1) << 59))
+        return cr::block_fail(CR_EINVAL, "negative or too large size");
     if (N == 0) return cr::block_fail(CR_OK, "");
     if (!perm || !gY || !gX) return cr::block_fail(CR_EINVAL, "NULL array");
-    if ((reinterpret_cast<uintptr_t>(perm) | reinterpret_cast<uintptr_t>(gY) |
-         reinterpret_cast<uintptr_t>(gX)) & 15u)
-        return cr::block_fail(CR_EALIGN, "array not 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(perm) & 1u) ||
+        ((reinterpret_cast<uintptr_t>(gY) | reinterpret_cast<uintptr_t>(gX)) %
+         uintptr_t(val_bytes)))
+        return cr::block_fail(CR_EALIGN, "array not aligned to its element size");
     const int64_t b = N * val_bytes;
     if (cr::overlaps(gX, b, gY, b) || cr::overlaps(gX, b, perm, N * 2))
         return cr::block_fail(CR_EALIAS, "gX overlaps another array");

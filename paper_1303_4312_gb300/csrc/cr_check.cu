@@ -65,9 +65,11 @@ extern "C" cr_status cr_check_sorted(int key_type, const void* A, int64_t m, int
     if ((m > 0 && A == nullptr) || d_first == nullptr || ws == nullptr)
         return check_fail(CR_EINVAL, "NULL array");
     if (ws_bytes < 16) return check_fail(CR_EINVAL, "scratch smaller than 16 bytes");
-    if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(ws) & 15u) ||
-        (reinterpret_cast<uintptr_t>(d_first) & 7u))
-        return check_fail(CR_EALIGN, "A or the scratch not 16-byte aligned, or d_first not 8");
+    if ((reinterpret_cast<uintptr_t>(A) % uintptr_t(cr::key_type_bytes(key_type))) ||
+        (reinterpret_cast<uintptr_t>(ws) & 15u) || (reinterpret_cast<uintptr_t>(d_first) & 7u))
+        return check_fail(CR_EALIGN,
+                          "A not aligned to its key size, the scratch not 16-byte aligned, or "
+                          "d_first not 8-byte aligned");
     const int order = cr::key_type_order(key_type);
     auto* scratch = static_cast<unsigned long long*>(ws);
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -56,6 +56,12 @@ struct MergeArgs {
     int64_t tag_b;       // tag of B[0]
     void* ws;            // workspace: header + tile records
     int32_t order;       // key order (order_key): 0 = the key type's own
+    // Array starts need only be aligned to their element size.  The pointers
+    // above are the 16-byte boundaries at or below each array's start (bulk
+    // copies address whole 16-byte chunks), and sh_* is the array's start
+    // measured from there in elements: element x of A is ak[x + sh_ak].
+    // flags and ws are library-format buffers and stay 16-byte aligned.
+    int32_t sh_ak, sh_bk, sh_av, sh_bv, sh_gc, sh_ck, sh_cv, sh_cv2, sh_tag;
 };
 
 // ---------------------------------------------------------------------------

@@ -66,7 +66,9 @@ cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream
         if (max_tiles <= 0) return cudaSuccess;
         int64_t grid = int64_t(sh.sms) * sh.blocks_per_sm;
         if (grid > max_tiles) grid = max_tiles;
-        kern<<<unsigned(grid), THREADS, L::TOTAL, st>>>(a);
+        MergeArgs aa = a;
+        align_merge_args(aa, KS, VB);
+        kern<<<unsigned(grid), THREADS, L::TOTAL, st>>>(aa);
         return cudaGetLastError();
     }
 }

@@ -71,7 +71,15 @@ inline bool shape_available(int key_bytes, int vb, int s) {
 // times longer than the other (nearly whole tiles come from one input);
 // else balanced (0).  Each class has its own tile shape.
 constexpr int64_t kSmallClassElems = int64_t(1) << 23;
-constexpr int kNumClasses = 3;
+// Batched calls (3) and merge passes (4) have classes of their own: their
+// segments or runs are not known on the host, and their best shapes differ
+// from a single merge's.
+constexpr int kClassBatched = 3;
+constexpr int kClassPass = 4;
+constexpr int kNumClasses = 5;
+// Recorded merge passes keep a tile's source flags in one CTA of the
+// routing backward: their tiles hold at most this many elements.
+constexpr int64_t kMaxRecordTile = 4096;
 inline int geometry_class(int64_t m, int64_t n) {
     if (m + n <= kSmallClassElems) return 2;
     const int64_t lo = m < n ? m : n, hi = m < n ? n : m;
@@ -89,6 +97,31 @@ constexpr int64_t kSmallMergeTiles = 4096;
 
 // Run formation: the chunk of the shared-memory merge stage (cr_block.cu).
 constexpr int64_t kSortRun = 4096;
+
+// Round an array pointer down to its 16-byte boundary; *sh receives the
+// array's start from there in elements of `elem` bytes (the pointer must be
+// aligned to `elem`).
+template <class P>
+inline P* align16_base(P* p, int elem, int32_t* sh) {
+    const uintptr_t u = reinterpret_cast<uintptr_t>(p);
+    *sh = elem > 0 ? int32_t((u & 15u) / uintptr_t(elem)) : 0;
+    return reinterpret_cast<P*>(u & ~uintptr_t(15));
+}
+
+// Apply align16_base to every data array of a tile-merge call (keys of ks
+// bytes; payloads and gradients of vb bytes; tags of 4).  flags and ws are
+// left as they are (they must be 16-byte aligned themselves).
+inline void align_merge_args(MergeArgs& a, int ks, int vb) {
+    a.ak = align16_base(a.ak, ks, &a.sh_ak);
+    a.bk = align16_base(a.bk, ks, &a.sh_bk);
+    a.av = align16_base(a.av, vb, &a.sh_av);
+    a.bv = align16_base(a.bv, vb, &a.sh_bv);
+    a.gc_in = align16_base(a.gc_in, vb, &a.sh_gc);
+    a.ck = align16_base(a.ck, ks, &a.sh_ck);
+    a.cv = align16_base(a.cv, vb, &a.sh_cv);
+    a.cv2 = align16_base(a.cv2, vb, &a.sh_cv2);
+    a.ctag = align16_base(a.ctag, 4, &a.sh_tag);
+}
 
 inline int64_t tile_of_shape(int s) {
     return int64_t(kShapes[s].nt) * kShapes[s].ipt * kShapes[s].ilp;

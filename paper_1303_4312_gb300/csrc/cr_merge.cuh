@@ -85,29 +85,50 @@ struct Layout {
     static_assert(TOTAL <= 232448, "exceeds 227 KB of shared memory per CTA");
 };
 
-// Plan for staging one window [g0, g0+len) of an array of `total` elements
-// with 16-byte chunks of E elements: the bulk copy covers
-// [s0, min(s1, floor_E(total))) and elements beyond the last full chunk of
-// the array are loaded one by one (only windows touching the array's end).
+// Plan for staging one window [g0, g0+len) of an array that occupies
+// [lo, total) (element indices from a 16-byte boundary at or below the
+// array's start, lo < E) with 16-byte chunks of E elements: the stage holds
+// the aligned superset [s0, s1) of the window; the bulk copy moves the whole
+// chunks of it that lie inside the array, [bb, bb + bulk), and the elements
+// of the window in the array's partial first or last chunk are loaded one by
+// one (only windows touching either end of the array have any).  Nothing
+// outside the array is read.
 struct WinPlan {
-    int64_t s0;        // first element copied (aligned down)
+    int64_t s0;        // first element of the superset (aligned down)
+    int64_t bb;        // first element moved by the bulk copy
     int64_t bulk;      // elements moved by the bulk copy
-    int64_t plain0;    // [plain0, plain1): elements loaded one by one
+    int64_t front0;    // [front0, front1): loaded one by one (array's first chunk)
+    int64_t front1;
+    int64_t plain0;    // [plain0, plain1): loaded one by one (array's last chunk)
     int64_t plain1;
     int32_t head;      // g0 - s0
     int32_t sup;       // aligned superset length (smem footprint)
 };
 
-__device__ __forceinline__ WinPlan plan_window(int64_t g0, int32_t len, int64_t total, int E) {
+__device__ __forceinline__ WinPlan plan_window(int64_t g0, int32_t len, int64_t lo,
+                                               int64_t total, int E) {
     WinPlan w;
     const int64_t mask = ~int64_t(E - 1);
     w.s0 = g0 & mask;
     const int64_t s1 = (g0 + len + E - 1) & mask;
-    const int64_t tot_al = total & mask;
-    const int64_t bulk_end = s1 < tot_al ? s1 : tot_al;
-    w.bulk = bulk_end > w.s0 ? bulk_end - w.s0 : 0;
-    const int64_t covered = w.s0 + w.bulk;
-    w.plain0 = covered > g0 ? covered : g0;
+    const int64_t lo_al = (lo + E - 1) & mask;   // first chunk wholly inside the array
+    const int64_t hi_al = total & mask;          // end of the last whole chunk
+    const int64_t bb = w.s0 > lo_al ? w.s0 : lo_al;
+    const int64_t be = s1 < hi_al ? s1 : hi_al;
+    if (be > bb) {
+        // bb <= g0 + len and be > g0: the copied chunks overlap the window
+        w.bb = bb;
+        w.bulk = be - bb;
+        w.front0 = g0;
+        w.front1 = bb > g0 ? bb : g0;
+        w.plain0 = be;
+    } else {
+        w.bb = w.s0;
+        w.bulk = 0;
+        w.front0 = g0;
+        w.front1 = g0;
+        w.plain0 = g0;
+    }
     w.plain1 = g0 + len;
     w.head = int32_t(g0 - w.s0);
     w.sup = int32_t(s1 - w.s0);
@@ -116,13 +137,15 @@ __device__ __forceinline__ WinPlan plan_window(int64_t g0, int32_t len, int64_t 
 
 template <class T>
 __device__ __forceinline__ void window_plain(T* region, const T* gbase, const WinPlan& w) {
+    for (int64_t g = w.front0; g < w.front1; ++g) region[g - w.s0] = gbase[g];
     for (int64_t g = w.plain0; g < w.plain1; ++g) region[g - w.s0] = gbase[g];
 }
 
 template <class T>
 __device__ __forceinline__ void window_bulk(T* region, const T* gbase, const WinPlan& w,
                                             uint64_t* bar) {
-    if (w.bulk > 0) bulk_g2s(region, gbase + w.s0, uint32_t(w.bulk * sizeof(T)), bar);
+    if (w.bulk > 0)
+        bulk_g2s(region + (w.bb - w.s0), gbase + w.bb, uint32_t(w.bulk * sizeof(T)), bar);
 }
 
 // Store the staged output window buf[ph + x] (x < len) to gbase[g0 + x],
@@ -287,32 +310,34 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             if constexpr (!BWD) {
                 K* C = static_cast<K*>(p.ck);
                 if (lane == 0) {
-                    store_bulk(C, stage_k(s), in.gc, len, EK);
+                    store_bulk(C, stage_k(s), in.gc + p.sh_ck, len, EK);
                     if constexpr (VB != 0)
-                        store_bulk(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV);
-                    if constexpr (TAG) store_bulk(p.ctag, stage_t(s), in.gc, len, 4);
+                        store_bulk(static_cast<V*>(p.cv), stage_v(s), in.gc + p.sh_cv, len, EV);
+                    if constexpr (TAG) store_bulk(p.ctag, stage_t(s), in.gc + p.sh_tag, len, 4);
                     if constexpr (REC) bulk_s2g(p.flags + t * L::WPT, stage_f(s), L::WPT * 4);
                     bulk_commit();
                 } else if (lane <= 2 * EK) {
-                    store_edges(C, stage_k(s), in.gc, len, EK, lane - 1);
+                    store_edges(C, stage_k(s), in.gc + p.sh_ck, len, EK, lane - 1);
                 } else if (VB != 0 && lane >= 9 && lane < 9 + 2 * EV) {
-                    store_edges(static_cast<V*>(p.cv), stage_v(s), in.gc, len, EV, lane - 9);
+                    store_edges(static_cast<V*>(p.cv), stage_v(s), in.gc + p.sh_cv, len, EV,
+                                lane - 9);
                 } else if (TAG && lane >= 17 && lane < 17 + 8) {
-                    store_edges(p.ctag, stage_t(s), in.gc, len, 4, lane - 17);
+                    store_edges(p.ctag, stage_t(s), in.gc + p.sh_tag, len, 4, lane - 17);
                 }
             } else {
                 V* gA = static_cast<V*>(p.cv);
                 V* gB = static_cast<V*>(p.cv2);
-                const int pha = int(in.ga & (EV - 1));
+                const int64_t ga = in.ga + p.sh_cv, gb = in.gb + p.sh_cv2;
+                const int pha = int(ga & (EV - 1));
                 const int ob = ((pha + in.alen + EV - 1) / EV) * EV;
                 if (lane == 0) {
-                    store_bulk(gA, stage_g(s), in.ga, in.alen, EV);
-                    store_bulk(gB, stage_g(s) + ob, in.gb, in.blen, EV);
+                    store_bulk(gA, stage_g(s), ga, in.alen, EV);
+                    store_bulk(gB, stage_g(s) + ob, gb, in.blen, EV);
                     bulk_commit();
                 } else if (lane <= 2 * EV) {
-                    store_edges(gA, stage_g(s), in.ga, in.alen, EV, lane - 1);
+                    store_edges(gA, stage_g(s), ga, in.alen, EV, lane - 1);
                 } else if (lane >= 9 && lane < 9 + 2 * EV) {
-                    store_edges(gB, stage_g(s) + ob, in.gb, in.blen, EV, lane - 9);
+                    store_edges(gB, stage_g(s) + ob, gb, in.blen, EV, lane - 9);
                 }
             }
             if (lane == 0) bulk_wait_read<0>();   // the bulk store has read the stage
@@ -351,8 +376,10 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             }
             const int32_t len = cur.alen + cur.blen;
             K* sk = stage_k(s);
-            const WinPlan wa = plan_window(cur.ga, cur.alen, p.a_total, EK);
-            const WinPlan wb = plan_window(cur.gb, cur.blen, p.b_total, EK);
+            const WinPlan wa = plan_window(cur.ga + p.sh_ak, cur.alen, p.sh_ak,
+                                           p.a_total + p.sh_ak, EK);
+            const WinPlan wb = plan_window(cur.gb + p.sh_bk, cur.blen, p.sh_bk,
+                                           p.b_total + p.sh_bk, EK);
             StageInfo in;
             in.ga = cur.ga;
             in.gb = cur.gb;
@@ -364,13 +391,13 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             uint32_t bytes = uint32_t((wa.bulk + wb.bulk) * sizeof(K));
             WinPlan va{}, vb{}, wg{};
             if (!BWD && VB) {
-                va = plan_window(cur.ga, cur.alen, p.a_total, EV);
-                vb = plan_window(cur.gb, cur.blen, p.b_total, EV);
+                va = plan_window(cur.ga + p.sh_av, cur.alen, p.sh_av, p.a_total + p.sh_av, EV);
+                vb = plan_window(cur.gb + p.sh_bv, cur.blen, p.sh_bv, p.b_total + p.sh_bv, EV);
                 in.av = va.head;
                 in.bv = va.sup + vb.head;
                 bytes += uint32_t((va.bulk + vb.bulk) * sizeof(V));
             } else if (BWD) {
-                wg = plan_window(cur.gc, len, p.c_total, EV);
+                wg = plan_window(cur.gc + p.sh_gc, len, p.sh_gc, p.c_total + p.sh_gc, EV);
                 in.av = wg.head;
                 in.bv = 0;
                 bytes += uint32_t(wg.bulk * sizeof(V));
@@ -490,7 +517,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                         if (q < cnt[c]) step(c, q, BoolC<true>{});
             }
             named_sync(1, NT);   // every input of stage s has been read
-            const int ph = int(in.gc & (EK - 1));
+            const int ph = int((in.gc + p.sh_ck) & (EK - 1));
 #pragma unroll
             for (int c = 0; c < ILP; ++c)
 #pragma unroll
@@ -499,7 +526,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                         sk[ph + d[c] + q] = ORD ? om.inverse(okey[c][q]) : okey[c][q];
             if constexpr (VB != 0) {
                 V* ov = stage_v(s);
-                const int phv = int(in.gc & (EV - 1));
+                const int phv = int((in.gc + p.sh_cv) & (EV - 1));
 #pragma unroll
                 for (int c = 0; c < ILP; ++c)
 #pragma unroll
@@ -508,7 +535,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             }
             if constexpr (TAG) {
                 uint32_t* ot = stage_t(s);
-                const int pht = int(in.gc & 3);
+                const int pht = int((in.gc + p.sh_tag) & 3);
 #pragma unroll
                 for (int c = 0; c < ILP; ++c)
 #pragma unroll
@@ -531,8 +558,9 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             V gval[ILP][IPT];
             int dst[ILP][IPT];
             const V* sg = stage_g(s) + in.av;
-            const int pha = int(in.ga & (EV - 1));
-            const int boff = ((pha + alen + EV - 1) / EV) * EV + int(in.gb & (EV - 1));
+            const int pha = int((in.ga + p.sh_cv) & (EV - 1));
+            const int boff =
+                ((pha + alen + EV - 1) / EV) * EV + int((in.gb + p.sh_cv2) & (EV - 1));
             auto step = [&](int c, int q, auto guard) {
                 const bool takeA = decltype(guard)::value
                                        ? (k[c] >= blen) || (j[c] < alen && !(b[c] < a[c]))

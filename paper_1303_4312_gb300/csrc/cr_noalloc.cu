@@ -13,9 +13,12 @@
 // The array (kNoAllocScratchBytes, 4 MiB) is a file-scope __device__ symbol:
 // every GPU on which the library is loaded holds it until the process exits.
 // In host code the symbol's name is only a host-side stand-in, so the device
-// address is looked up with cudaGetSymbolAddress once per device (the first
-// call on that device, with that device current) and then passed to the
-// kernels.  That first call should be made before any stream capture begins.
+// address is looked up with cudaGetSymbolAddress on the first call on each
+// device (with that device current) and then passed to the kernels.  Only a
+// successful lookup is kept; a failed one is retried by the next call.  That
+// first call should be made before any stream capture begins.  The kept
+// address belongs to the device context it was looked up in: after
+// cudaDeviceReset the library must not be called again in this process.
 //
 // All calls share the one array: two calls whose kernels overlap on the GPU
 // (different streams, or different host threads) race on it and may produce
@@ -43,9 +46,8 @@ constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDev = 64;
-void* g_scratch_ptr[kMaxDev];
-std::once_flag g_scratch_once[kMaxDev];
-cudaError_t g_scratch_err[kMaxDev];
+std::mutex g_scratch_mu[kMaxDev];
+void* g_scratch_ptr[kMaxDev];   // nullptr until a lookup on that device succeeded
 
 cr_status na_fail(cr_status st, const char* fmt, ...) {
     char buf[384];
@@ -57,21 +59,26 @@ cr_status na_fail(cr_status st, const char* fmt, ...) {
     return st;
 }
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device.  A successful
+// lookup is kept for later calls; a failed one is not, so the next call
+// tries again.
 cr_status scratch_on_current_device(void** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return na_fail(CR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDev) return na_fail(CR_EUNSUPPORTED, "device %d out of range", dev);
-    std::call_once(g_scratch_once[dev], [dev] {
+    std::lock_guard<std::mutex> lock(g_scratch_mu[dev]);
+    if (g_scratch_ptr[dev] == nullptr) {
         void* p = nullptr;
-        g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        g_scratch_ptr[dev] = (g_scratch_err[dev] == cudaSuccess) ? p : nullptr;
-    });
-    if (g_scratch_err[dev] != cudaSuccess || g_scratch_ptr[dev] == nullptr)
-        return na_fail(CR_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
-                       cudaGetErrorString(g_scratch_err[dev]));
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            if (e != cudaSuccess) (void)cudaGetLastError();   // not sticky: clear it
+            return na_fail(CR_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                           cudaGetErrorString(e));
+        }
+        g_scratch_ptr[dev] = p;
+    }
     *out = g_scratch_ptr[dev];
     return CR_OK;
 }
@@ -90,11 +97,23 @@ extern "C" cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_
     const int ks = cr::key_type_bytes(key_type);
     if (ks == 0) return na_fail(CR_EINVAL, "unknown key type %d", key_type);
     if (m < 0 || n < 0) return na_fail(CR_EINVAL, "negative size");
+    const int64_t max_tiles =
+        int64_t((kNoAllocScratchBytes - size_t(cr::kHeaderBytes)) / sizeof(cr::TileRec));
+    // Refused before m + n is formed: no table of any tile shape could hold
+    // more than max_tiles * largest_tile elements (far below 2^63), so the
+    // sum and the tile count below cannot overflow.
+    int64_t largest_tile = 0;
+    for (int s = 0; s < cr::kNumShapes; ++s)
+        largest_tile = cr::tile_of_shape(s) > largest_tile ? cr::tile_of_shape(s) : largest_tile;
+    const int64_t cap = max_tiles * largest_tile;
+    if (m > cap || n > cap - m)
+        return na_fail(CR_EINVAL,
+                       "m + n exceeds the %lld elements the fixed %zu-byte scratch array can "
+                       "plan with any tile shape; use cr_stable_merge with a workspace",
+                       static_cast<long long>(cap), kNoAllocScratchBytes);
     const int64_t mn = m + n;
     const int shape = cr::current_shape(ks, 0, cr::geometry_class(m, n));
     const int64_t tile = cr::tile_of_shape(shape);
-    const int64_t max_tiles =
-        int64_t((kNoAllocScratchBytes - size_t(cr::kHeaderBytes)) / sizeof(cr::TileRec));
     const int64_t ntiles = (mn + tile - 1) / tile;
     if (ntiles > max_tiles)
         return na_fail(CR_EINVAL,
@@ -102,13 +121,15 @@ extern "C" cr_status cr_stable_merge_noalloc(int key_type, const void* A, int64_
                        "array can plan for this key type; use cr_stable_merge with a workspace",
                        static_cast<long long>(mn), static_cast<long long>(max_tiles * tile),
                        kNoAllocScratchBytes);
-    struct { const void* p; int64_t count; const char* name; } arrs[4] = {
-        {A, m, "A"}, {B, n, "B"}, {C, mn, "C"}, {C_tag, C_tag ? mn : 0, "C tag"}};
+    // Arrays need only be aligned to their element size (the kernels
+    // address whole 16-byte chunks from the boundary below each start).
+    struct { const void* p; int64_t count; int elem; const char* name; } arrs[4] = {
+        {A, m, ks, "A"}, {B, n, ks, "B"}, {C, mn, ks, "C"}, {C_tag, C_tag ? mn : 0, 4, "C tag"}};
     for (auto& a : arrs) {
         if (a.count == 0) continue;
         if (a.p == nullptr) return na_fail(CR_EINVAL, "%s is NULL", a.name);
-        if (reinterpret_cast<uintptr_t>(a.p) & 15u)
-            return na_fail(CR_EALIGN, "%s is not 16-byte aligned", a.name);
+        if (reinterpret_cast<uintptr_t>(a.p) % uintptr_t(a.elem))
+            return na_fail(CR_EALIGN, "%s is not aligned to %d bytes", a.name, a.elem);
     }
     if (ranges_overlap(C, mn * ks, A, m * ks) || ranges_overlap(C, mn * ks, B, n * ks) ||
         (C_tag && (ranges_overlap(C_tag, mn * 4, A, m * ks) ||

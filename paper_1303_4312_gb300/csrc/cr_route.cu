@@ -23,7 +23,8 @@ namespace cr {
 namespace {
 
 constexpr int kRouteThreads = 128;
-constexpr int kRouteMaxTile = 4096;   // >= every shape's TILE
+constexpr int kRouteMaxTile = 4096;   // the largest tile a recorded pass may use
+static_assert(kRouteMaxTile == kMaxRecordTile, "recorded-pass tile limit");
 constexpr int kRouteMaxWords = kRouteMaxTile / 32;
 
 // Asynchronous global -> shared copies (no registers held while in flight).

@@ -89,7 +89,7 @@ def test_status_strings(lib):
     for code, name in _lib.STATUS.items():
         assert lib.cr_status_string(code).decode() == name
     assert lib.cr_status_string(99).decode() == "CR_UNKNOWN"
-    assert lib.cr_abi_version() == 101
+    assert lib.cr_abi_version() == 200
 
 
 def test_tile_sizes(lib):
@@ -114,9 +114,25 @@ def test_validation_without_gpu(lib):
     assert lib.cr_stable_merge(9, A, 1, A, 1, A, None, A, 1 << 20, None) == 1
     # negative size
     assert lib.cr_stable_merge(0, A, -1, A, 1, A, None, A, 1 << 20, None) == 1
-    # misaligned
-    assert lib.cr_stable_merge(0, ctypes.c_void_p(0x10004), 4, A, 4, ctypes.c_void_p(0x20000),
+    # misaligned: not a multiple of the 4-byte key size (4-byte offsets are fine)
+    assert lib.cr_stable_merge(0, ctypes.c_void_p(0x10002), 4, A, 4, ctypes.c_void_p(0x20000),
                                None, A, 1 << 20, None) == 3
+    assert "aligned to 4" in _err(lib)
+    # 8-byte keys need 8-byte alignment; a 4-byte aligned payload array is fine for
+    # 4-byte payloads but not for 8-byte ones
+    assert lib.cr_stable_merge(3, ctypes.c_void_p(0x10004), 4, A, 4, ctypes.c_void_p(0x20000),
+                               None, A, 1 << 20, None) == 3
+    assert lib.cr_stable_merge_kv(0, 8, A, ctypes.c_void_p(0x30004), 4, ctypes.c_void_p(0x40000),
+                                  ctypes.c_void_p(0x50000), 4, ctypes.c_void_p(0x60000),
+                                  ctypes.c_void_p(0x70000), None, ctypes.c_void_p(0x80000),
+                                  1 << 20, None) == 3
+    # the workspace itself must stay 16-byte aligned
+    assert lib.cr_stable_merge(0, ctypes.c_void_p(0x10004), 4, A, 4, ctypes.c_void_p(0x20000),
+                               None, ctypes.c_void_p(0x50008), 1 << 20, None) == 3
+    assert "workspace" in _err(lib)
+    # sizes whose products with an element width or whose sum would overflow
+    assert lib.cr_stable_merge(0, A, 1 << 62, A, 1 << 62, A, None, A, 1 << 20, None) == 1
+    assert lib.cr_merge_pass(0, 0, A, None, (1 << 63) - 1, 2, A, None, A, 1 << 20, None) == 1
     # output overlaps input
     assert lib.cr_stable_merge(0, ctypes.c_void_p(0x10000), 64, ctypes.c_void_p(0x30000), 64,
                                ctypes.c_void_p(0x10040), None, ctypes.c_void_p(0x50000), 1 << 20,
@@ -127,8 +143,19 @@ def test_validation_without_gpu(lib):
                                None) == 4
     # payload width
     assert lib.cr_stable_merge_kv(0, 3, A, A, 1, A, A, 1, A, A, None, A, 1 << 20, None) == 1
-    # rank out of range
-    assert lib.cr_co_rank(0, A, 4, A, 4, 9, A, None) == 1
+    # rank out of range (host-result and device-result forms)
+    i, j = ctypes.c_int64(-5), ctypes.c_int64(-5)
+    assert lib.cr_co_rank(0, A, 4, A, 4, 9, ctypes.byref(i), ctypes.byref(j), None) == 1
+    assert lib.cr_co_rank(0, A, 4, A, 4, -1, ctypes.byref(i), ctypes.byref(j), None) == 1
+    assert lib.cr_co_rank(0, A, 4, A, 4, 2, None, ctypes.byref(j), None) == 1
+    assert lib.cr_co_rank_async(0, A, 4, A, 4, 9, A, None) == 1
+    assert lib.cr_co_rank_async(0, A, 4, A, 4, 2, ctypes.c_void_p(0x10004), None) == 3
+    # trivial ranks are answered on the host without a launch: rank 0, rank m + n,
+    # and every rank of a merge with one empty side
+    for m, n, k, want in ((4, 4, 0, (0, 0)), (4, 4, 8, (4, 4)), (0, 7, 5, (0, 5)),
+                          (7, 0, 5, (5, 0))):
+        assert lib.cr_co_rank(0, A, m, A, n, k, ctypes.byref(i), ctypes.byref(j), None) == 0
+        assert (i.value, j.value) == want
     # tags need m + n <= 2^32
     big = 1 << 31
     assert lib.cr_stable_merge(0, ctypes.c_void_p(0x1_0000_0000), big,
@@ -148,10 +175,10 @@ def test_workspace_sizes(lib):
     assert lib.cr_merge_workspace_size(0, 0, 5 * t, 3 * t + 1, ctypes.byref(out)) == 0
     assert out.value == 256 + 32 * 9
     assert lib.cr_batched_workspace_size(0, 4, 10, 1000, 2000, ctypes.byref(out)) == 0
-    t4 = lib.cr_tile_size(0, 4)
+    t4 = lib.cr_tile_size_class(0, 4, 3)          # the batched class
     assert out.value == 256 + 32 * ((3000 + t4 - 1) // t4 + 10) + 8 * 11
     assert lib.cr_merge_pass_workspace_size(3, 4, 1 << 20, 1024, ctypes.byref(out)) == 0
-    t8 = lib.cr_tile_size(3, 4)
+    t8 = lib.cr_tile_size_class(3, 4, 4)          # the pass class
     assert out.value == 256 + 32 * ((1 << 20) // 2048) * ((2048 + t8 - 1) // t8)
 
 
@@ -218,14 +245,61 @@ def test_geometry_classes(lib):
         assert lib.cr_tile_size_for(kt, 0, big // 2, big // 2 + 1) == t2
         assert lib.cr_merge_workspace_size(kt, 0, 10, 100000, ctypes.byref(out)) == 0
         assert out.value == 256 + 32 * ((100010 + t0 - 1) // t0)
-        # classes other than 0, 1, 2 are refused
-        assert lib.cr_set_tile_shape_for(kt, 0, 3, 0) == 1
+        # classes other than 0 .. 4 are refused
+        assert lib.cr_set_tile_shape_for(kt, 0, 5, 0) == 1
         assert lib.cr_set_tile_shape_for(kt, 0, -1, 0) == 1
-        assert lib.cr_get_tile_shape_for(kt, 0, 3) == -1
+        assert lib.cr_get_tile_shape_for(kt, 0, 5) == -1
+        assert lib.cr_tile_size_class(kt, 0, 5) == 0
     finally:
         lib.cr_set_tile_shape_for(kt, 0, 0, b0)
         lib.cr_set_tile_shape_for(kt, 0, 1, s0)
         lib.cr_set_tile_shape_for(kt, 0, 2, m0)
+
+
+def test_batched_and_pass_classes(lib):
+    """Batched calls and merge passes take shapes of their own (classes 3 and
+    4): their workspace sizes follow those shapes, not the single-merge ones;
+    a pass-class shape with payloads is limited to tiles of 4096 elements."""
+    nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    tiles = []
+    for s in range(lib.cr_tile_shape_count()):
+        lib.cr_tile_shape_info(s, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
+        tiles.append(nt.value * ipt.value * ilp.value)
+    kt, vb = 0, 4
+    saved = [lib.cr_get_tile_shape_for(kt, vb, c) for c in range(5)]
+    saved0 = [lib.cr_get_tile_shape_for(kt, 0, c) for c in range(5)]
+    out = ctypes.c_size_t()
+    try:
+        assert lib.cr_set_tile_shape_for(kt, vb, 0, 0) == 0
+        assert lib.cr_set_tile_shape_for(kt, vb, 3, 2) == 0
+        assert lib.cr_set_tile_shape_for(kt, vb, 4, 3) == 0
+        assert lib.cr_tile_size_class(kt, vb, 3) == tiles[2]
+        assert lib.cr_tile_size_class(kt, vb, 4) == tiles[3]
+        assert lib.cr_tile_size(kt, vb) == tiles[0]
+        assert lib.cr_batched_workspace_size(kt, vb, 3, 10000, 5000, ctypes.byref(out)) == 0
+        assert out.value == 256 + 32 * ((15000 + tiles[2] - 1) // tiles[2] + 3) + 8 * 4
+        assert lib.cr_merge_pass_workspace_size(kt, vb, 100000, 4096, ctypes.byref(out)) == 0
+        tpp = (8192 + tiles[3] - 1) // tiles[3]
+        npairs = (100000 + 8191) // 8192
+        last = 100000 - 8192 * (npairs - 1)
+        assert out.value == 256 + 32 * ((npairs - 1) * tpp + (last + tiles[3] - 1) // tiles[3])
+        big = [s for s, t in enumerate(tiles) if t > 4096]
+        for s in big:
+            if lib.cr_set_tile_shape_for(kt, vb, 0, s) == 0:     # fits this combination
+                assert lib.cr_set_tile_shape_for(kt, vb, 4, s) == 7
+                assert b"4096" in lib.cr_last_error()
+                # setting every class leaves the pass class as it was
+                assert lib.cr_set_tile_shape(kt, vb, s) == 0
+                assert lib.cr_get_tile_shape_for(kt, vb, 4) == 3
+                assert lib.cr_get_tile_shape_for(kt, vb, 3) == s
+            # keys-only passes are not recorded: any fitting shape is fine
+            if lib.cr_set_tile_shape_for(kt, 0, 0, s) == 0:
+                assert lib.cr_set_tile_shape_for(kt, 0, 4, s) == 0
+    finally:
+        for c, s in enumerate(saved):
+            lib.cr_set_tile_shape_for(kt, vb, c, s)
+        for c, s in enumerate(saved0):
+            lib.cr_set_tile_shape_for(kt, 0, c, s)
 
 
 def test_recorded_pass_sizes_and_validation(lib):
@@ -233,8 +307,8 @@ def test_recorded_pass_sizes_and_validation(lib):
     (all fail before any launch)."""
     ws, fw = ctypes.c_size_t(), ctypes.c_size_t()
     for code, vb in ((0, 4), (1, 8), (2, 4), (3, 4), (3, 8)):
-        t = lib.cr_tile_size(code, vb)
-        assert t % 128 == 0
+        t = lib.cr_tile_size_class(code, vb, 4)
+        assert t % 128 == 0 and t <= 4096
         for N, w in ((1 << 20, 1024), (1 << 20, 3000), (12345, 100), (7, 1 << 40), (5000, 1)):
             assert lib.cr_merge_pass_record_size(code, vb, N, w, ctypes.byref(ws),
                                                  ctypes.byref(fw)) == 0
@@ -286,7 +360,7 @@ def test_recorded_run_sort_validation(lib):
     # keys-only payload width, NULL perm, misaligned or overlapping perm
     assert lib.cr_sort_runs_record(0, 0, X, None, N, Y, None, P, None) == 1
     assert lib.cr_sort_runs_record(0, 4, X, Xv, N, Y, Yv, None, None) == 1
-    assert lib.cr_sort_runs_record(0, 4, X, Xv, N, Y, Yv, ctypes.c_void_p(0x500002), None) == 3
+    assert lib.cr_sort_runs_record(0, 4, X, Xv, N, Y, Yv, ctypes.c_void_p(0x500001), None) == 3
     assert lib.cr_sort_runs_record(0, 4, X, Xv, N, Y, Yv, ctypes.c_void_p(0x300010), None) == 2
     assert lib.cr_sort_runs_record(9, 4, X, Xv, N, Y, Yv, P, None) == 1
     G, GX = ctypes.c_void_p(0x600000), ctypes.c_void_p(0x700000)
@@ -313,7 +387,7 @@ def test_merge_runs_block_validation(lib):
     assert lib.cr_merge_runs_block(0, 0, X, None, N, 1, Y, None, P, None) == 1
     assert lib.cr_merge_runs_block(99, 4, X, Xv, N, 1, Y, Yv, P, None) == 1
     assert lib.cr_merge_runs_block(0, 4, X, Xv, -1, 1, Y, Yv, P, None) == 1
-    assert lib.cr_merge_runs_block(0, 4, X, Xv, N, 1, ctypes.c_void_p(0x300004), Yv, P,
+    assert lib.cr_merge_runs_block(0, 4, X, Xv, N, 1, ctypes.c_void_p(0x300002), Yv, P,
                                    None) == 3
     assert lib.cr_merge_runs_block(0, 4, X, Xv, N, 1, ctypes.c_void_p(0x100010), Yv, P,
                                    None) == 2
@@ -326,7 +400,7 @@ def test_merge_runs_block_validation(lib):
     assert lib.cr_merge_runs_block_backward_recorded(0, N, P, G, GX, None) == 1
     assert lib.cr_merge_runs_block_backward_recorded(4, N, P, G, ctypes.c_void_p(0x600100),
                                                      None) == 2
-    assert lib.cr_merge_runs_block_backward_recorded(4, N, ctypes.c_void_p(0x500002), G, GX,
+    assert lib.cr_merge_runs_block_backward_recorded(4, N, ctypes.c_void_p(0x500001), G, GX,
                                                      None) == 3
     assert lib.cr_merge_runs_block_backward_recorded(4, 0, None, None, None, None) == 0
 
@@ -367,5 +441,5 @@ def test_check_sorted_argument_checks(lib):
     assert lib.cr_check_sorted(0, None, 10, O, WS, 16, None) == 1
     assert lib.cr_check_sorted(0, A, 10, None, WS, 16, None) == 1
     assert lib.cr_check_sorted(0, A, 10, O, WS, 8, None) == 1
-    assert lib.cr_check_sorted(0, ctypes.c_void_p(0x100004), 10, O, WS, 16, None) == 3
+    assert lib.cr_check_sorted(0, ctypes.c_void_p(0x100002), 10, O, WS, 16, None) == 3
     assert b"aligned" in lib.cr_last_error()
