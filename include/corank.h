@@ -177,6 +177,56 @@ cr_status cr_co_rank_many(int key_type, const void* A, int64_t m, const void* B,
                           cr_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Block-distributed co-rank: Algorithm 1 (Section 2) when A and B are spread
+ * over the processing elements of Algorithm 2 in contiguous blocks, as in the
+ * distributed-memory remark of Section 3: every key a search compares is a
+ * remote point read.  One iteration of cnt searches is split into the parts
+ * a process group runs between its collectives:
+ *   1. cr_dist_co_rank_probes: the positions each live search reads next;
+ *   2. cr_dist_co_rank_answer: every rank answers the probes that fall in
+ *      its own block (0 elsewhere), and the group sums the answers (one
+ *      all-reduce), which delivers every key exactly once;
+ *   3. cr_dist_co_rank_step: one iteration of Algorithm 1 on those keys.
+ * After at most ceil(log2(min(m, n) + 1)) + 1 iterations every search has
+ * finished (the corrected iteration bound of Proposition 1 plus the final
+ * check); cr_dist_co_rank_result reads the co-ranks and counts unfinished
+ * searches.  The arithmetic runs in these kernels; the caller only moves
+ * the probe positions and answers between ranks.
+ *
+ * State (device, int64, 6 * cnt entries, column by column): rank k, co-rank
+ * i (into A), co-rank j (into B), the low bounds of i and j, and a finished
+ * flag.  Probe arrays (device, int64, 2 * cnt entries each): pa[2q] = i - 1,
+ * pa[2q+1] = i, pb[2q] = j - 1, pb[2q+1] = j of search q, -1 where that key
+ * is not needed.  Answers (device, int64, as many as probes): the key's bits
+ * (4-byte keys zero-extended).  All arrays 8-byte aligned; m, n are the
+ * global lengths of A and B; key order as everywhere else.  Asynchronous on
+ * `stream`.  A rank outside [0, m + n] gives a finished search with
+ * i = j = -1.
+ * ------------------------------------------------------------------------ */
+cr_status cr_dist_co_rank_init(int64_t m, int64_t n, const int64_t* d_ranks, int64_t cnt,
+                               int64_t* d_state, cr_stream stream);
+
+cr_status cr_dist_co_rank_probes(int64_t m, int64_t n, const int64_t* d_state, int64_t cnt,
+                                 int64_t* d_probe_a, int64_t* d_probe_b, cr_stream stream);
+
+/* d_vals[q] = bits of blk[d_idx[q] - lo] when lo <= d_idx[q] < hi, else 0.
+ * blk (device): this rank's block of A or B, the elements [lo, hi) of that
+ * array. */
+cr_status cr_dist_co_rank_answer(int key_type, const void* blk, int64_t lo, int64_t hi,
+                                 const int64_t* d_idx, int64_t cnt, int64_t* d_vals,
+                                 cr_stream stream);
+
+/* d_vals_a / d_vals_b: the summed answers to d_probe_a / d_probe_b. */
+cr_status cr_dist_co_rank_step(int key_type, int64_t m, int64_t n, const int64_t* d_vals_a,
+                               const int64_t* d_vals_b, int64_t* d_state, int64_t cnt,
+                               cr_stream stream);
+
+/* d_i[q], d_j[q] = the co-ranks of search q; *d_live (device, one uint64) =
+ * the number of searches not yet finished. */
+cr_status cr_dist_co_rank_result(const int64_t* d_state, int64_t cnt, int64_t* d_i,
+                                 int64_t* d_j, uint64_t* d_live, cr_stream stream);
+
+/* ------------------------------------------------------------------------
  * stable_merge -- Algorithm 2 (Section 3) with fixed-size output tiles.
  * C[0, m+n) = stable merge of A[0, m) and B[0, n).
  * ------------------------------------------------------------------------ */

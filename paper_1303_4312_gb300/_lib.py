@@ -70,6 +70,11 @@ SIGNATURES = {
     "cr_sort_runs_backward_recorded": ([INT, I64, P, P, P, P], INT),
     "cr_sort_runs_backward": ([INT, INT, P, I64, P, P, P], INT),
     "cr_stable_merge_noalloc": ([INT, P, I64, P, I64, P, P, P], INT),
+    "cr_dist_co_rank_init": ([I64, I64, P, I64, P, P], INT),
+    "cr_dist_co_rank_probes": ([I64, I64, P, I64, P, P, P], INT),
+    "cr_dist_co_rank_answer": ([INT, P, I64, I64, P, I64, P, P], INT),
+    "cr_dist_co_rank_step": ([INT, I64, I64, P, P, P, I64, P], INT),
+    "cr_dist_co_rank_result": ([P, I64, P, P, P, P], INT),
 }
 
 STATUS = {0: "CR_OK", 1: "CR_EINVAL", 2: "CR_EALIAS", 3: "CR_EALIGN", 4: "CR_ENOSPACE",

@@ -78,13 +78,20 @@ def _size(fn, *args) -> int:
     return out.value
 
 
+TILE_CLASSES = {"balanced": 0, "skewed": 1, "small": 2, "batched": 3, "pass": 4}
+
+
 def tile_size(key_type: str, val_bytes: int = 0, m: int | None = None,
-              n: int | None = None) -> int:
+              n: int | None = None, cls: str | int | None = None) -> int:
     """Output elements per tile used for this key type and payload width: by
-    a single merge of m and n elements when given (its geometry class), else
-    by batched calls, merge passes and large balanced merges."""
+    a single merge of m and n elements when given (its geometry class), by
+    class `cls` when given ("balanced", "skewed", "small", "batched" for
+    batched calls, "pass" for merge passes), else by large balanced merges."""
     lib = _lib.load()
     code = _lib.key_code(key_type)
+    if cls is not None:
+        c = TILE_CLASSES[cls] if isinstance(cls, str) else int(cls)
+        return int(lib.cr_tile_size_class(code, int(val_bytes), c))
     if m is None and n is None:
         return int(lib.cr_tile_size(code, int(val_bytes)))
     return int(lib.cr_tile_size_for(code, int(val_bytes), int(m or 0), int(n or 0)))
@@ -138,6 +145,67 @@ def co_rank_many(A: torch.Tensor, B: torch.Tensor, ks: torch.Tensor, key_type: s
     _lib.check(lib.cr_co_rank_many(kt, _ptr(A), A.numel(), _ptr(B), B.numel(), _ptr(ks),
                                    ks.numel(), _ptr(oi), _ptr(oj), _stream(dev)))
     return oi, oj
+
+
+class DistCoRank:
+    """Algorithm 1 for block-distributed A and B (the library's
+    cr_dist_co_rank_* calls): `cnt` searches whose state lives on `device`.
+    One iteration is probes() -> answer() on every rank's blocks -> a sum of
+    the answers over the ranks -> step().  m, n: global lengths."""
+
+    def __init__(self, m: int, n: int, ranks, key_type: str, device):
+        self.lib = _lib.load()
+        self.m, self.n = int(m), int(n)
+        self.code = _lib.key_code(key_type)
+        self.dev = torch.device(device)
+        r = torch.as_tensor(list(ranks) if not torch.is_tensor(ranks) else ranks,
+                            dtype=torch.int64).to(self.dev).contiguous()
+        self.cnt = r.numel()
+        self.state = torch.empty(6 * self.cnt, dtype=torch.int64, device=self.dev)
+        self._pa = torch.empty(2 * self.cnt, dtype=torch.int64, device=self.dev)
+        self._pb = torch.empty(2 * self.cnt, dtype=torch.int64, device=self.dev)
+        self._live = torch.empty(1, dtype=torch.int64, device=self.dev)
+        _lib.check(self.lib.cr_dist_co_rank_init(self.m, self.n, _ptr(r), self.cnt,
+                                                 _ptr(self.state), _stream(self.dev)))
+        self._ranks = r
+
+    def iterations(self) -> int:
+        """Iterations after which every search has finished: the corrected
+        bound of Proposition 1, ceil(log2(min(m, n) + 1)), plus the final
+        check."""
+        return int(min(self.m, self.n)).bit_length() + 1
+
+    def probes(self):
+        """(pa, pb): the A and B positions the next iteration reads (-1: none)."""
+        _lib.check(self.lib.cr_dist_co_rank_probes(self.m, self.n, _ptr(self.state), self.cnt,
+                                                   _ptr(self._pa), _ptr(self._pb),
+                                                   _stream(self.dev)))
+        return self._pa, self._pb
+
+    def answer(self, blk: torch.Tensor, lo: int, idx: torch.Tensor) -> torch.Tensor:
+        """Keys (int64 bits) of the positions in idx that fall in this rank's
+        block blk = X[lo, lo + len(blk)), 0 for the others."""
+        out = torch.empty(idx.numel(), dtype=torch.int64, device=self.dev)
+        if blk.numel():
+            _dev(blk, idx)
+        _lib.check(self.lib.cr_dist_co_rank_answer(self.code, _ptr(blk) if blk.numel() else None,
+                                                   int(lo), int(lo) + blk.numel(), _ptr(idx),
+                                                   idx.numel(), _ptr(out), _stream(self.dev)))
+        return out
+
+    def step(self, va: torch.Tensor, vb: torch.Tensor) -> None:
+        """One iteration of Algorithm 1 with the summed answers to probes()."""
+        va, vb = va.contiguous(), vb.contiguous()
+        _lib.check(self.lib.cr_dist_co_rank_step(self.code, self.m, self.n, _ptr(va), _ptr(vb),
+                                                 _ptr(self.state), self.cnt, _stream(self.dev)))
+
+    def result(self):
+        """([(i, j) per search], number of unfinished searches); synchronises."""
+        oi = torch.empty(self.cnt, dtype=torch.int64, device=self.dev)
+        oj = torch.empty(self.cnt, dtype=torch.int64, device=self.dev)
+        _lib.check(self.lib.cr_dist_co_rank_result(_ptr(self.state), self.cnt, _ptr(oi),
+                                                   _ptr(oj), _ptr(self._live), _stream(self.dev)))
+        return list(zip(oi.tolist(), oj.tolist())), int(self._live.item())
 
 
 # ---------------------------------------------------------------------------

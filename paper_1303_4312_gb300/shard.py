@@ -82,36 +82,12 @@ def sharded_merge(A, B, group=None, co_rank=None, merge=None, gather: bool = Tru
 
 # ---------------------------------------------------------------------------
 # Block-distributed inputs: rank r holds only A[a_off[r], a_off[r+1]) and
-# B[b_off[r], b_off[r+1]).  The co-ranks of every rank's output block are
-# found by Algorithm 1 with remote point reads, then each rank fetches the
-# two windows they delimit from their owners and merges them locally.
+# B[b_off[r], b_off[r+1]).  The co-ranks of every block boundary are found
+# by Algorithm 1 with remote point reads (the library's cr_dist_co_rank_*
+# kernels do the arithmetic; this module only runs the collectives), then
+# each rank fetches the two windows they delimit from their owners and
+# merges them locally.
 # ---------------------------------------------------------------------------
-_WIDTH = {"i32": 32, "u32": 32, "f32": 32, "i64": 64, "u64": 64, "f64": 64, "pair_u32": 64,
-          "pair_i32": 64}
-
-
-def _as_key(v: int, key_type: str) -> int:
-    """A key read back from an int64 carrier (the bits of the stored key,
-    sign-extended from its width), as a Python int whose integer order is the
-    key type's order: unsigned types are masked to their width; float bits
-    (IEEE-754 totalOrder) keep positives and flip the magnitude of negatives;
-    ':desc' negates."""
-    base, _, mod = key_type.partition(":")
-    bits = _WIDTH[base]
-    if base.startswith("pair"):
-        v &= (1 << 64) - 1
-        if base == "pair_i32":
-            v ^= (1 << 63) | (1 << 31)      # both halves' sign bits: lexicographic
-        return -v if mod == "desc" else v
-    if base[0] == "u":
-        v &= (1 << bits) - 1
-    else:
-        v = ((v + (1 << (bits - 1))) & ((1 << bits) - 1)) - (1 << (bits - 1))   # sign-extend
-        if base[0] == "f" and v < 0:
-            v ^= (1 << (bits - 1)) - 1
-    return -v if mod == "desc" else v
-
-
 def _bits(t):
     """Integer view of a key block (floats travel as their bit patterns)."""
     import torch
@@ -120,85 +96,43 @@ def _bits(t):
     return t
 
 
-class _Prober:
-    """Point reads of A and B by global index: every rank all-gathers the
-    indices it wants (-1 for none), answers those that fall in its own
-    blocks, and an all-reduce (sum) hands each rank its answers (exactly one
-    rank owns each index, the others contribute zero)."""
-
-    def __init__(self, A_blk, B_blk, a_off, b_off, rank, world, group):
-        import torch
-        self.torch = torch
-        self.A, self.B = _bits(A_blk), _bits(B_blk)
-        self.a0, self.a1 = a_off[rank], a_off[rank + 1]
-        self.b0, self.b1 = b_off[rank], b_off[rank + 1]
-        self.world, self.group = world, group
-        self.dev = A_blk.device
-
-    def read(self, ia, ib):
-        import torch.distributed as dist
-        torch = self.torch
-        ra = len(ia)
-        req = torch.tensor(list(ia) + list(ib), dtype=torch.int64, device=self.dev)
-        parts = [torch.empty_like(req) for _ in range(self.world)]
-        dist.all_gather(parts, req, group=self.group)
-        allreq = torch.stack(parts)                       # world x (ra + rb)
-        ans = torch.zeros_like(allreq)
-        for lo, hi, blk, cols in ((self.a0, self.a1, self.A, slice(0, ra)),
-                                  (self.b0, self.b1, self.B, slice(ra, None))):
-            idx = allreq[:, cols]
-            mine = (idx >= lo) & (idx < hi)
-            if bool(mine.any()):
-                sub = ans[:, cols]
-                sub[mine] = blk[idx[mine] - lo].to(torch.int64)
-                ans[:, cols] = sub
-        dist.all_reduce(ans, group=self.group)
-        mine = ans[dist.get_rank(self.group)].tolist()
-        return mine[:ra], mine[ra:]
-
-
-def distributed_co_rank(ranks, m, n, prober, key_type, group=None):
-    """Algorithm 1 (Section 2) for each output rank in `ranks`, run in lock
-    step on every rank of the group (each passes the same number of ranks),
-    with the keys it compares read remotely: one round of point reads per
-    iteration, A[j-1], A[j], B[k-1], B[k] of every unfinished search.
-    k_low starts at max(0, i - m) (the printed algorithm leaves it unset and
-    argues the first move always sets it).  Returns [(j, k), ...]."""
+def distributed_co_rank(ranks, m, n, A_blk, a_lo, B_blk, b_lo, key_type, group=None,
+                        search=None):
+    """Algorithm 1 (Section 2) for each output rank in `ranks` -- the same
+    list on every rank of the group -- with A and B block-distributed: this
+    rank holds A[a_lo, a_lo + len(A_blk)) and B[b_lo, b_lo + len(B_blk)).
+    Every rank runs all the searches in lock step; per iteration the
+    positions they read are the same everywhere, each rank answers those in
+    its own blocks (zero elsewhere) and one all-reduce (sum) delivers every
+    key.  After the iteration bound (Proposition 1, corrected: at most
+    ceil(log2(min(m, n) + 1)) moves, plus the final check) every search has
+    finished.  `search` makes the search object (default: the library's
+    kernels, api.DistCoRank).  Returns [(i, j), ...]."""
     import torch
     import torch.distributed as dist
-    st = []
-    for i in ranks:
-        j = min(i, m)
-        st.append({"i": i, "j": j, "k": i - j, "jl": max(0, i - n), "kl": max(0, i - m),
-                   "done": False})
-    while True:
-        ia, ib = [], []
-        for s in st:
-            j, k, live = s["j"], s["k"], not s["done"]
-            ia += [j - 1 if live and j > 0 else -1, j if live and j < m else -1]
-            ib += [k - 1 if live and k > 0 else -1, k if live and k < n else -1]
-        va, vb = prober.read(ia, ib)
-        for q, s in enumerate(st):
-            if s["done"]:
-                continue
-            j, k = s["j"], s["k"]
-            a_prev, a_cur = _as_key(va[2 * q], key_type), _as_key(va[2 * q + 1], key_type)
-            b_prev, b_cur = _as_key(vb[2 * q], key_type), _as_key(vb[2 * q + 1], key_type)
-            if j > 0 and k < n and a_prev > b_cur:            # first condition fails
-                d = (j - s["jl"] + 1) // 2
-                s["kl"] = k
-                s["j"], s["k"] = j - d, k + d
-            elif k > 0 and j < m and b_prev >= a_cur:         # second condition fails
-                d = (k - s["kl"] + 1) // 2
-                s["jl"] = j
-                s["j"], s["k"] = j + d, k - d
-            else:
-                s["done"] = True
-        live = torch.tensor([sum(not s["done"] for s in st)], dtype=torch.int64,
-                            device=prober.dev)
-        dist.all_reduce(live, group=group)
-        if int(live.item()) == 0:
-            return [(s["j"], s["k"]) for s in st]
+    if search is None:
+        from . import api
+        search = api.DistCoRank
+    s = search(m, n, ranks, key_type, A_blk.device)
+    a, b = _bits(A_blk), _bits(B_blk)
+
+    def iterate(times):
+        for _ in range(times):
+            pa, pb = s.probes()
+            ans = torch.cat([s.answer(a, a_lo, pa), s.answer(b, b_lo, pb)])
+            dist.all_reduce(ans, group=group)
+            s.step(ans[:pa.numel()], ans[pa.numel():])
+    iterate(s.iterations())
+    res, live = s.result()
+    # every rank holds the same state, so all take the same decision here
+    extra = 0
+    while live and extra < 64:
+        iterate(1)
+        extra += 1
+        res, live = s.result()
+    if live:
+        raise RuntimeError(f"{live} co-rank searches did not finish")
+    return res
 
 
 def _offsets(local_len, world, group, dev):
@@ -234,18 +168,20 @@ def _fetch_window(blk, off, lo_all, hi_all, rank, world, group):
 
 
 def distributed_merge(A_blk, B_blk, key_type: str, group=None, Av_blk=None, Bv_blk=None,
-                      merge=None):
+                      merge=None, search=None):
     """Stable merge of A and B block-distributed over the ranks of `group`
     (rank r holds the r-th contiguous blocks, any sizes, possibly empty).
     Rank g returns its equal output block C[floor(g(m+n)/G), floor((g+1)(m+n)/G))
     (and its payloads when Av_blk/Bv_blk are given) with its ShardPlan.
 
     Steps (Section 3's distributed reading of Algorithm 2):
-      1. co-rank both block ends with Algorithm 1 and remote point reads;
+      1. co-rank every block boundary with Algorithm 1 and remote point
+         reads (distributed_co_rank; every rank then knows every window);
       2. fetch the windows A[i0, i1) and B[j0, j1) from their owners
          (one all-to-all per array);
       3. merge them locally: `merge(A, B)` or, with payloads,
          `merge(A, Av, B, Bv) -> (C, Cv)`; by default this library's kernels.
+    `search` is passed to distributed_co_rank.
     """
     import torch.distributed as dist
     world = dist.get_world_size(group)
@@ -254,19 +190,17 @@ def distributed_merge(A_blk, B_blk, key_type: str, group=None, Av_blk=None, Bv_b
     a_off = _offsets(A_blk.numel(), world, group, dev)
     b_off = _offsets(B_blk.numel(), world, group, dev)
     m, n = a_off[-1], b_off[-1]
-    k0, k1 = block_bounds(m + n, world, rank)
-    prober = _Prober(A_blk, B_blk, a_off, b_off, rank, world, group)
-    (i0, j0), (i1, j1) = distributed_co_rank([k0, k1], m, n, prober, key_type, group)
+    # every block boundary, co-ranked by all ranks together
+    ks = [block_bounds(m + n, world, g)[0] for g in range(world)] + [m + n]
+    cr = distributed_co_rank(ks, m, n, A_blk, a_off[rank], B_blk, b_off[rank], key_type, group,
+                             search)
+    (i0, j0), (i1, j1) = cr[rank], cr[rank + 1]
+    k0, k1 = ks[rank], ks[rank + 1]
     if i0 + j0 != k0 or i1 + j1 != k1 or not (0 <= i0 <= i1 <= m and 0 <= j0 <= j1 <= n):
         raise RuntimeError("co_rank returned an inconsistent split")
     p = ShardPlan(rank, world, k0, k1, i0, i1, j0, j1)
-    import torch
-    win = torch.tensor([i0, i1, j0, j1], dtype=torch.int64, device=dev)
-    parts = [torch.empty_like(win) for _ in range(world)]
-    dist.all_gather(parts, win, group=group)
-    w = [t.tolist() for t in parts]
-    ia = [x[0] for x in w], [x[1] for x in w]
-    jb = [x[2] for x in w], [x[3] for x in w]
+    ia = [c[0] for c in cr[:-1]], [c[0] for c in cr[1:]]
+    jb = [c[1] for c in cr[:-1]], [c[1] for c in cr[1:]]
     A = _fetch_window(A_blk, a_off, ia[0], ia[1], rank, world, group)
     B = _fetch_window(B_blk, b_off, jb[0], jb[1], rank, world, group)
     kv = Av_blk is not None

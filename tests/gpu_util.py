@@ -41,3 +41,14 @@ def sorted_keys(rng, size, dtype, spread=None):
 
 def same_bits(a: np.ndarray, b: np.ndarray) -> bool:
     return a.shape == b.shape and a.tobytes() == b.tobytes()
+
+
+def save_shapes(lib, code, vb):
+    """Tile shape of every class (balanced, skewed, small, batched, pass) of
+    a key type and payload width, for restore_shapes."""
+    return [lib.cr_get_tile_shape_for(code, vb, c) for c in range(5)]
+
+
+def restore_shapes(lib, code, vb, saved):
+    for c, s in enumerate(saved):
+        assert lib.cr_set_tile_shape_for(code, vb, c, s) == 0

@@ -196,8 +196,8 @@ def test_tile_shapes(lib):
     assert lib.cr_tile_shape_info(n, ctypes.byref(nt), ctypes.byref(ipt), None) == 1
     for kt in range(4):
         for vb in (0, 4, 8):
-            before = lib.cr_get_tile_shape(kt, vb)
-            assert 0 <= before < n
+            before = [lib.cr_get_tile_shape_for(kt, vb, c) for c in range(5)]
+            assert all(0 <= b < n for b in before)
             try:
                 for s in range(n):
                     st = lib.cr_set_tile_shape(kt, vb, s)
@@ -206,7 +206,8 @@ def test_tile_shapes(lib):
                         assert lib.cr_get_tile_shape(kt, vb) == s
                         assert lib.cr_tile_size(kt, vb) == shapes[s]
             finally:
-                assert lib.cr_set_tile_shape(kt, vb, before) == 0
+                for c, b in enumerate(before):
+                    assert lib.cr_set_tile_shape_for(kt, vb, c, b) == 0
     # the largest tiles do not fit 8-byte keys with 8-byte payloads and tags
     assert lib.cr_set_tile_shape(3, 8, 0) == 7
     assert lib.cr_get_tile_shape(9, 0) == -1
@@ -443,3 +444,26 @@ def test_check_sorted_argument_checks(lib):
     assert lib.cr_check_sorted(0, A, 10, O, WS, 8, None) == 1
     assert lib.cr_check_sorted(0, ctypes.c_void_p(0x100002), 10, O, WS, 16, None) == 3
     assert b"aligned" in lib.cr_last_error()
+
+
+def test_dist_co_rank_argument_checks(lib):
+    """The block-distributed co-rank calls refuse bad arguments before any
+    launch (fake device addresses are never dereferenced)."""
+    P = ctypes.c_void_p
+    S, R, X = P(0x100000), P(0x200000), P(0x300000)
+    assert lib.cr_dist_co_rank_init(-1, 5, R, 4, S, None) == 1
+    assert lib.cr_dist_co_rank_init(5, 5, None, 4, S, None) == 1
+    assert lib.cr_dist_co_rank_init(5, 5, P(0x200004), 4, S, None) == 3
+    assert lib.cr_dist_co_rank_init(5, 5, R, -1, S, None) == 1
+    assert lib.cr_dist_co_rank_init(5, 5, None, 0, None, None) == 0      # nothing to do
+    assert lib.cr_dist_co_rank_probes(5, 5, S, 4, None, X, None) == 1
+    assert lib.cr_dist_co_rank_probes(5, 5, S, 4, X, P(0x400002), None) == 3
+    assert lib.cr_dist_co_rank_answer(99, X, 0, 10, R, 4, S, None) == 1
+    assert lib.cr_dist_co_rank_answer(0, X, 10, 5, R, 4, S, None) == 1      # hi < lo
+    assert lib.cr_dist_co_rank_answer(0, None, 0, 10, R, 4, S, None) == 1
+    assert lib.cr_dist_co_rank_answer(3, P(0x300004), 0, 10, R, 4, S, None) == 3
+    assert lib.cr_dist_co_rank_answer(0, None, 7, 7, R, 0, S, None) == 0
+    assert lib.cr_dist_co_rank_step(99, 5, 5, R, X, S, 4, None) == 1
+    assert lib.cr_dist_co_rank_step(0, 5, 5, None, X, S, 4, None) == 1
+    assert lib.cr_dist_co_rank_result(S, 4, R, X, None, None) == 1
+    assert lib.cr_dist_co_rank_result(S, 4, R, X, P(0x500004), None) == 3

@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import paper_1303_4312_gb300 as cr
-from gpu_util import dev, host, key_type, same_bits, sorted_keys
+from gpu_util import dev, host, key_type, restore_shapes, same_bits, save_shapes, sorted_keys
 
 pytestmark = pytest.mark.gpu
 
@@ -169,7 +169,7 @@ def test_batched_segments_across_partition_blocks(dt):
     the oracle's."""
     rng = np.random.default_rng(109)
     kt = key_type(np.empty(0, dt))
-    t = cr.tile_size(kt, 4)                 # batched calls use the balanced shape
+    t = cr.tile_size(kt, 4, cls="batched")  # batched calls use their own class
     cases = [
         ([255 * t // 2 + 7, 3, 600 * t // 2], [255 * t // 2 - 5, 0, 600 * t // 2 + 11]),
         ([5 * t + 1], [7 * t - 3]),
@@ -378,7 +378,7 @@ def test_every_tile_shape():
         kt = key_type(np.empty(0, dt))
         vb = np.dtype(vdt).itemsize if vdt else 0
         code = _lib.KEY_TYPES[kt]
-        before = lib.cr_get_tile_shape(code, vb)
+        before = save_shapes(lib, code, vb)
         try:
             for shape in range(lib.cr_tile_shape_count()):
                 if lib.cr_set_tile_shape(code, vb, shape) != 0:
@@ -414,7 +414,7 @@ def test_every_tile_shape():
                 assert same_bits(host(Bk, dt), bk), shape
                 assert same_bits(host(Bkv, vdt), bv), shape
         finally:
-            assert lib.cr_set_tile_shape(code, vb, before) == 0
+            restore_shapes(lib, code, vb, before)
 
 
 def test_table_for_another_shape_is_refused():
@@ -424,7 +424,8 @@ def test_table_for_another_shape_is_refused():
     from paper_1303_4312_gb300 import _lib
     lib = _lib.load()
     code = _lib.KEY_TYPES["i32"]
-    before = lib.cr_get_tile_shape(code, 0)
+    saved = save_shapes(lib, code, 0)
+    before = saved[0]
     other = next(s for s in range(lib.cr_tile_shape_count())
                  if s != before and lib.cr_set_tile_shape(code, 0, s) == 0)
     try:
@@ -444,7 +445,7 @@ def test_table_for_another_shape_is_refused():
             cr.workspace_status(ws)
         assert e.value.name == "CR_EINTERNAL"
     finally:
-        _lib.check(lib.cr_set_tile_shape(code, 0, before))
+        restore_shapes(lib, code, 0, saved)
 
 
 def test_merge_many_overlapped_partitions():

@@ -58,7 +58,7 @@ def test_recorded_pass_forward_flags_backward(dt, vb):
     rng = np.random.default_rng(300 + vb)
     vdt = VAL_DTYPES[vb]
     kt = key_type(np.empty(0, dt))
-    tile = cr.tile_size(kt, vb)
+    tile = cr.tile_size(kt, vb, cls="pass")     # merge passes use the pass class
     for N, w in CASES:
         for spread in (None, 5):
             X = run_sorted_keys(rng, N, w, dt, spread)
@@ -86,12 +86,12 @@ def test_recorded_pass_every_tile_shape(shape):
     from paper_1303_4312_gb300 import _lib
     lib = _lib.load()
     code = _lib.KEY_TYPES["u64"]
-    before = [lib.cr_get_tile_shape_for(code, 4, c) for c in (0, 1)]
-    if lib.cr_set_tile_shape(code, 4, shape) != 0:
-        pytest.skip("shape does not fit uint64 keys with 4-byte payloads")
+    before = lib.cr_get_tile_shape_for(code, 4, 4)
+    if lib.cr_set_tile_shape_for(code, 4, 4, shape) != 0:
+        pytest.skip("shape does not fit recorded passes of uint64 keys with 4-byte payloads")
     try:
         rng = np.random.default_rng(310 + shape)
-        tile = cr.tile_size("u64", 4)
+        tile = cr.tile_size("u64", 4, cls="pass")
         for N, w in ((5 * tile + 77, 2 * tile - 3), (40000, 512), (3 * tile, tile)):
             X = run_sorted_keys(rng, N, w, np.uint64, 9)
             Xv = rng.standard_normal(N).astype(np.float32)
@@ -109,8 +109,7 @@ def test_recorded_pass_every_tile_shape(shape):
             want[src] = gY
             assert same_bits(host(gX, np.float32), want)
     finally:
-        for c in (0, 1):
-            lib.cr_set_tile_shape_for(code, 4, c, before[c])
+        lib.cr_set_tile_shape_for(code, 4, 4, before)
 
 
 def test_recorded_backward_refuses_other_table():

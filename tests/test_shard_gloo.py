@@ -1,7 +1,10 @@
-"""The sharded merge plan on two CPU ranks (gloo): every rank co-ranks the
+"""The sharded merge plan on CPU ranks (gloo): every rank co-ranks the
 ends of its equal output block, merges its windows, and the gathered blocks
-equal the whole stable merge.  Co-rank and local merge come from the CPU
-oracle here (test-only injection); on GPUs they are the library's kernels."""
+equal the whole stable merge.  On these CPU ranks the local merges come
+from the CPU oracle and the co-rank iterations of the block-distributed form
+from HostSearch below (test-only injections: the library's kernels need a
+GPU, where tests/test_gpu_dist.py runs them); the oracle checks every
+result."""
 import os
 import socket
 
@@ -12,6 +15,77 @@ import torch.distributed as dist
 import torch.multiprocessing as mp
 
 from paper_1303_4312_gb300 import shard
+
+
+def _as_key(v: int, key_type: str) -> int:
+    """A key read back from an int64 carrier (the stored key's bits, sign-
+    or zero-extended from its width), as a Python int whose integer order is
+    the key type's order: unsigned types are masked to their width; float
+    bits (IEEE-754 totalOrder) keep positives and flip the magnitude of
+    negatives; pairs of signed halves flip both sign bits; ':desc' negates."""
+    base, _, mod = key_type.partition(":")
+    bits = 32 if base in ("i32", "u32", "f32") else 64
+    if base.startswith("pair"):
+        v &= (1 << 64) - 1
+        if base == "pair_i32":
+            v ^= (1 << 63) | (1 << 31)
+        return -v if mod == "desc" else v
+    if base[0] == "u":
+        v &= (1 << bits) - 1
+    else:
+        v = ((v + (1 << (bits - 1))) & ((1 << bits) - 1)) - (1 << (bits - 1))
+        if base[0] == "f" and v < 0:
+            v ^= (1 << (bits - 1)) - 1
+    return -v if mod == "desc" else v
+
+
+class HostSearch:
+    """Test double of the library's block-distributed co-rank
+    (api.DistCoRank) on CPU tensors: the same state (rank k, co-ranks i, j,
+    their low bounds, finished flag), probes and Algorithm-1 iteration,
+    written out in Python; keys compared through _as_key."""
+
+    def __init__(self, m, n, ranks, key_type, device):
+        self.m, self.n, self.kt = m, n, key_type
+        self.st = [[k, min(k, m), k - min(k, m), max(0, k - n), max(0, k - m), False]
+                   for k in ranks]
+
+    def iterations(self):
+        return int(min(self.m, self.n)).bit_length() + 1
+
+    def probes(self):
+        pa, pb = [], []
+        for _, i, j, _, _, done in self.st:
+            c1 = not done and i > 0 and j < self.n
+            c2 = not done and j > 0 and i < self.m
+            pa += [i - 1 if c1 else -1, i if c2 else -1]
+            pb += [j - 1 if c2 else -1, j if c1 else -1]
+        return torch.tensor(pa, dtype=torch.int64), torch.tensor(pb, dtype=torch.int64)
+
+    def answer(self, blk, lo, idx):
+        out = torch.zeros(idx.numel(), dtype=torch.int64)
+        mine = (idx >= lo) & (idx < lo + blk.numel())
+        if bool(mine.any()):
+            out[mine] = blk[idx[mine] - lo].to(torch.int64)
+        return out
+
+    def step(self, va, vb):
+        va, vb, key = va.tolist(), vb.tolist(), lambda v: _as_key(v, self.kt)
+        for q, s in enumerate(self.st):
+            _, i, j, il, jl, done = s
+            if done:
+                continue
+            if i > 0 and j < self.n and key(vb[2 * q + 1]) < key(va[2 * q]):
+                d = (i - il + 1) // 2
+                s[4], s[1], s[2] = j, i - d, j + d
+            elif j > 0 and i < self.m and not key(vb[2 * q]) < key(va[2 * q + 1]):
+                d = (j - jl + 1) // 2
+                s[3], s[1], s[2] = i, i + d, j - d
+            else:
+                s[5] = True
+
+    def result(self):
+        return [(s[1], s[2]) for s in self.st], sum(not s[5] for s in self.st)
 
 
 def _free_port():
@@ -105,13 +179,13 @@ def _dist_worker(rank, world, port, cases, out_q):
             a_t = torch.from_numpy(a_blk.numpy().view(np.int64 if dt.itemsize == 8 else np.int32))
             b_t = torch.from_numpy(b_blk.numpy().view(np.int64 if dt.itemsize == 8 else np.int32))
             if Av is None:
-                C, p = shard.distributed_merge(a_t, b_t, kt, merge=merge)
+                C, p = shard.distributed_merge(a_t, b_t, kt, merge=merge, search=HostSearch)
                 Cv = None
             else:
                 av = torch.from_numpy(Av[a_cuts[rank]:a_cuts[rank + 1]].copy())
                 bv = torch.from_numpy(Bv[b_cuts[rank]:b_cuts[rank + 1]].copy())
                 C, Cv, p = shard.distributed_merge(a_t, b_t, kt, Av_blk=av, Bv_blk=bv,
-                                                   merge=merge_kv)
+                                                   merge=merge_kv, search=HostSearch)
             out_q.put((ci, rank, (p.k0, p.k1, p.i0, p.i1, p.j0, p.j1), C.numpy().tobytes(),
                        None if Cv is None else Cv.numpy().tobytes()))
     finally:
@@ -183,9 +257,9 @@ def test_distributed_merge_block_inputs(world):
 @pytest.mark.parametrize("kt", ["i32", "u32", "i64", "u64", "f32", "f64", "pair_u32", "pair_i32",
                                 "i32:desc", "f64:desc", "pair_i32:desc"])
 def test_remote_key_order_matches_oracle(kt):
-    """The distributed co-rank compares keys read back through int64
-    carriers (_as_key): their order must be the oracle's order for every key
-    type, including floats (totalOrder), pairs and descending orders."""
+    """The CPU test double compares keys read back through int64 carriers
+    (_as_key): their order must be the oracle's order for every key type,
+    including floats (totalOrder), pairs and descending orders."""
     import oracle
     rng = np.random.default_rng(113)
     base = kt.split(":")[0]
@@ -194,8 +268,8 @@ def test_remote_key_order_matches_oracle(kt):
     bits = rng.integers(0, np.iinfo(ut).max, 3000, dtype=ut, endpoint=True)
     bits[:30] = bits[30:60]
     st = {32: np.int32, 64: np.int64}[width]
-    carriers = bits.view(st).astype(np.int64)        # what the prober all-reduces
-    keys = [shard._as_key(int(v), kt) for v in carriers]
+    carriers = bits.view(st).astype(np.int64)        # what the ranks all-reduce
+    keys = [_as_key(int(v), kt) for v in carriers]
     ref = np.argsort(oracle.order_key(bits, kt if base[0] != "f" else kt), kind="stable")
     got = sorted(range(len(keys)), key=lambda i: keys[i])
     assert np.array_equal(got, ref)
@@ -217,7 +291,7 @@ def _dist_order_worker(rank, world, port, cases, out_q):
 
             a_t = torch.from_numpy(A[a_cuts[rank]:a_cuts[rank + 1]].copy().view(carrier))
             b_t = torch.from_numpy(B[b_cuts[rank]:b_cuts[rank + 1]].copy().view(carrier))
-            C, p = shard.distributed_merge(a_t, b_t, kt, merge=merge)
+            C, p = shard.distributed_merge(a_t, b_t, kt, merge=merge, search=HostSearch)
             out_q.put((ci, rank, (p.k0, p.k1, p.i0, p.i1, p.j0, p.j1), C.numpy().tobytes()))
     finally:
         dist.destroy_process_group()
