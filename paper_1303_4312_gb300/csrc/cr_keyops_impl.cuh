@@ -44,7 +44,7 @@ cudaError_t launch_shape(Kern kern, int threads, size_t smem, LaunchShape* cache
     return cudaSuccess;
 }
 
-template <class K, int VB, bool TAG, bool BWD, int S, bool REC, bool ORD>
+template <class K, int VB, bool TAG, bool BWD, int S, bool REC, int ORD>
 cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
     constexpr int KS = int(sizeof(K));
     if constexpr (!Stages<KS, VB, TAG, BWD, S>::FITS) {
@@ -73,7 +73,7 @@ cudaError_t launch_merge_shape(const MergeArgs& a, int64_t max_tiles, cudaStream
     }
 }
 
-template <class K, int VB, bool TAG, bool BWD, bool REC = false, bool ORD = false>
+template <class K, int VB, bool TAG, bool BWD, bool REC = false, int ORD = 0>
 cudaError_t launch_merge(int shape, const MergeArgs& a, int64_t max_tiles, cudaStream_t st) {
     static_assert(kNumShapes == 6, "dispatch below lists every shape");
     switch (shape) {
@@ -87,9 +87,10 @@ cudaError_t launch_merge(int shape, const MergeArgs& a, int64_t max_tiles, cudaS
     }
 }
 
-// The forward tile merges of one key type, for its own order (ORD false) or
-// another one (ORD true; a.order != 0).
-template <class K, bool ORD>
+// The forward tile merges of one key type, for its own order (ORD 0),
+// another one through the order map (ORD 1) or its own order descending
+// (ORD 2, the comparison reversed).
+template <class K, int ORD>
 cudaError_t merge_fwd_impl(int shape, int vb, bool tag, const MergeArgs& a, int64_t max_tiles,
                            cudaStream_t st) {
     switch (vb * 2 + (tag ? 1 : 0)) {
@@ -103,7 +104,7 @@ cudaError_t merge_fwd_impl(int shape, int vb, bool tag, const MergeArgs& a, int6
     }
 }
 
-template <class K, bool ORD>
+template <class K, int ORD>
 cudaError_t merge_fwd_rec_impl(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                cudaStream_t st) {
     if (vb == 4) return launch_merge<K, 4, false, false, true, ORD>(shape, a, max_tiles, st);
@@ -111,7 +112,7 @@ cudaError_t merge_fwd_rec_impl(int shape, int vb, const MergeArgs& a, int64_t ma
     return cudaErrorInvalidValue;
 }
 
-template <class K, bool ORD>
+template <class K, int ORD>
 cudaError_t merge_bwd_impl(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                            cudaStream_t st) {
     if (vb == 4) return launch_merge<K, 4, false, true, false, ORD>(shape, a, max_tiles, st);
@@ -122,40 +123,89 @@ cudaError_t merge_bwd_impl(int shape, int vb, const MergeArgs& a, int64_t max_ti
 template <class K>
 cudaError_t KeyOps<K>::merge_fwd(int shape, int vb, bool tag, const MergeArgs& a,
                                  int64_t max_tiles, cudaStream_t st) {
+    if (a.order == 1) return merge_fwd_desc(shape, vb, tag, a, max_tiles, st);
+    if constexpr (std::is_signed<K>::value)
+        if (a.order == 2 || a.order == 3) return merge_fwd_flt(shape, vb, tag, a, max_tiles, st);
     if (a.order != 0) return merge_fwd_ord(shape, vb, tag, a, max_tiles, st);
-    return merge_fwd_impl<K, false>(shape, vb, tag, a, max_tiles, st);
+    return merge_fwd_impl<K, 0>(shape, vb, tag, a, max_tiles, st);
 }
 
 template <class K>
 cudaError_t KeyOps<K>::merge_fwd_rec(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                      cudaStream_t st) {
+    if (a.order == 1) return merge_fwd_rec_desc(shape, vb, a, max_tiles, st);
+    if constexpr (std::is_signed<K>::value)
+        if (a.order == 2 || a.order == 3) return merge_fwd_rec_flt(shape, vb, a, max_tiles, st);
     if (a.order != 0) return merge_fwd_rec_ord(shape, vb, a, max_tiles, st);
-    return merge_fwd_rec_impl<K, false>(shape, vb, a, max_tiles, st);
+    return merge_fwd_rec_impl<K, 0>(shape, vb, a, max_tiles, st);
 }
 
 template <class K>
 cudaError_t KeyOps<K>::merge_bwd(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                  cudaStream_t st) {
+    if (a.order == 1) return merge_bwd_desc(shape, vb, a, max_tiles, st);
+    if constexpr (std::is_signed<K>::value)
+        if (a.order == 2 || a.order == 3) return merge_bwd_flt(shape, vb, a, max_tiles, st);
     if (a.order != 0) return merge_bwd_ord(shape, vb, a, max_tiles, st);
-    return merge_bwd_impl<K, false>(shape, vb, a, max_tiles, st);
+    return merge_bwd_impl<K, 0>(shape, vb, a, max_tiles, st);
 }
 
 template <class K>
 cudaError_t KeyOps<K>::merge_fwd_ord(int shape, int vb, bool tag, const MergeArgs& a,
                                      int64_t max_tiles, cudaStream_t st) {
-    return merge_fwd_impl<K, true>(shape, vb, tag, a, max_tiles, st);
+    return merge_fwd_impl<K, 1>(shape, vb, tag, a, max_tiles, st);
 }
 
 template <class K>
 cudaError_t KeyOps<K>::merge_fwd_rec_ord(int shape, int vb, const MergeArgs& a,
                                          int64_t max_tiles, cudaStream_t st) {
-    return merge_fwd_rec_impl<K, true>(shape, vb, a, max_tiles, st);
+    return merge_fwd_rec_impl<K, 1>(shape, vb, a, max_tiles, st);
 }
 
 template <class K>
 cudaError_t KeyOps<K>::merge_bwd_ord(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                      cudaStream_t st) {
-    return merge_bwd_impl<K, true>(shape, vb, a, max_tiles, st);
+    return merge_bwd_impl<K, 1>(shape, vb, a, max_tiles, st);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_fwd_desc(int shape, int vb, bool tag, const MergeArgs& a,
+                                      int64_t max_tiles, cudaStream_t st) {
+    return merge_fwd_impl<K, 2>(shape, vb, tag, a, max_tiles, st);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_fwd_rec_desc(int shape, int vb, const MergeArgs& a,
+                                          int64_t max_tiles, cudaStream_t st) {
+    return merge_fwd_rec_impl<K, 2>(shape, vb, a, max_tiles, st);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_bwd_desc(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                      cudaStream_t st) {
+    return merge_bwd_impl<K, 2>(shape, vb, a, max_tiles, st);
+}
+
+// Float keys (signed storage types only): order 2 ascending, 3 descending.
+template <class K>
+cudaError_t KeyOps<K>::merge_fwd_flt(int shape, int vb, bool tag, const MergeArgs& a,
+                                     int64_t max_tiles, cudaStream_t st) {
+    return a.order == 3 ? merge_fwd_impl<K, 4>(shape, vb, tag, a, max_tiles, st)
+                        : merge_fwd_impl<K, 3>(shape, vb, tag, a, max_tiles, st);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_fwd_rec_flt(int shape, int vb, const MergeArgs& a,
+                                         int64_t max_tiles, cudaStream_t st) {
+    return a.order == 3 ? merge_fwd_rec_impl<K, 4>(shape, vb, a, max_tiles, st)
+                        : merge_fwd_rec_impl<K, 3>(shape, vb, a, max_tiles, st);
+}
+
+template <class K>
+cudaError_t KeyOps<K>::merge_bwd_flt(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                     cudaStream_t st) {
+    return a.order == 3 ? merge_bwd_impl<K, 4>(shape, vb, a, max_tiles, st)
+                        : merge_bwd_impl<K, 3>(shape, vb, a, max_tiles, st);
 }
 
 static inline unsigned blocks_for(int64_t n, int threads) {
@@ -251,6 +301,20 @@ cudaError_t KeyOps<K>::co_rank_one(const void* A, int64_t m, const void* B, int6
     template cudaError_t cr::KeyOps<K>::merge_fwd_rec_ord(int, int, const cr::MergeArgs&,      \
                                                           int64_t, cudaStream_t);              \
     template cudaError_t cr::KeyOps<K>::merge_bwd_ord(int, int, const cr::MergeArgs&, int64_t, \
+                                                      cudaStream_t);
+#define CR_INSTANTIATE_DESC(K)                                                                 \
+    template cudaError_t cr::KeyOps<K>::merge_fwd_desc(int, int, bool, const cr::MergeArgs&,   \
+                                                       int64_t, cudaStream_t);                 \
+    template cudaError_t cr::KeyOps<K>::merge_fwd_rec_desc(int, int, const cr::MergeArgs&,     \
+                                                           int64_t, cudaStream_t);             \
+    template cudaError_t cr::KeyOps<K>::merge_bwd_desc(int, int, const cr::MergeArgs&, int64_t,\
+                                                       cudaStream_t);
+#define CR_INSTANTIATE_FLOAT(K)                                                                \
+    template cudaError_t cr::KeyOps<K>::merge_fwd_flt(int, int, bool, const cr::MergeArgs&,    \
+                                                      int64_t, cudaStream_t);                  \
+    template cudaError_t cr::KeyOps<K>::merge_fwd_rec_flt(int, int, const cr::MergeArgs&,      \
+                                                          int64_t, cudaStream_t);              \
+    template cudaError_t cr::KeyOps<K>::merge_bwd_flt(int, int, const cr::MergeArgs&, int64_t, \
                                                       cudaStream_t);
 #define CR_INSTANTIATE_RECORD(K)                                                               \
     template cudaError_t cr::KeyOps<K>::merge_fwd_rec(int, int, const cr::MergeArgs&, int64_t, \

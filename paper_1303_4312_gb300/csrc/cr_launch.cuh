@@ -148,6 +148,23 @@ struct KeyOps {
                                          int64_t max_tiles, cudaStream_t st);
     static cudaError_t merge_bwd_ord(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
                                      cudaStream_t st);
+    // The same three for the descending order of the storage type
+    // (a.order == 1): the comparisons reversed, keys neither mapped nor
+    // mapped back.
+    static cudaError_t merge_fwd_desc(int shape, int vb, bool tag, const MergeArgs& a,
+                                      int64_t max_tiles, cudaStream_t st);
+    static cudaError_t merge_fwd_rec_desc(int shape, int vb, const MergeArgs& a,
+                                          int64_t max_tiles, cudaStream_t st);
+    static cudaError_t merge_bwd_desc(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                      cudaStream_t st);
+    // And for IEEE-754 totalOrder floats stored in a signed K (a.order 2
+    // ascending, 3 descending), with the order map fixed at compile time.
+    static cudaError_t merge_fwd_flt(int shape, int vb, bool tag, const MergeArgs& a,
+                                     int64_t max_tiles, cudaStream_t st);
+    static cudaError_t merge_fwd_rec_flt(int shape, int vb, const MergeArgs& a,
+                                         int64_t max_tiles, cudaStream_t st);
+    static cudaError_t merge_bwd_flt(int shape, int vb, const MergeArgs& a, int64_t max_tiles,
+                                     cudaStream_t st);
     // order: key order of the call (order_key in cr_device.cuh).
     static cudaError_t partition_single(const void* A, int64_t m, const void* B, int64_t n,
                                         int64_t tile, int64_t ntiles, void* ws, int order,

@@ -192,12 +192,22 @@ struct KeyIdentity {
     __device__ __forceinline__ K operator()(K x) const { return x; }
 };
 
+// Key comparison of the merge: `<` of the storage type, or reversed (for a
+// descending order, whose order map is the complement: ~x < ~y exactly when
+// y < x, so comparing the stored keys with the operands swapped needs no
+// per-key work).
+template <bool REV>
+struct KeyLess {
+    template <class K>
+    __device__ __forceinline__ bool operator()(K x, K y) const { return REV ? (y < x) : (x < y); }
+};
+
 // `key` maps every key read before it is compared (the call's key order;
-// the identity for the storage type's own order).
-template <int LOG, int ILP, class K, class KeyMap = KeyIdentity>
+// the identity for the storage type's own order); `less` compares mapped keys.
+template <int LOG, int ILP, class K, class KeyMap = KeyIdentity, class Less = KeyLess<false>>
 __device__ __forceinline__ void split_in_tile(const K* sA, int alen, const K* sB, int blen,
                                               const int (&d)[ILP], int (&pos)[ILP],
-                                              KeyMap key = KeyMap()) {
+                                              KeyMap key = KeyMap(), Less less = Less()) {
     int hi[ILP];
 #pragma unroll
     for (int c = 0; c < ILP; ++c) {
@@ -209,7 +219,7 @@ __device__ __forceinline__ void split_in_tile(const K* sA, int alen, const K* sB
 #pragma unroll
         for (int c = 0; c < ILP; ++c) {
             const int np = pos[c] + step;
-            if (np <= hi[c] && !(key(sB[d[c] - np]) < key(sA[np - 1]))) pos[c] = np;
+            if (np <= hi[c] && !less(key(sB[d[c] - np]), key(sA[np - 1]))) pos[c] = np;
         }
     }
 }
@@ -229,12 +239,16 @@ template <int NT> constexpr int merge_block_threads() { return NT + 64; }
 // p.flags + t * WPT for tile t (the backward then routes gradients from
 // these bits and the tile table without reading keys).
 //
-// ORD: keys in another order than their storage type's (p.order, order_key):
-// every key read from shared memory is mapped before it is compared and the
-// output keys are mapped back.  With ORD false the code is that of the
-// storage type's own order.
+// ORD: the key order.  0: the storage type's own (plain `<`).  1: another
+// order (p.order, order_key): every key read from shared memory is mapped
+// before it is compared and the output keys are mapped back.  2: the
+// descending order of the storage type, by comparing with the operands
+// swapped (keys are neither mapped nor mapped back).  3 and 4: IEEE-754
+// totalOrder of floats stored in the signed integer of their width, with
+// the map's masks known at compile time, ascending (3) or descending (4,
+// the comparison reversed).
 template <class K, int VB, bool TAG, int NT, int IPT, int ILP, int NS, int MINB, bool BWD,
-          bool REC, bool ORD>
+          bool REC, int ORD>
 __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeArgs p) {
     using L = Layout<K, VB, TAG, NT, IPT, ILP, NS, BWD, REC>;
     using V = typename VBits<VB>::T;
@@ -431,8 +445,10 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
     }
 
     // ---------------------------------------------------------------- consumers
-    const OrderMap<K> om(ORD ? p.order : 0);
-    const auto km = [om](K x) { return ORD ? om(x) : x; };
+    constexpr bool MAPPED = ORD == 1 || ORD >= 3;
+    const OrderMap<K> om(ORD == 1 ? p.order : (ORD >= 3 ? 2 : 0));
+    const auto km = [om](K x) { return MAPPED ? om(x) : x; };
+    const KeyLess<ORD == 2 || ORD == 4> lt;
     // Thread tid merges ILP chains; chain c starts at diagonal (c*NT + tid)*IPT
     // and the chains run interleaved, so each thread has ILP independent
     // dependency chains of shared-memory loads in flight.
@@ -460,7 +476,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             d[c] = min((c * NT + tid) * IPT, len);
             cnt[c] = min(IPT, len - d[c]);
         }
-        split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d, j, km);
+        split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d, j, km, lt);
 #pragma unroll
         for (int c = 0; c < ILP; ++c) {
             k[c] = d[c] - j[c];
@@ -491,8 +507,8 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             // run out within the chain's IPT steps (only near the windows' ends).
             auto step = [&](int c, int q, auto guard) {
                 const bool takeA = decltype(guard)::value
-                                       ? (k[c] >= blen) || (j[c] < alen && !(b[c] < a[c]))
-                                       : !(b[c] < a[c]);
+                                       ? (k[c] >= blen) || (j[c] < alen && !lt(b[c], a[c]))
+                                       : !lt(b[c], a[c]);
                 okey[c][q] = takeA ? a[c] : b[c];
                 if constexpr (VB != 0) oval[c][q] = sv[takeA ? avo + j[c] : bvo + k[c]];
                 if constexpr (TAG)
@@ -523,7 +539,7 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
 #pragma unroll
                 for (int q = 0; q < IPT; ++q)
                     if (q < cnt[c])
-                        sk[ph + d[c] + q] = ORD ? om.inverse(okey[c][q]) : okey[c][q];
+                        sk[ph + d[c] + q] = MAPPED ? om.inverse(okey[c][q]) : okey[c][q];
             if constexpr (VB != 0) {
                 V* ov = stage_v(s);
                 const int phv = int((in.gc + p.sh_cv) & (EV - 1));
@@ -563,8 +579,8 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                 ((pha + alen + EV - 1) / EV) * EV + int((in.gb + p.sh_cv2) & (EV - 1));
             auto step = [&](int c, int q, auto guard) {
                 const bool takeA = decltype(guard)::value
-                                       ? (k[c] >= blen) || (j[c] < alen && !(b[c] < a[c]))
-                                       : !(b[c] < a[c]);
+                                       ? (k[c] >= blen) || (j[c] < alen && !lt(b[c], a[c]))
+                                       : !lt(b[c], a[c]);
                 gval[c][q] = sg[d[c] + q];
                 dst[c][q] = takeA ? pha + j[c] : boff + k[c];
                 j[c] += takeA ? 1 : 0;
