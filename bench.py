@@ -602,6 +602,23 @@ def row_batched(lib, dev, stream, K, W, peak, pairs=8192):
         mark("bwd")
     t = _timed(stream, K, W, body, ["fwd", "bwd"])
     api.workspace_status(ws)
+    del Ck, Cv, gA, gB, ws
+    # the same two calls captured into CUDA graphs (BatchedMergeGraph) and
+    # replayed on its static buffers, filled once with these inputs
+    g = api.BatchedMergeGraph(ao, bo, torch.int32, torch.float32, dev)
+    for dst, src in zip(g.inputs(), (A, Av, B, Bv, gC)):
+        dst.copy_(src)
+    del A, Av, B, Bv, gC
+
+    def gbody(mark):
+        mark()
+        g.forward()
+        mark("fwd")
+        g.backward()
+        mark("bwd")
+    tg = _timed(stream, K, W, gbody, ["fwd", "bwd"])
+    g.check()
+    del g
     nt, ipt, ilp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     shape = lib.cr_get_tile_shape_for(0, 4, 0)
     lib.cr_tile_shape_info(shape, ctypes.byref(nt), ctypes.byref(ipt), ctypes.byref(ilp))
@@ -609,7 +626,10 @@ def row_batched(lib, dev, stream, K, W, peak, pairs=8192):
             "tile_shape": f"{nt.value}x{ipt.value}x{ilp.value}",
             "fwd": _dir_row(N, t["fwd"], 16 * N, peak, launches=3),
             "bwd": _dir_row(N, t["bwd"], 12 * N, peak, launches=3),
-            "note": "each direction is one call: segment scan + partition + tile merge"}
+            "fwd_graph": _dir_row(N, tg["fwd"], 16 * N, peak, launches=3),
+            "bwd_graph": _dir_row(N, tg["bwd"], 12 * N, peak, launches=3),
+            "note": "each direction is one call (segment scan + partition + tile merge); "
+                    "*_graph: the same call captured in a CUDA graph and replayed"}
 
 
 def row_sort(lib, dev, stream, K, W, peak, shift):

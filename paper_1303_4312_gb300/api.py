@@ -513,7 +513,8 @@ def batched_merge_kv(a_off, b_off, Ak, Av, Bk, Bv, key_type: str | None = None, 
     return Ck, Cv
 
 
-def batched_merge_kv_backward(a_off, b_off, Ak, Bk, gC, key_type: str | None = None, ws=None):
+def batched_merge_kv_backward(a_off, b_off, Ak, Bk, gC, key_type: str | None = None, ws=None,
+                              out=None):
     lib = _lib.load()
     gC = gC.contiguous()
     dev = _dev(Ak, Bk, gC)
@@ -522,8 +523,11 @@ def batched_merge_kv_backward(a_off, b_off, Ak, Bk, gC, key_type: str | None = N
     nseg = ao.numel() - 1
     vb = gC.element_size()
     at, bt = Ak.numel(), Bk.numel()
-    gA = torch.empty(at, dtype=gC.dtype, device=dev)
-    gB = torch.empty(bt, dtype=gC.dtype, device=dev)
+    if out is None:
+        gA = torch.empty(at, dtype=gC.dtype, device=dev)
+        gB = torch.empty(bt, dtype=gC.dtype, device=dev)
+    else:
+        gA, gB = out
     need = _size(lib.cr_batched_workspace_size, kt, vb, nseg, at, bt)
     if ws is None:
         ws = _ws(need, dev)
@@ -531,6 +535,86 @@ def batched_merge_kv_backward(a_off, b_off, Ak, Bk, gC, key_type: str | None = N
                                                 _ptr(Bk), bt, _ptr(gC), _ptr(gA), _ptr(gB),
                                                 _ptr(ws), ws.numel(), _stream(dev)))
     return gA, gB
+
+
+class BatchedMergeGraph:
+    """Batched merges of a fixed segment table, forward and payload
+    backward, each captured once into a CUDA graph and then replayed: one
+    replay runs the segment scan, the batched partition and the persistent
+    tile merge (cr_batched_merge_kv, or its backward) on static buffers.
+
+    a_off, b_off: the segment tables (nseg + 1 int64 entries each, host or
+    device); key_dtype / val_dtype: torch dtypes of keys and payloads.
+    forward(Ak, Av, Bk, Bv) copies the inputs into the static buffers (unless
+    they are those buffers: `inputs()`), replays and returns (Ck, Cv);
+    backward(gC) does the same for the gradient and returns (gA, gB).  The
+    returned tensors are the static outputs, overwritten by the next replay.
+    """
+
+    def __init__(self, a_off, b_off, key_dtype, val_dtype, device="cuda",
+                 key_type: str | None = None):
+        self.dev = torch.device(device)
+        self.ao = _offsets(a_off, self.dev)
+        self.bo = _offsets(b_off, self.dev)
+        at, bt = int(self.ao[-1].item()), int(self.bo[-1].item())
+        self.Ak = torch.zeros(at, dtype=key_dtype, device=self.dev)
+        self.Bk = torch.zeros(bt, dtype=key_dtype, device=self.dev)
+        self.Av = torch.zeros(at, dtype=val_dtype, device=self.dev)
+        self.Bv = torch.zeros(bt, dtype=val_dtype, device=self.dev)
+        self.Ck = torch.empty(at + bt, dtype=key_dtype, device=self.dev)
+        self.Cv = torch.empty(at + bt, dtype=val_dtype, device=self.dev)
+        self.gC = torch.zeros(at + bt, dtype=val_dtype, device=self.dev)
+        self.gA = torch.empty(at, dtype=val_dtype, device=self.dev)
+        self.gB = torch.empty(bt, dtype=val_dtype, device=self.dev)
+        self.key_type = key_type
+        lib = _lib.load()
+        kt = _key_code(self.Ak, key_type)
+        vb = self.Av.element_size()
+        need = _size(lib.cr_batched_workspace_size, kt, vb, self.ao.numel() - 1, at, bt)
+        self.ws = _ws(need, self.dev)
+        self._gf = self._capture(self._fwd)
+        self._gb = self._capture(self._bwd)
+
+    def _fwd(self):
+        batched_merge_kv(self.ao, self.bo, self.Ak, self.Av, self.Bk, self.Bv,
+                         key_type=self.key_type, ws=self.ws, out=(self.Ck, self.Cv))
+
+    def _bwd(self):
+        batched_merge_kv_backward(self.ao, self.bo, self.Ak, self.Bk, self.gC,
+                                  key_type=self.key_type, ws=self.ws, out=(self.gA, self.gB))
+
+    def _capture(self, body):
+        # one eager run first (kernel attributes are set on first use), then capture
+        s = torch.cuda.Stream(self.dev)
+        s.wait_stream(torch.cuda.current_stream(self.dev))
+        with torch.cuda.stream(s):
+            body()
+        torch.cuda.current_stream(self.dev).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            body()
+        return g
+
+    def inputs(self):
+        """The static input buffers (Ak, Av, Bk, Bv) and gradient buffer gC."""
+        return self.Ak, self.Av, self.Bk, self.Bv, self.gC
+
+    def forward(self, Ak=None, Av=None, Bk=None, Bv=None):
+        for dst, src in ((self.Ak, Ak), (self.Av, Av), (self.Bk, Bk), (self.Bv, Bv)):
+            if src is not None and src is not dst:
+                dst.copy_(src)
+        self._gf.replay()
+        return self.Ck, self.Cv
+
+    def backward(self, gC=None):
+        if gC is not None and gC is not self.gC:
+            self.gC.copy_(gC)
+        self._gb.replay()
+        return self.gA, self.gB
+
+    def check(self):
+        """Device status of the last replay (raises CorankError on a device error)."""
+        workspace_status(self.ws)
 
 
 # ---------------------------------------------------------------------------

@@ -108,6 +108,37 @@ def test_batched_full_forward_backward():
     assert same_bits(host(gB, np.float32), gb)
 
 
+def test_batched_graph_capture_replays():
+    """The batched forward and backward captured into CUDA graphs
+    (BatchedMergeGraph) and replayed on two sets of inputs for one segment
+    table (log-uniform sizes as in the batched workload, with empty
+    segments), against the oracle bit for bit."""
+    rng = np.random.default_rng(57)
+    ms, ns = W.log_uniform_sizes(58, 300, max_log2=14)
+    ms[5] = 0
+    ns[7] = 0
+    a_off, b_off = W.offsets(ms), W.offsets(ns)
+    g = cr.BatchedMergeGraph(a_off, b_off, torch.int32, torch.float32, "cuda")
+    for rep in range(2):
+        A = np.concatenate([np.sort(rng.integers(0, 1 << 24, m)) for m in ms]).astype(np.int32)
+        B = np.concatenate([np.sort(rng.integers(0, 1 << 24, n)) for n in ns]).astype(np.int32)
+        Av = rng.standard_normal(len(A)).astype(np.float32)
+        Bv = rng.standard_normal(len(B)).astype(np.float32)
+        gC = rng.standard_normal(len(A) + len(B)).astype(np.float32)
+        Ck, Cv = g.forward(torch.from_numpy(A).cuda(), torch.from_numpy(Av).cuda(),
+                           torch.from_numpy(B).cuda(), torch.from_numpy(Bv).cuda())
+        torch.cuda.synchronize()
+        wk, wv = oracle.batched_merge_kv(a_off, b_off, A, Av, B, Bv)
+        assert np.array_equal(host(Ck, np.int32), wk), rep
+        assert same_bits(host(Cv, np.float32), wv), rep
+        gA, gB = g.backward(torch.from_numpy(gC).cuda())
+        torch.cuda.synchronize()
+        g.check()
+        ga, gb = oracle.batched_merge_grad(a_off, b_off, A, B, gC)
+        assert same_bits(host(gA, np.float32), ga), rep
+        assert same_bits(host(gB, np.float32), gb), rep
+
+
 def test_merge_sort_full_graph_forward_backward():
     X, Xv = W.t_sort_u64_f32()
     Xv.requires_grad_(True)
