@@ -56,6 +56,8 @@ struct BlockSlots {
     // slot of element R included: a merge step may read one past its pair
     static constexpr int KEYS = kBlockR + (kBlockR >> SHIFT) + 1;
     static constexpr int IDX = kBlockR + ((kBlockR >> 6) << 1) + 1;
+    static_assert((1 << SHIFT) % kBlockIPT == 0 && 64 % kBlockIPT == 0,
+                  "the IPT outputs of a thread never straddle a gap");
 };
 
 template <class K, int VB>
@@ -167,13 +169,16 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
             int k = d - j;
             K a = ik[S::key(ps + j)];     // at most element len <= R: the slack slot
             K b = ik[S::key(bs + k)];
+            // a thread's IPT outputs are consecutive slots (no gap inside them)
+            K* const okt = ok + S::key(d0);
+            uint16_t* const oit = oi + S::idx(d0);
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 if (q < cnt) {
                     const bool takeA = (k >= blen) || (j < alen && !(b < a));
                     const int src = takeA ? ps + j : bs + k;
-                    ok[S::key(d0 + q)] = takeA ? a : b;
-                    oi[S::idx(d0 + q)] = ii[S::idx(src)];
+                    okt[q] = takeA ? a : b;
+                    oit[q] = ii[S::idx(src)];
                     j += takeA ? 1 : 0;
                     k += takeA ? 0 : 1;
                     const K nx = ik[S::key(takeA ? ps + j : bs + k)];   // unused past a run

@@ -19,7 +19,9 @@
 //      chain serially into registers (ties take A; the chains interleave
 //      so their shared-memory latencies overlap), and after a barrier
 //      writes them back into the same stage, which then serves as the output
-//      staging buffer, and signals the stage's "staged" mbarrier.
+//      staging buffer, and signals the stage's "staged" mbarrier.  In the
+//      forward with payloads the barrier is an mbarrier and a warp finds its
+//      splits in the next tile's stage between arriving and waiting on it.
 //  storer (one warp): waits for a staged tile, issues the bulk store of its
 //      16-byte aligned interior, stores the ragged ends with plain stores,
 //      and hands the stage back to the producer as soon as the bulk store has
@@ -72,12 +74,12 @@ struct Layout {
     static constexpr size_t STAGE_G = align_up_sz(size_t(SG) * VS, 128);
     static constexpr size_t STAGE_F = REC ? align_up_sz(size_t(WPT) * 4, 128) : 0;
     static constexpr size_t STAGE = STAGE_K + STAGE_V + STAGE_T + STAGE_G + STAGE_F;
-    static constexpr size_t BAR_OFF = 0;              // full, staged, empty [NS]; flags
+    static constexpr size_t BAR_OFF = 0;              // full, staged, empty, consumed [NS]; flags
     static constexpr size_t INFO_OFF = 256;
     static constexpr size_t STAGE_OFF = align_up_sz(INFO_OFF + NS * sizeof(StageInfo), 128);
     static constexpr size_t TOTAL = STAGE_OFF + NS * STAGE + 128;  // + slack for one-past reads
     static_assert(NS >= 2, "at least one stage can load while another is merged");
-    static_assert(3 * NS * 8 + 16 <= INFO_OFF, "barrier area");
+    static_assert(4 * NS * 8 + 20 <= INFO_OFF, "barrier area");
     static_assert(TILE % EK == 0 && TILE % EV == 0 && TILE % 4 == 0, "tile alignment");
     // a tile's flag words form whole 16-byte chunks (bulk store at t * WPT)
     static_assert(!REC || (!BWD && TILE % 32 == 0 && (WPT * 4) % 16 == 0 && WPT <= NT),
@@ -260,12 +262,15 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
     uint64_t* staged = full + NS;
     uint64_t* empty = staged + NS;
-    // s_abort[it & 1]: written only by consumer threads of iteration it before
-    // that iteration's barrier and read by all of them after it (the other
-    // slot belongs to the neighbouring iterations), so every consumer takes
-    // the same exit decision.
-    volatile int32_t* s_abort = reinterpret_cast<volatile int32_t*>(empty + NS);
-    volatile int32_t* s_issued = s_abort + 2;
+    uint64_t* consumed = empty + NS;   // PIPE: one arrival per consumer warp
+    // s_abort[it & 1] (s_abort[it & 3] with PIPE): written only by consumer
+    // threads before the barrier that separates iteration it's reads from
+    // its writes (with PIPE, also while preparing iteration it in iteration
+    // it - 1) and read by all of them after it (the other slots belong to
+    // the neighbouring iterations), so every consumer takes the same exit
+    // decision.
+    volatile int32_t* s_abort = reinterpret_cast<volatile int32_t*>(consumed + NS);
+    volatile int32_t* s_issued = s_abort + 4;
     StageInfo* info = reinterpret_cast<StageInfo*>(smem + L::INFO_OFF);
 
     auto base = [&](int s) { return smem + L::STAGE_OFF + size_t(s) * L::STAGE; };
@@ -291,9 +296,9 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
             mbar_init(&full[s], 1);
             mbar_init(&staged[s], NT);
             mbar_init(&empty[s], 1);
+            mbar_init(&consumed[s], NT / 32);
         }
-        s_abort[0] = 0;
-        s_abort[1] = 0;
+        for (int q = 0; q < 4; ++q) s_abort[q] = 0;
         *s_issued = 0;
         fence_barrier_init();
     }
@@ -449,74 +454,97 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
     const OrderMap<K> om(ORD == 1 ? p.order : (ORD >= 3 ? 2 : 0));
     const auto km = [om](K x) { return MAPPED ? om(x) : x; };
     const KeyLess<ORD == 2 || ORD == 4> lt;
+    constexpr bool PIPE = VB != 0 && !BWD && !REC;
     // Thread tid merges ILP chains; chain c starts at diagonal (c*NT + tid)*IPT
     // and the chains run interleaved, so each thread has ILP independent
     // dependency chains of shared-memory loads in flight.
     int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const int s = it % NS;
-        const bool ready = mbar_wait(&full[s], (it / NS) & 1);
-        if (!ready) {
-            set_status(&hdr->status, kDevTimeout);
-            s_abort[it & 1] = 1;
-        }
-        const StageInfo in = info[s];
-        const int alen = ready ? in.alen : 0;
-        const int blen = ready ? in.blen : 0;
-        const int len = alen + blen;
-        K* sk = stage_k(s);
-        const int ao = in.ak, bo = in.bk;   // A[0] and B[0] of the tile in the stage
-        const K* sA = sk + ao;
-        const K* sB = sk + bo;
-        int d[ILP], cnt[ILP], j[ILP], k[ILP];
-        K a[ILP], b[ILP];
-        bool fast = true;
-#pragma unroll
-        for (int c = 0; c < ILP; ++c) {
-            d[c] = min((c * NT + tid) * IPT, len);
-            cnt[c] = min(IPT, len - d[c]);
-        }
-        split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d, j, km, lt);
-#pragma unroll
-        for (int c = 0; c < ILP; ++c) {
-            k[c] = d[c] - j[c];
-            a[c] = K(0);
-            b[c] = K(0);
-            if (cnt[c] > 0) {
-                a[c] = km(sA[j[c]]);   // may be one past A's window: never taken then
-                b[c] = km(sB[k[c]]);
+    if constexpr (PIPE) {
+        // Forward with payloads, whose merge steps also gather a payload
+        // from the stage: the consumers run one tile ahead.  After merging
+        // tile it into registers a warp arrives on consumed[s] (its lanes
+        // have read their inputs), waits for the next tile's stage and finds
+        // its splits there, and only then waits for every warp's arrival
+        // before its outputs overwrite stage s, so warps that finish a merge
+        // early search the next tile instead of idling at a barrier.  One
+        // lane per warp arrives and polls; the others wait at __syncwarp.
+        struct Split {
+            int alen, blen;
+            int j[ILP];
+            K a[ILP], b[ILP];
+            bool fast;
+        };
+        bool timed_out = false;
+        // Wait for the stage of iteration q and find this thread's splits in it.
+        auto prepare = [&](int q, Split& P) {
+            const int s = q % NS;
+            const bool ready = !timed_out && mbar_wait(&full[s], (q / NS) & 1);
+            if (!ready) {
+                if (!timed_out) set_status(&hdr->status, kDevTimeout);
+                timed_out = true;
+                s_abort[q & 3] = 1;
             }
-            fast = fast && cnt[c] == IPT && j[c] + IPT <= alen && k[c] + IPT <= blen;
-        }
-        // One loop version per warp: a warp whose threads disagree would run both.
-        fast = __all_sync(0xffffffffu, fast);
-        if constexpr (!BWD) {
-            K okey[ILP][IPT];
-            V oval[ILP][VB ? IPT : 1];
-            uint32_t otag[ILP][TAG ? IPT : 1];
-            uint32_t obit[ILP];   // REC: bit q set when output q of chain c came from B
+            P.alen = ready ? info[s].alen : 0;
+            P.blen = ready ? info[s].blen : 0;
+            const int len = P.alen + P.blen;
+            const K* sk = stage_k(s);
+            const K* sA = sk + info[s].ak;
+            const K* sB = sk + info[s].bk;
+            int d[ILP];
+#pragma unroll
+            for (int c = 0; c < ILP; ++c) d[c] = min((c * NT + tid) * IPT, len);
+            split_in_tile<Log2Ceil<TILE + 1>::v>(sA, P.alen, sB, P.blen, d, P.j, km, lt);
+            P.fast = true;
+#pragma unroll
+            for (int c = 0; c < ILP; ++c) {
+                const int k = d[c] - P.j[c];
+                const int cnt = min(IPT, len - d[c]);
+                P.a[c] = K(0);
+                P.b[c] = K(0);
+                if (cnt > 0) {
+                    P.a[c] = km(sA[P.j[c]]);   // may be one past A's window: never taken then
+                    P.b[c] = km(sB[k]);
+                }
+                P.fast = P.fast && cnt == IPT && P.j[c] + IPT <= P.alen && k + IPT <= P.blen;
+            }
+            P.fast = __all_sync(0xffffffffu, P.fast);
+        };
+        const int lane = tid & 31;
+        Split P;
+        if (blockIdx.x < ntiles) prepare(0, P);
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int s = it % NS;
+            const StageInfo in = info[s];
+            const int alen = P.alen, blen = P.blen, len = alen + blen;
+            K* sk = stage_k(s);
             const V* sv = stage_v(s);
-            const int avo = in.av, bvo = in.bv;
-            if constexpr (REC) {
+            const int ao = in.ak, bo = in.bk, avo = in.av, bvo = in.bv;
+            int d[ILP], cnt[ILP], j[ILP], k[ILP];
+            K a[ILP], b[ILP];
+            const bool fast = P.fast;
 #pragma unroll
-                for (int c = 0; c < ILP; ++c) obit[c] = 0;
-                // cleared before the barrier below, set after it
-                if (tid < L::WPT) stage_f(s)[tid] = 0;
+            for (int c = 0; c < ILP; ++c) {
+                d[c] = min((c * NT + tid) * IPT, len);
+                cnt[c] = min(IPT, len - d[c]);
+                j[c] = P.j[c];
+                k[c] = d[c] - j[c];
+                a[c] = P.a[c];
+                b[c] = P.b[c];
             }
-            // One merge step of chain c (ties take A).  GUARD: some side may
-            // run out within the chain's IPT steps (only near the windows' ends).
+            K okey[ILP][IPT];
+            V oval[ILP][IPT];
+            uint32_t otag[ILP][TAG ? IPT : 1];
             auto step = [&](int c, int q, auto guard) {
                 const bool takeA = decltype(guard)::value
                                        ? (k[c] >= blen) || (j[c] < alen && !lt(b[c], a[c]))
                                        : !lt(b[c], a[c]);
                 okey[c][q] = takeA ? a[c] : b[c];
-                if constexpr (VB != 0) oval[c][q] = sv[takeA ? avo + j[c] : bvo + k[c]];
+                oval[c][q] = sv[takeA ? avo + j[c] : bvo + k[c]];
                 if constexpr (TAG)
                     otag[c][q] = takeA ? uint32_t(in.ga + j[c]) : uint32_t(p.tag_b + in.gb + k[c]);
-                if constexpr (REC) obit[c] |= (takeA ? 0u : 1u) << q;
                 j[c] += takeA ? 1 : 0;
                 k[c] += takeA ? 0 : 1;
-                const K nx = km(sk[takeA ? ao + j[c] : bo + k[c]]);   // one load from either window
+                const K nx = km(sk[takeA ? ao + j[c] : bo + k[c]]);
                 a[c] = takeA ? nx : a[c];
                 b[c] = takeA ? b[c] : nx;
             };
@@ -532,23 +560,28 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                     for (int c = 0; c < ILP; ++c)
                         if (q < cnt[c]) step(c, q, BoolC<true>{});
             }
-            named_sync(1, NT);   // every input of stage s has been read
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&consumed[s]);
+            if (t + gridDim.x < ntiles) prepare(it + 1, P);
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(&consumed[s], (it / NS) & 1);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();   // every input of stage s has been read
+            if (!ok) {
+                if (lane == 0) set_status(&hdr->status, kDevTimeout);
+                s_abort[it & 3] = 1;
+            }
             const int ph = int((in.gc + p.sh_ck) & (EK - 1));
+            const int phv = int((in.gc + p.sh_cv) & (EV - 1));
+            V* ov = stage_v(s);
 #pragma unroll
             for (int c = 0; c < ILP; ++c)
 #pragma unroll
                 for (int q = 0; q < IPT; ++q)
-                    if (q < cnt[c])
+                    if (q < cnt[c]) {
                         sk[ph + d[c] + q] = MAPPED ? om.inverse(okey[c][q]) : okey[c][q];
-            if constexpr (VB != 0) {
-                V* ov = stage_v(s);
-                const int phv = int((in.gc + p.sh_cv) & (EV - 1));
-#pragma unroll
-                for (int c = 0; c < ILP; ++c)
-#pragma unroll
-                    for (int q = 0; q < IPT; ++q)
-                        if (q < cnt[c]) ov[phv + d[c] + q] = oval[c][q];
-            }
+                        ov[phv + d[c] + q] = oval[c][q];
+                    }
             if constexpr (TAG) {
                 uint32_t* ot = stage_t(s);
                 const int pht = int((in.gc + p.sh_tag) & 3);
@@ -558,62 +591,173 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
                     for (int q = 0; q < IPT; ++q)
                         if (q < cnt[c]) ot[pht + d[c] + q] = otag[c][q];
             }
-            if constexpr (REC) {
-                // a chain's IPT (< 32) bits straddle at most two words
-                uint32_t* sf = stage_f(s);
-#pragma unroll
-                for (int c = 0; c < ILP; ++c) {
-                    if (cnt[c] > 0 && obit[c] != 0) {
-                        const int w = d[c] >> 5, o = d[c] & 31;
-                        atomicOr(&sf[w], obit[c] << o);
-                        if (o + cnt[c] > 32) atomicOr(&sf[w + 1], obit[c] >> (32 - o));
-                    }
-                }
+            fence_proxy_async_smem();   // the outputs are read by the bulk-store engine
+            mbar_arrive(&staged[s]);
+            if (s_abort[it & 3]) break;
+        }
+    } else {
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int s = it % NS;
+            const bool ready = mbar_wait(&full[s], (it / NS) & 1);
+            if (!ready) {
+                set_status(&hdr->status, kDevTimeout);
+                s_abort[it & 1] = 1;
             }
-        } else {
-            V gval[ILP][IPT];
-            int dst[ILP][IPT];
-            const V* sg = stage_g(s) + in.av;
-            const int pha = int((in.ga + p.sh_cv) & (EV - 1));
-            const int boff =
-                ((pha + alen + EV - 1) / EV) * EV + int((in.gb + p.sh_cv2) & (EV - 1));
-            auto step = [&](int c, int q, auto guard) {
-                const bool takeA = decltype(guard)::value
-                                       ? (k[c] >= blen) || (j[c] < alen && !lt(b[c], a[c]))
-                                       : !lt(b[c], a[c]);
-                gval[c][q] = sg[d[c] + q];
-                dst[c][q] = takeA ? pha + j[c] : boff + k[c];
-                j[c] += takeA ? 1 : 0;
-                k[c] += takeA ? 0 : 1;
-                const K nx = km(sk[takeA ? ao + j[c] : bo + k[c]]);   // one load from either window
-                a[c] = takeA ? nx : a[c];
-                b[c] = takeA ? b[c] : nx;
-            };
-            if (fast) {
+            const StageInfo in = info[s];
+            const int alen = ready ? in.alen : 0;
+            const int blen = ready ? in.blen : 0;
+            const int len = alen + blen;
+            K* sk = stage_k(s);
+            const int ao = in.ak, bo = in.bk;   // A[0] and B[0] of the tile in the stage
+            const K* sA = sk + ao;
+            const K* sB = sk + bo;
+            int d[ILP], cnt[ILP], j[ILP], k[ILP];
+            K a[ILP], b[ILP];
+            bool fast = true;
 #pragma unroll
-                for (int q = 0; q < IPT; ++q)
+            for (int c = 0; c < ILP; ++c) {
+                d[c] = min((c * NT + tid) * IPT, len);
+                cnt[c] = min(IPT, len - d[c]);
+            }
+            split_in_tile<Log2Ceil<TILE + 1>::v>(sA, alen, sB, blen, d, j, km, lt);
 #pragma unroll
-                    for (int c = 0; c < ILP; ++c) step(c, q, BoolC<false>{});
-            } else {
+            for (int c = 0; c < ILP; ++c) {
+                k[c] = d[c] - j[c];
+                a[c] = K(0);
+                b[c] = K(0);
+                if (cnt[c] > 0) {
+                    a[c] = km(sA[j[c]]);   // may be one past A's window: never taken then
+                    b[c] = km(sB[k[c]]);
+                }
+                fast = fast && cnt[c] == IPT && j[c] + IPT <= alen && k[c] + IPT <= blen;
+            }
+            // One loop version per warp: a warp whose threads disagree would run both.
+            fast = __all_sync(0xffffffffu, fast);
+            if constexpr (!BWD) {
+                K okey[ILP][IPT];
+                V oval[ILP][VB ? IPT : 1];
+                uint32_t otag[ILP][TAG ? IPT : 1];
+                uint32_t obit[ILP];   // REC: bit q set when output q of chain c came from B
+                const V* sv = stage_v(s);
+                const int avo = in.av, bvo = in.bv;
+                if constexpr (REC) {
 #pragma unroll
-                for (int q = 0; q < IPT; ++q)
+                    for (int c = 0; c < ILP; ++c) obit[c] = 0;
+                    // cleared before the barrier below, set after it
+                    if (tid < L::WPT) stage_f(s)[tid] = 0;
+                }
+                // One merge step of chain c (ties take A).  GUARD: some side may
+                // run out within the chain's IPT steps (only near the windows' ends).
+                auto step = [&](int c, int q, auto guard) {
+                    const bool takeA = decltype(guard)::value
+                                           ? (k[c] >= blen) || (j[c] < alen && !lt(b[c], a[c]))
+                                           : !lt(b[c], a[c]);
+                    okey[c][q] = takeA ? a[c] : b[c];
+                    if constexpr (VB != 0) oval[c][q] = sv[takeA ? avo + j[c] : bvo + k[c]];
+                    if constexpr (TAG)
+                        otag[c][q] = takeA ? uint32_t(in.ga + j[c]) : uint32_t(p.tag_b + in.gb + k[c]);
+                    if constexpr (REC) obit[c] |= (takeA ? 0u : 1u) << q;
+                    j[c] += takeA ? 1 : 0;
+                    k[c] += takeA ? 0 : 1;
+                    const K nx = km(sk[takeA ? ao + j[c] : bo + k[c]]);   // one load from either window
+                    a[c] = takeA ? nx : a[c];
+                    b[c] = takeA ? b[c] : nx;
+                };
+                if (fast) {
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+#pragma unroll
+                        for (int c = 0; c < ILP; ++c) step(c, q, BoolC<false>{});
+                } else {
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+#pragma unroll
+                        for (int c = 0; c < ILP; ++c)
+                            if (q < cnt[c]) step(c, q, BoolC<true>{});
+                }
+                named_sync(1, NT);   // every input of stage s has been read
+                const int ph = int((in.gc + p.sh_ck) & (EK - 1));
+#pragma unroll
+                for (int c = 0; c < ILP; ++c)
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+                        if (q < cnt[c])
+                            sk[ph + d[c] + q] = MAPPED ? om.inverse(okey[c][q]) : okey[c][q];
+                if constexpr (VB != 0) {
+                    V* ov = stage_v(s);
+                    const int phv = int((in.gc + p.sh_cv) & (EV - 1));
 #pragma unroll
                     for (int c = 0; c < ILP; ++c)
-                        if (q < cnt[c]) step(c, q, BoolC<true>{});
+#pragma unroll
+                        for (int q = 0; q < IPT; ++q)
+                            if (q < cnt[c]) ov[phv + d[c] + q] = oval[c][q];
+                }
+                if constexpr (TAG) {
+                    uint32_t* ot = stage_t(s);
+                    const int pht = int((in.gc + p.sh_tag) & 3);
+#pragma unroll
+                    for (int c = 0; c < ILP; ++c)
+#pragma unroll
+                        for (int q = 0; q < IPT; ++q)
+                            if (q < cnt[c]) ot[pht + d[c] + q] = otag[c][q];
+                }
+                if constexpr (REC) {
+                    // a chain's IPT (< 32) bits straddle at most two words
+                    uint32_t* sf = stage_f(s);
+#pragma unroll
+                    for (int c = 0; c < ILP; ++c) {
+                        if (cnt[c] > 0 && obit[c] != 0) {
+                            const int w = d[c] >> 5, o = d[c] & 31;
+                            atomicOr(&sf[w], obit[c] << o);
+                            if (o + cnt[c] > 32) atomicOr(&sf[w + 1], obit[c] >> (32 - o));
+                        }
+                    }
+                }
+            } else {
+                V gval[ILP][IPT];
+                int dst[ILP][IPT];
+                const V* sg = stage_g(s) + in.av;
+                const int pha = int((in.ga + p.sh_cv) & (EV - 1));
+                const int boff =
+                    ((pha + alen + EV - 1) / EV) * EV + int((in.gb + p.sh_cv2) & (EV - 1));
+                auto step = [&](int c, int q, auto guard) {
+                    const bool takeA = decltype(guard)::value
+                                           ? (k[c] >= blen) || (j[c] < alen && !lt(b[c], a[c]))
+                                           : !lt(b[c], a[c]);
+                    gval[c][q] = sg[d[c] + q];
+                    dst[c][q] = takeA ? pha + j[c] : boff + k[c];
+                    j[c] += takeA ? 1 : 0;
+                    k[c] += takeA ? 0 : 1;
+                    const K nx = km(sk[takeA ? ao + j[c] : bo + k[c]]);   // one load from either window
+                    a[c] = takeA ? nx : a[c];
+                    b[c] = takeA ? b[c] : nx;
+                };
+                if (fast) {
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+#pragma unroll
+                        for (int c = 0; c < ILP; ++c) step(c, q, BoolC<false>{});
+                } else {
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+#pragma unroll
+                        for (int c = 0; c < ILP; ++c)
+                            if (q < cnt[c]) step(c, q, BoolC<true>{});
+                }
+                named_sync(1, NT);   // every input of stage s has been read
+                V* og = stage_g(s);
+#pragma unroll
+                for (int c = 0; c < ILP; ++c)
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+                        if (q < cnt[c]) og[dst[c][q]] = gval[c][q];
             }
-            named_sync(1, NT);   // every input of stage s has been read
-            V* og = stage_g(s);
-#pragma unroll
-            for (int c = 0; c < ILP; ++c)
-#pragma unroll
-                for (int q = 0; q < IPT; ++q)
-                    if (q < cnt[c]) og[dst[c][q]] = gval[c][q];
+            fence_proxy_async_smem();   // the outputs are read by the bulk-store engine
+            mbar_arrive(&staged[s]);
+            if (s_abort[it & 1]) break;
         }
-        fence_proxy_async_smem();   // the outputs are read by the bulk-store engine
-        mbar_arrive(&staged[s]);
-        if (s_abort[it & 1]) break;
     }
-    if ((s_abort[0] || s_abort[1]) && tid == 0) {
+    if ((s_abort[0] || s_abort[1] || s_abort[2] || s_abort[3]) && tid == 0) {
         // Let copies that were issued but never consumed land before exit.
         const int issued = *s_issued;
         for (int q = it; q < issued; ++q) mbar_wait(&full[q % NS], (q / NS) & 1, 100000000ull);
