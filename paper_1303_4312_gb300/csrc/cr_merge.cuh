@@ -20,8 +20,9 @@
 //      so their shared-memory latencies overlap), and after a barrier
 //      writes them back into the same stage, which then serves as the output
 //      staging buffer, and signals the stage's "staged" mbarrier.  In the
-//      forward with payloads the barrier is an mbarrier and a warp finds its
-//      splits in the next tile's stage between arriving and waiting on it.
+//      forward with payloads and at least 15 merge steps per thread and
+//      tile the barrier is an mbarrier and a warp finds its splits in the
+//      next tile's stage between arriving and waiting on it.
 //  storer (one warp): waits for a staged tile, issues the bulk store of its
 //      16-byte aligned interior, stores the ragged ends with plain stores,
 //      and hands the stage back to the producer as soon as the bulk store has
@@ -454,14 +455,16 @@ __global__ void __launch_bounds__(NT + 64, MINB) merge_tiles_kernel(const MergeA
     const OrderMap<K> om(ORD == 1 ? p.order : (ORD >= 3 ? 2 : 0));
     const auto km = [om](K x) { return MAPPED ? om(x) : x; };
     const KeyLess<ORD == 2 || ORD == 4> lt;
-    constexpr bool PIPE = VB != 0 && !BWD && !REC;
+    constexpr bool PIPE = VB != 0 && !BWD && !REC && IPT * ILP >= 15;
     // Thread tid merges ILP chains; chain c starts at diagonal (c*NT + tid)*IPT
     // and the chains run interleaved, so each thread has ILP independent
     // dependency chains of shared-memory loads in flight.
     int it = 0;
     if constexpr (PIPE) {
         // Forward with payloads, whose merge steps also gather a payload
-        // from the stage: the consumers run one tile ahead.  After merging
+        // from the stage, and at least 15 merge steps per thread and tile
+        // (with fewer the extra arrivals and polls outweigh the overlap):
+        // the consumers run one tile ahead.  After merging
         // tile it into registers a warp arrives on consumed[s] (its lanes
         // have read their inputs), waits for the next tile's stage and finds
         // its splits there, and only then waits for every warp's arrival
