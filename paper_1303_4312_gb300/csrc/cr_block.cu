@@ -99,6 +99,9 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
     using S = BlockSlots<K>;
     using V = typename VBits<VB>::T;
     constexpr int IPT = kBlockIPT;
+    // Chunk positions ride along with the keys only when something reads
+    // them at the end: payloads, the permutation or the replay backward.
+    constexpr bool IDX = VB != 0 || MODE != 0;
     extern __shared__ __align__(128) unsigned char smem[];
     K* const sk0 = reinterpret_cast<K*>(smem);
     K* const sk1 = reinterpret_cast<K*>(smem + L::KEYS);
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
 
     for (int x = tid; x < len; x += kBlockNT) {
         sk0[S::key(x)] = order_key(X[base + x], order);
-        si0[S::idx(x)] = uint16_t(x);
+        if constexpr (IDX) si0[S::idx(x)] = uint16_t(x);
         if constexpr (VB != 0 && MODE != 2) sv[x] = static_cast<const V*>(Xv)[base + x];
     }
     __syncthreads();
@@ -137,9 +140,11 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
                     const K tk = rk[q];
                     rk[q] = rk[q + 1];
                     rk[q + 1] = tk;
-                    const uint16_t ti = ri[q];
-                    ri[q] = ri[q + 1];
-                    ri[q + 1] = ti;
+                    if constexpr (IDX) {
+                        const uint16_t ti = ri[q];
+                        ri[q] = ri[q + 1];
+                        ri[q + 1] = ti;
+                    }
                 }
             }
         }
@@ -147,7 +152,7 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
         for (int q = 0; q < IPT; ++q) {
             if (q < cnt) {
                 sk0[S::key(d0 + q)] = rk[q];
-                si0[S::idx(d0 + q)] = ri[q];
+                if constexpr (IDX) si0[S::idx(d0 + q)] = ri[q];
             }
         }
         __syncthreads();
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
                     const bool takeA = (k >= blen) || (j < alen && !(b < a));
                     const int src = takeA ? ps + j : bs + k;
                     okt[q] = takeA ? a : b;
-                    oit[q] = ii[S::idx(src)];
+                    if constexpr (IDX) oit[q] = ii[S::idx(src)];
                     j += takeA ? 1 : 0;
                     k += takeA ? 0 : 1;
                     const K nx = ik[S::key(takeA ? ps + j : bs + k)];   // unused past a run
@@ -195,9 +200,11 @@ __global__ void __launch_bounds__(kBlockNT, 2) merge_runs_block_kernel(
     if constexpr (MODE != 2) {
         for (int x = tid; x < len; x += kBlockNT) {
             Y[base + x] = order_key_inverse(fk[S::key(x)], order);
-            const uint16_t src = fi[S::idx(x)];
-            if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[src];
-            if constexpr (MODE == 1) perm[base + x] = src;
+            if constexpr (IDX) {
+                const uint16_t src = fi[S::idx(x)];
+                if constexpr (VB != 0) static_cast<V*>(Yv)[base + x] = sv[src];
+                if constexpr (MODE == 1) perm[base + x] = src;
+            }
         }
     } else {
         const V* gy = static_cast<const V*>(gY);
