@@ -20,7 +20,7 @@ __all__ = [
     "merge_pass_record_bytes", "sort_runs_record", "sort_runs_backward_recorded",
     "check_sorted", "merge_runs_block", "merge_runs_block_backward_recorded",
     "merge_runs_block_length", "merge_workspace_bytes", "merge_pass_workspace_bytes",
-    "new_pass_record", "BatchedMergeGraph", "co_rank_async", "DistCoRank",
+    "new_pass_record", "BatchedMergeGraph", "co_rank_async", "DistCoRank", "host_empty",
 ]
 
 

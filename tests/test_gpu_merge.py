@@ -486,6 +486,31 @@ def test_host_merger_pipeline():
             assert same_bits(o.numpy().view(a.dtype), oracle.merge(a, b)[0])
 
 
+def test_host_merger_on_registered_buffers():
+    """HostMerger with inputs and outputs in host_empty buffers (page-locked by
+    cudaHostRegister): the buffers report pinned, have the asked shape and
+    type, and two runs in a row equal the oracle; dropping them releases the
+    registration after the device is idle, and new ones work again."""
+    rng = np.random.default_rng(110)
+    a = sorted_keys(rng, 400001, np.int32, None)
+    b = sorted_keys(rng, 123457, np.int32, None)
+    for _ in range(2):
+        hA, hB = cr.host_empty(len(a), torch.int32), cr.host_empty(len(b), torch.int32)
+        out = cr.host_empty(len(a) + len(b), torch.int32)
+        assert hA.is_pinned() and hB.is_pinned() and out.is_pinned()
+        assert hA.dtype == torch.int32 and out.shape == (len(a) + len(b),)
+        hA.copy_(torch.from_numpy(a))
+        hB.copy_(torch.from_numpy(b))
+        hm = cr.HostMerger([(len(a), len(b), torch.int32, "i32")])
+        for _ in range(2):
+            out.fill_(0)
+            hm.run([(hA, hB)], [out])
+            hm.check()
+            torch.cuda.synchronize()
+            assert same_bits(out.numpy(), oracle.merge(a, b)[0])
+        del hA, hB, out, hm
+
+
 def test_sharded_merge_single_rank_nccl():
     """The sharded merge with the library's own co-rank and merge kernels, in
     a one-rank NCCL group on this GPU (plan, windows, gather)."""
