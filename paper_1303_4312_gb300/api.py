@@ -346,12 +346,14 @@ class _HostRegistration:
 def host_empty(numel: int, dtype=torch.float32) -> torch.Tensor:
     """A page-locked host tensor for fast, asynchronous copies to and from the
     GPU (`HostMerger`'s inputs and outputs), on freshly mapped anonymous
-    memory registered with cudaHostRegister.  Unlike ``pin_memory=True``
-    (cudaHostAlloc), such buffers kept their copy bandwidth on a GB300 after
-    other processes had used much host memory: device-to-host 193 against
-    123 GB/s, both directions at once 299 against 117 GB/s (8 GiB each way).
-    The registration lasts as long as the returned tensor object; a view that
-    outlives it still reads and writes the memory, as unpinned memory."""
+    memory registered with cudaHostRegister.  On a GB300 whose host memory
+    other processes had used heavily, such buffers copied device-to-host at
+    193 GB/s and both ways at once at 299 GB/s where ``pin_memory=True``
+    (cudaHostAlloc) buffers reached 123 and 117 GB/s (8 GiB each way); the
+    copy speed in that state also depends on which host memory a buffer
+    lands on, so this is not a guarantee.  The registration lasts as long as
+    the returned tensor object; a view that outlives it still reads and
+    writes the memory, as unpinned memory."""
     es = torch.empty(0, dtype=dtype).element_size()
     reg = _HostRegistration(int(numel) * es)
     t = reg.base[:int(numel) * es].view(dtype)
